@@ -1,0 +1,357 @@
+"""Benchmark: KADABRA samples/s and time-to-stop on one GB300 per rank.
+
+One step = one complete KADABRA query (calibration, adaptive sampling until the
+stop rule holds, b~ = c/tau) on the resident R-MAT scale-20 graph (edge factor
+16, a,b,c = .57,.19,.19, undirected, largest component; eps = .01, delta = .1,
+seed 1) through the C ABI (kad_run_device).  The graph's inputs are in HBM
+before the timed region; L2 (129 MB) is flushed by writing a 512 MB buffer
+between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload rmat20]
+
+N > 1 runs under torch.distributed.run: every rank answers its own replica of
+the query stream (the sampling path has no data exchange between GPUs), the
+timed region is bracketed by barriers, the max over ranks is taken, and the
+value is the sum of samples over ranks divided by that time.
+
+--impl reference times the oracle (the plain CPU statement of the method) on
+the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "KADABRA samples/s and time-to-stop at fixed eps,delta; batched query p50/p99 vs plain"
+UNIT = "samples/s"
+
+# Algorithmic bytes per unit of the adaptive-phase work counters: 8 B row-offset
+# pair per expanded frontier vertex; 4 B column + 4 B neighbour state per scanned
+# arc; 12 B state + sigma per labelled vertex; 8 B sigma per arc into the next
+# level (or meeting set); 8 B (column + state) per arc read by the trace-back;
+# 4 B per path increment.
+BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=8, increments=4)
+
+# DRAM traffic of the adaptive-phase sampling kernel measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum), bytes per computed sample, for
+# the kernel source it was taken on; None when not measured for the current kernel.
+NCU_TRAFFIC_PER_SAMPLE = {}
+
+
+def alg_bytes(counters):
+    return sum(BYTES_PER[k] * int(v) for k, v in counters.items())
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        rows = []
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 10:
+                continue
+            if self.uuid and p[1] != self.uuid:
+                continue
+            rows.append(p)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus):
+    if n_gpus <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    world = int(os.environ["WORLD_SIZE"])
+    backend = "nccl"
+    dist.init_process_group(backend=backend)
+    return rank, world, dist
+
+
+def graph_for(workload):
+    from paper_1903_09422_gb300 import gen
+    w = gen.WORKLOADS[workload]
+    return gen.workload_graph(workload), w
+
+
+def cpu_oracle_sample(g, w, budget_s=20.0):
+    """Time the oracle on a bounded prefix of the same query: calibration plus the
+    first k adaptive epochs, k grown until the run takes at least a few seconds."""
+    import oracle
+    k, best = 1, None
+    while True:
+        t0 = time.perf_counter()
+        r = oracle.kadabra(g, w["eps"], w["delta"], w["seed"], max_epochs=k)
+        dt = time.perf_counter() - t0
+        best = (k, r, dt)
+        if dt > budget_s / 4 or r["tau"] >= r["omega"] or k >= 64:
+            break
+        k *= 2
+    k, r, dt = best
+    samples = r["calib_samples"] + r["tau"]
+    return {"value": samples / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"calibration ({r['calib_samples']} samples) + first {r['epochs']} adaptive epochs "
+                      f"({r['tau']} samples) of the same query, single-threaded C, {dt:.2f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    g, w = graph_for(args.workload)
+    import oracle
+    oracle.build()
+    # each step: calibration + one adaptive epoch of the query (the bounded sample)
+    for _ in range(args.warmup):
+        oracle.kadabra(g, w["eps"], w["delta"], w["seed"], max_epochs=1)
+    tot, samples = 0.0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.kadabra(g, w["eps"], w["delta"], w["seed"], max_epochs=1)
+        tot += time.perf_counter() - t0
+        samples += r["calib_samples"] + r["tau"]
+    v = samples / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: R-MAT scale 20 ef 16 LCC n={g.n} arcs={g.m}, "
+                                   f"eps={w['eps']} delta={w['delta']} seed={w['seed']}"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: calibration + first adaptive epoch of the query, "
+                                       "single-threaded C oracle"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="rmat20")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--slots", type=int, default=0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, dist = dist_setup(args.gpus)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1903_09422_gb300 import build, kad
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    kad.load()
+
+    g, w = graph_for(args.workload)
+    eps, delta, seed = w["eps"], w["delta"], w["seed"]
+    opts = dict(block_threads=args.block_threads or None, slots=args.slots or None)
+    stream = torch.cuda.current_stream()
+
+    # inputs resident in HBM before timing
+    d_rp = torch.from_numpy(g.row_ptr).to(dev)
+    d_col = torch.from_numpy(g.col).to(dev)
+    t0 = time.perf_counter()
+    G = kad.Graph.from_device(d_rp, d_col)
+    torch.cuda.synchronize()
+    setup_ms = 1000 * (time.perf_counter() - t0)
+    d_bc = torch.empty(g.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        G.run_device(eps, delta, seed, d_bc=d_bc, timing=True, **opts)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.4)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    results = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        ev[i][0].record(stream)
+        r = G.run_device(eps, delta, seed, d_bc=d_bc, timing=True, **opts)
+        ev[i][1].record(stream)
+        results.append(r)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    samples = sum(r["tau"] + r["calib_samples"] for r in results)
+    computed = sum(r["samples_computed"] + r["calib_samples"] for r in results)
+    if dist:
+        t = torch.tensor([total_ms, float(samples), float(computed)], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms_all, samples_all, computed_all = mx[0].item(), t[1].item(), t[2].item()
+    else:
+        total_ms_all, samples_all, computed_all = total_ms, samples, computed
+
+    # ---- end to end through the C ABI with host buffers: pinned CSR -> graph
+    # create (copy + set-up) -> run -> b~ back to pinned host memory
+    h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+    h_col = torch.from_numpy(g.col).pin_memory()
+    h_bc = torch.empty(g.n, dtype=torch.float64).pin_memory()
+    lib = kad.load()
+    import ctypes
+    e2e_times, e2e_samples = [], 0
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = ctypes.c_void_p()
+        st = lib.kad_graph_create(g.n, h_rp.data_ptr(), h_col.data_ptr(), 0, stream.cuda_stream, ctypes.byref(h))
+        if st != 0:
+            raise kad.KadError(st, "kad_graph_create")
+        res = kad.Result()
+        res.bc = h_bc.data_ptr()
+        o = kad.options(**opts)
+        st = lib.kad_run(h, eps, delta, seed, stream.cuda_stream, ctypes.byref(o), ctypes.byref(res))
+        lib.kad_graph_free(h)
+        if st != 0:
+            raise kad.KadError(st, "kad_run")
+        dt = time.perf_counter() - t0
+        if i > 0:  # first call warms the allocator
+            e2e_times.append(dt)
+            e2e_samples += res.tau + res.calib_samples
+    e2e_value = e2e_samples / sum(e2e_times)
+    if dist:
+        t = torch.tensor([e2e_value], dtype=torch.float64, device=dev)
+        dist.all_reduce(t)
+        e2e_value = t.item()
+
+    # ---- roofline of the dominant kernel (adaptive-phase sampling launch)
+    peak, peak_kind = load_peaks()
+    ab = [alg_bytes(r["counters"]) for r in results]
+    kt = [r["t_ads_kernel_ms"] for r in results]
+    achieved = sum(ab) / (sum(kt) / 1000.0) / 1e9
+    per_sample = sum(ab) / max(1, sum(r["samples_computed"] for r in results))
+    traffic = None
+    tps = NCU_TRAFFIC_PER_SAMPLE.get(args.workload)
+    if tps is not None:
+        traffic = tps * statistics.mean(r["samples_computed"] for r in results)
+    r0 = results[-1]
+    scanned = sum(r["counters"]["scanned"] for r in results)
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            try:
+                cpu = cpu_oracle_sample(g, w)
+            except Exception as ex:  # the baseline must not sink the bench line
+                cpu = {"error": str(ex)}
+        line = {
+            "metric": METRIC, "value": samples_all / (total_ms_all / 1000.0), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: R-MAT scale 20 ef 16 (a,b,c=.57,.19,.19) undirected LCC, "
+                                   f"n={g.n} arcs={g.m}; eps={eps} delta={delta} seed={seed}",
+                       "step": "one full KADABRA query (calibration + adaptive sampling to stop + b~)",
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+            "time_to_stop_ms": statistics.median(step_ms),
+            "time_to_stop_ads_ms": statistics.median(r["t_ads_ms"] for r in results),
+            "samples_computed_per_s": computed_all / (total_ms_all / 1000.0),
+            "tau": r0["tau"], "calib_samples": r0["calib_samples"], "epochs": r0["epochs"], "omega": r0["omega"],
+            "vd_bound": r0["vd_bound"], "stopped_by_omega": r0["stopped_by_omega"],
+            "algorithmic_teps": scanned / (sum(kt) / 1000.0),
+            "graph_setup_ms": setup_ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_sample (adaptive phase, one persistent launch)",
+                         "alg_bytes_per_sample": per_sample, "peak_kind": f"{peak_kind} (hbm_gbs burst)",
+                         "kernel_ms": statistics.median(kt)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.m),
+                    "d2h_bytes_per_step": int(8 * g.n), "steps": args.e2e_steps,
+                    "ms_per_step": 1000 * statistics.mean(e2e_times)},
+            "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    G.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

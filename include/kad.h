@@ -1,0 +1,177 @@
+/*
+ * kad.h -- C ABI of the GB300 (sm_103a) KADABRA sampling library.
+ *
+ * KADABRA (Borassi & Natale) approximates betweenness centrality by adaptive
+ * sampling; arXiv 1903.09422 (van der Grinten, Angriman, Meyerhenke, "Parallel
+ * Adaptive Sampling with almost no Synchronization") parallelises its sampling
+ * loop.  This library runs that loop on one GPU: every sample, the fold of
+ * samples into the sampling state, and the stop check are CUDA kernels.
+ *
+ * Problem statement (Section 2.2-2.3): given an undirected graph G, eps and
+ * delta, return b~(v) with |b~(v) - b(v)/(n(n-1))| <= eps for all v with
+ * probability >= 1 - delta, where b(v) = sum over ordered pairs s != t != v of
+ * sigma_st(v)/sigma_st.
+ *
+ * Conventions for every entry point:
+ *   - Errors are returned as kad_status; the library never aborts or exits.
+ *   - Pointers documented "host" are ordinary CPU memory; "device" pointers are
+ *     CUDA global memory on the graph's device.  The caller keeps ownership of
+ *     every array it passes; the library keeps none of them after returning.
+ *   - A CUDA error poisons the graph handle (every later call on it returns
+ *     KAD_ERR_CUDA); free it with kad_graph_free.
+ *   - Calls that take a cudaStream_t enqueue their device work on that stream
+ *     and return after synchronising it (the results are ready on return).
+ *   - A graph handle must not be used by two host threads at once.
+ */
+#ifndef KAD_H
+#define KAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *kad_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    KAD_OK = 0,
+    KAD_ERR_INVALID_ARG = 1, /* argument out of range (eps, delta, n, NULL where required, ...) */
+    KAD_ERR_BAD_CSR = 2,     /* CSR not symmetric / unsorted / self-loop / duplicate / out of range */
+    KAD_ERR_OOM = 3,         /* device or host allocation failed; nothing leaked */
+    KAD_ERR_CUDA = 4,        /* a CUDA call failed; the graph handle is poisoned */
+    KAD_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+    KAD_ERR_CANCELLED = 6,   /* the run was cancelled */
+    KAD_ERR_INTERNAL = 7     /* a device-side consistency check failed (bug report material) */
+} kad_status;
+
+typedef struct kad_graph kad_graph; /* opaque; owns a device copy of the CSR */
+
+/* Flags for kad_graph_create*. */
+#define KAD_GRAPH_TRUSTED 1u /* skip the O(m log d) symmetry/sortedness validation */
+
+/*
+ * kad_graph_create -- copy an undirected graph to the current CUDA device.
+ *
+ * Input (host): row_ptr[n+1] and col[row_ptr[n]], int32, a symmetric CSR: every
+ * undirected edge {u,v} appears as arcs u->v and v->u, each row sorted strictly
+ * ascending, no self-loops, no duplicates.  n >= 2.
+ *
+ * Graph set-up computes on the device (Section 2.3 preprocessing and
+ * Appendix C.1): the connected components, and the vertex-diameter bound
+ * VD = max over components of 2 ecc(v0) + 1, v0 = the component's vertex of
+ * largest degree (smallest id on ties), by one multi-source BFS.
+ * Errors: KAD_ERR_INVALID_ARG (n < 2, NULL pointer, m >= 2^31), KAD_ERR_BAD_CSR,
+ * KAD_ERR_OOM, KAD_ERR_CUDA.  On error *out is NULL.
+ */
+kad_status kad_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col, uint32_t flags,
+                            kad_stream_t stream, kad_graph **out);
+
+/* Same, from device arrays (copied device-to-device; the caller keeps them). */
+kad_status kad_graph_create_device(int32_t n, int64_t m, const int32_t *d_row_ptr, const int32_t *d_col,
+                                   uint32_t flags, kad_stream_t stream, kad_graph **out);
+
+/* Releases the graph and every device buffer the library holds for it. NULL is a no-op. */
+void kad_graph_free(kad_graph *g);
+
+/* Graph facts computed at creation: vertex and arc counts, VD bound, components. */
+kad_status kad_graph_info(const kad_graph *g, int32_t *n, int64_t *m, int32_t *vd_bound, int32_t *components);
+
+typedef struct {
+    uint32_t epoch_size; /* N: samples per epoch; the stop check runs after each (App. C.2; default 1000) */
+    uint32_t calib_div;  /* calibration length tau0 = N ceil(max(1, ceil(omega/calib_div))/N); default 100 */
+    uint32_t ring_epochs;/* epochs of sample frames in flight at once (0 = automatic) */
+    int32_t slots;       /* concurrent samples = resident sampling blocks (0 = automatic) */
+    int32_t mcap;        /* meeting-set size handled by the fast selection path (-1 = default;
+                            0 forces the general path; results do not depend on it) */
+    int32_t block_threads; /* threads per sampling block: 128, 256 or 512 (0 = 256) */
+    uint32_t flags;      /* KAD_RUN_* */
+    uint32_t reserved;
+} kad_options;
+
+#define KAD_RUN_TIMING 1u /* fill kad_result.t_* with CUDA-event times of each phase */
+
+/* Initialises *opt to the defaults above. */
+void kad_options_default(kad_options *opt);
+
+typedef struct {
+    /* outputs the caller may request by setting the pointer before the call (NULL = not wanted) */
+    double *bc;       /* host, n: b~(v) = counts[v]/tau, estimating b(v)/(n(n-1)) */
+    uint32_t *counts; /* host, n: sum over the used samples of x_i(v) */
+    uint32_t *c0;     /* host, n: calibration counts */
+    double *ltab;     /* host, ltab_cap: L[c] = log(1/delta_v) for calibration count c, c = 0..tau0 */
+    int64_t ltab_cap;
+    /* scalars filled by the call */
+    uint64_t tau;              /* samples used (= epochs * N) */
+    uint64_t omega;            /* maximal number of samples (Section 2.3) */
+    uint64_t calib_samples;    /* tau0 */
+    uint64_t samples_computed; /* adaptive-phase samples computed, including speculative ones */
+    uint64_t overflow_samples; /* used samples whose shortest-path count saturated at 2^64-1 */
+    uint32_t epochs;           /* stop-check epochs used */
+    int32_t vd_bound;
+    int32_t sigma_overflow;    /* 1 if any used sample saturated */
+    int32_t stopped_by_omega;  /* 1 if the run stopped because tau >= omega */
+    double tau_star;           /* calibration's bisection result */
+    /* work of the adaptive phase (all samples computed): frontier vertices expanded,
+       arcs scanned, vertices labelled, arcs into the next level or meeting set,
+       arcs scanned by the trace-back, path increments */
+    uint64_t work[6];
+    /* KAD_RUN_TIMING: milliseconds, CUDA events on the run's stream */
+    double t_total_ms, t_calib_ms, t_ads_ms, t_ads_kernel_ms;
+    uint32_t ads_launches;     /* adaptive-phase sampling-kernel launches */
+    int32_t slots_used;        /* concurrent samples (resident sampling blocks) */
+    uint32_t kernel_launches;  /* kernels this call launched (all phases) */
+    uint32_t reserved_;
+} kad_result;
+
+/*
+ * kad_run -- KADABRA on g: calibration, then adaptive sampling until the stop
+ * rule holds (Algorithm 1 of Section 2.1 with KADABRA's sample() and
+ * checkForStop of Section 2.3 and Appendix B, checked every N samples).
+ *
+ * Random numbers: sample i of phase d (0 = adaptive, 1 = calibration) draws from
+ * Philox4x32-10 with key = seed and counter = (i, block, d), so the result depends
+ * only on (g, eps, delta, seed, N, calib_div) -- never on the launch configuration
+ * (the deterministic indexed-frame idea of Appendix D.2).
+ * 0 < eps < 1, 0 < delta < 1.  Errors: KAD_ERR_INVALID_ARG, KAD_ERR_OOM,
+ * KAD_ERR_CUDA, KAD_ERR_INTERNAL.  opt NULL = defaults.
+ */
+kad_status kad_run(kad_graph *g, double eps, double delta, uint64_t seed, kad_stream_t stream,
+                   const kad_options *opt, kad_result *out);
+
+/* As kad_run, but the per-vertex outputs go to device arrays (either may be NULL):
+   d_bc[n] (double) and d_counts[n] (uint32).  out->bc/counts/c0/ltab are ignored. */
+kad_status kad_run_device(kad_graph *g, double eps, double delta, uint64_t seed, kad_stream_t stream,
+                          const kad_options *opt, double *d_bc, uint32_t *d_counts, kad_result *out);
+
+/*
+ * kad_sample_records -- the per-sample view used by parity tests: samples
+ * [i0, i0+count) of phase `domain` (0 or 1), computed by the same sampling
+ * kernel.  Host outputs (each count entries unless noted): s, t, D (= d(s,t), 0
+ * if disconnected), sigma_st (saturating), overflow (0/1), paths[count * cap]
+ * (the D-1 interior vertices in order of distance from s, then -1 padding),
+ * work[6] (as kad_result.work).  cap >= max(VD-2, 1).
+ */
+kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint64_t i0, int64_t count,
+                              kad_stream_t stream, const kad_options *opt, int32_t *s, int32_t *t, int32_t *D,
+                              uint64_t *sigma_st, int32_t *overflow, int32_t *paths, int32_t cap, uint64_t *work);
+
+/*
+ * kad_eval_fg -- the stop-check kernel's f and g (Appendix B) for n vertices on
+ * the device: f[v] = f(counts[v]/tau, exp(-ltab[c0[v]]), omega, tau), same for g.
+ * All arrays host; ltab has nclass entries; every c0[v] < nclass.
+ */
+kad_status kad_eval_fg(int32_t n, const uint32_t *counts, const uint32_t *c0, const double *ltab, int32_t nclass,
+                       uint64_t tau, uint64_t omega, double *f, double *g);
+
+/* Human-readable text of a status. Never NULL. */
+const char *kad_status_string(kad_status s);
+
+/* Library version, (major << 16) | minor. */
+uint32_t kad_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KAD_H */

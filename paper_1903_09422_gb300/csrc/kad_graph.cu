@@ -1,0 +1,314 @@
+// Graph set-up on the device: CSR validation, connected components and the
+// vertex-diameter bound that fixes omega (Section 2.3 preprocessing: "mostly
+// computing an upper bound on the diameter"; Appendix C.1: components are
+// computed with it so that pairs in different components can be skipped).
+//
+// VD = max over components C of 2 ecc_C(v0_C) + 1, with v0_C the vertex of
+// largest degree in C (smallest id on ties).  One multi-source BFS from all
+// v0_C at once computes every ecc_C, since the components are disjoint.  The
+// BFS is level-synchronous and direction-optimising (top-down while the
+// frontier's arcs are few, bottom-up once they are a large share of the graph).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kad_internal.cuh"
+
+namespace {
+
+#define GERR_RANGE 1
+#define GERR_SELF 2
+#define GERR_ORDER 4
+#define GERR_SYM 8
+#define GERR_ROWPTR 16
+#define GERR_CC 32
+
+__global__ void k_validate_rows(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+                                int64_t m, int *err) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        const int a = rp[v], b = rp[v + 1];
+        if (a > b || a < 0 || (int64_t)b > m) {
+            if (lane == 0) atomicOr(err, GERR_ROWPTR);
+            continue;
+        }
+        for (int e = a + lane; e < b; e += 32) {
+            const int w = col[e];
+            if (w < 0 || w >= n) {
+                atomicOr(err, GERR_RANGE);
+                continue;
+            }
+            if (w == v) atomicOr(err, GERR_SELF);
+            if (e > a && col[e - 1] >= w) atomicOr(err, GERR_ORDER);
+        }
+    }
+}
+
+// Every arc v->w needs its reverse w->v (binary search in the sorted row of w).
+// Runs only after k_validate_rows passed; the bounds checks stay as a guard.
+__global__ void k_validate_sym(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+                               int64_t m, int *err) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        const int a = rp[v], b = rp[v + 1];
+        if (a > b || a < 0 || (int64_t)b > m) continue;
+        for (int e = a + lane; e < b; e += 32) {
+            const int w = col[e];
+            if (w < 0 || w >= n) continue;
+            int lo = rp[w], hi = rp[w + 1];
+            if (lo > hi || lo < 0 || (int64_t)hi > m) continue;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (col[mid] < v)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            if (lo >= rp[w + 1] || col[lo] != v) atomicOr(err, GERR_SYM);
+        }
+    }
+}
+
+__global__ void k_check_ends(const int32_t *__restrict__ rp, int32_t n, int64_t m, int *err) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || (int64_t)rp[n] != m)) atomicOr(err, GERR_ROWPTR);
+}
+
+// ------------------------------------------------ connected components
+// Union-find with hooking of the larger root under the smaller one, so the
+// final root of a component is its smallest vertex id.
+__global__ void k_cc_init(int32_t *parent, int32_t n) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) parent[v] = v;
+}
+
+__device__ __forceinline__ int cc_find(int32_t *parent, int x, int32_t n) {
+    // Pointer jumping; every value written is an ancestor, so races are benign.
+    // Parent ids strictly decrease along a chain, so n steps always suffice.
+    for (int guard = 0; guard <= n; guard++) {
+        const int p = *(volatile int32_t *)(parent + x);
+        if (p == x) return x;
+        const int gp = *(volatile int32_t *)(parent + p);
+        if (gp != p) *(volatile int32_t *)(parent + x) = gp;
+        x = p;
+    }
+    return x;
+}
+
+__global__ void k_cc_hook(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+                          int32_t *parent, int *err) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        const int a = rp[v], b = rp[v + 1];
+        for (int e = a + lane; e < b; e += 32) {
+            const int w = col[e];
+            if (w >= v) continue; // each undirected edge once
+            int x = v, y = w;
+            int guard = 0;
+            for (;;) {
+                int rx = cc_find(parent, x, n), ry = cc_find(parent, y, n);
+                if (rx == ry) break;
+                if (rx < ry) {
+                    const int t = rx;
+                    rx = ry;
+                    ry = t;
+                }
+                const int old = atomicCAS(parent + rx, rx, ry);
+                if (old == rx) break;
+                x = rx;
+                y = ry;
+                if (++guard > (1 << 20)) {
+                    atomicOr(err, GERR_CC);
+                    break;
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_cc_flatten(int32_t *parent, int32_t *comp, int32_t n) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        comp[v] = cc_find(parent, v, n);
+}
+
+// best[root] = max over the component of (deg << 32) | (~v & 0xffffffff):
+// largest degree, then smallest id.
+__global__ void k_best_root(const int32_t *__restrict__ rp, const int32_t *__restrict__ comp, int32_t n,
+                            unsigned long long *best) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const unsigned long long key =
+            ((unsigned long long)(uint32_t)(rp[v + 1] - rp[v]) << 32) | (0xffffffffu - (uint32_t)v);
+        atomicMax(best + comp[v], key);
+    }
+}
+
+__global__ void k_bfs_seed(const int32_t *__restrict__ comp, const unsigned long long *__restrict__ best, int32_t n,
+                           int32_t *dist, int32_t *queue, int *qlen, int *ncomp) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (comp[v] == v) {
+            const int src = (int)(0xffffffffu - (uint32_t)(best[v] & 0xffffffffull));
+            dist[src] = 0;
+            queue[atomicAdd(qlen, 1)] = src;
+            atomicAdd(ncomp, 1);
+        }
+    }
+}
+
+__global__ void k_fill(int32_t *p, int32_t n, int32_t val) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) p[v] = val;
+}
+
+// top-down: warp per frontier vertex, coalesced neighbour loads
+__global__ void k_bfs_td(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                         const int32_t *__restrict__ q, int qlen, int32_t *dist, int32_t *nq, int *nqlen,
+                         unsigned long long *narcs, int level) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < qlen; i += warps) {
+        const int u = q[i];
+        const int a = rp[u], b = rp[u + 1];
+        for (int e = a + lane; e < b; e += 32) {
+            const int w = col[e];
+            if (*(volatile int32_t *)(dist + w) < 0 && atomicCAS(dist + w, -1, level + 1) == -1) {
+                nq[atomicAdd(nqlen, 1)] = w;
+                atomicAdd(narcs, (unsigned long long)(rp[w + 1] - rp[w]));
+            }
+        }
+    }
+}
+
+// bottom-up: thread per unvisited vertex, stop at the first parent found
+__global__ void k_bfs_bu(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n, int32_t *dist,
+                         int32_t *nq, int *nqlen, unsigned long long *narcs, int level) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (dist[v] >= 0) continue;
+        const int a = rp[v], b = rp[v + 1];
+        for (int e = a; e < b; e++) {
+            if (*(volatile int32_t *)(dist + col[e]) == level) {
+                dist[v] = level + 1;
+                nq[atomicAdd(nqlen, 1)] = v;
+                atomicAdd(narcs, (unsigned long long)(b - a));
+                break;
+            }
+        }
+    }
+}
+
+int grid_for(int64_t work, int threads, int cap) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+} // namespace
+
+#define GCHK(x)                                                                                                       \
+    do {                                                                                                              \
+        cudaError_t e_ = (x);                                                                                         \
+        if (e_ != cudaSuccess) {                                                                                      \
+            *cerr = e_;                                                                                               \
+            status = KAD_ERR_CUDA;                                                                                    \
+            goto done;                                                                                                \
+        }                                                                                                             \
+    } while (0)
+
+kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int32_t *vd_out, int32_t *ncomp_out,
+                           cudaError_t *cerr) {
+    const int32_t n = gd.n;
+    kad_status status = KAD_OK;
+    int *d_flags = nullptr; // [0] err, [1] qlen, [2] ncomp
+    int32_t *parent = nullptr, *dist = nullptr, *q0 = nullptr, *q1 = nullptr;
+    unsigned long long *best = nullptr, *d_arcs = nullptr;
+    int h_flags[3] = {0, 0, 0};
+    const int T = 256;
+    const int gw = grid_for((int64_t)n * 32, T, 65535); // warp-per-vertex kernels
+    const int gv = grid_for(n, T, 65535);
+    int level = 0, qlen = 0;
+    unsigned long long arcs = 0;
+    int32_t *qa, *qb;
+
+    if (cudaMalloc(&d_flags, 3 * sizeof(int)) != cudaSuccess || cudaMalloc(&parent, (size_t)n * 4) != cudaSuccess ||
+        cudaMalloc(&dist, (size_t)n * 4) != cudaSuccess || cudaMalloc(&q0, (size_t)n * 4) != cudaSuccess ||
+        cudaMalloc(&q1, (size_t)n * 4) != cudaSuccess || cudaMalloc(&best, (size_t)n * 8) != cudaSuccess ||
+        cudaMalloc(&d_arcs, 8) != cudaSuccess) {
+        cudaGetLastError();
+        status = KAD_ERR_OOM;
+        goto done;
+    }
+    GCHK(cudaMemsetAsync(d_flags, 0, 3 * sizeof(int), st));
+    k_check_ends<<<1, 32, 0, st>>>(gd.rp, n, gd.m, d_flags);
+    k_validate_rows<<<gw, T, 0, st>>>(gd.rp, gd.col, n, gd.m, d_flags);
+    GCHK(cudaGetLastError());
+    GCHK(cudaMemcpyAsync(h_flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaStreamSynchronize(st));
+    if (h_flags[0]) {
+        status = KAD_ERR_BAD_CSR;
+        goto done;
+    }
+    if (!(flags & KAD_GRAPH_TRUSTED)) {
+        k_validate_sym<<<gw, T, 0, st>>>(gd.rp, gd.col, n, gd.m, d_flags);
+        GCHK(cudaGetLastError());
+        GCHK(cudaMemcpyAsync(h_flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GCHK(cudaStreamSynchronize(st));
+        if (h_flags[0]) {
+            status = KAD_ERR_BAD_CSR;
+            goto done;
+        }
+    }
+
+    // components
+    k_cc_init<<<gv, T, 0, st>>>(parent, n);
+    k_cc_hook<<<gw, T, 0, st>>>(gd.rp, gd.col, n, parent, d_flags);
+    k_cc_flatten<<<gv, T, 0, st>>>(parent, gd.comp, n);
+    GCHK(cudaGetLastError());
+    GCHK(cudaMemsetAsync(best, 0, (size_t)n * 8, st));
+    k_best_root<<<gv, T, 0, st>>>(gd.rp, gd.comp, n, best);
+    k_fill<<<gv, T, 0, st>>>(dist, n, -1);
+    k_bfs_seed<<<gv, T, 0, st>>>(gd.comp, best, n, dist, q0, d_flags + 1, d_flags + 2);
+    GCHK(cudaGetLastError());
+    GCHK(cudaMemcpyAsync(h_flags, d_flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaStreamSynchronize(st));
+    if (h_flags[0] & GERR_CC) {
+        status = KAD_ERR_INTERNAL;
+        goto done;
+    }
+    qlen = h_flags[1];
+    *ncomp_out = h_flags[2];
+
+    // multi-source BFS, level by level
+    qa = q0;
+    qb = q1;
+    arcs = 0; // unknown for the seed level: start top-down
+    for (level = 0;; level++) {
+        GCHK(cudaMemsetAsync(d_flags + 1, 0, sizeof(int), st));
+        GCHK(cudaMemsetAsync(d_arcs, 0, 8, st));
+        const bool bottom_up = (int64_t)arcs * 14 > gd.m && qlen > n / 64;
+        if (bottom_up)
+            k_bfs_bu<<<gv, T, 0, st>>>(gd.rp, gd.col, n, dist, qb, d_flags + 1, d_arcs, level);
+        else
+            k_bfs_td<<<grid_for((int64_t)qlen * 32, T, 65535), T, 0, st>>>(gd.rp, gd.col, qa, qlen, dist, qb,
+                                                                          d_flags + 1, d_arcs, level);
+        GCHK(cudaGetLastError());
+        GCHK(cudaMemcpyAsync(h_flags + 1, d_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GCHK(cudaMemcpyAsync(&arcs, d_arcs, 8, cudaMemcpyDeviceToHost, st));
+        GCHK(cudaStreamSynchronize(st));
+        qlen = h_flags[1];
+        if (qlen == 0) break;
+        int32_t *t = qa;
+        qa = qb;
+        qb = t;
+    }
+    // `level` is now the largest distance reached from any source
+    *vd_out = 2 * level + 1;
+
+done:
+    cudaFree(d_flags);
+    cudaFree(parent);
+    cudaFree(dist);
+    cudaFree(q0);
+    cudaFree(q1);
+    cudaFree(best);
+    cudaFree(d_arcs);
+    return status;
+}

@@ -1,0 +1,148 @@
+// Internal definitions shared by the CUDA translation units of libkad.
+// (Nothing here is shared with the CPU oracle.)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/kad.h"
+
+// ----------------------------------------------------------------- labels
+// One 32-bit word per vertex and sampling slot:
+//   bit 31      side (0 = s side, 1 = t side)
+//   bit 30      OVF : sigma[v] wrapped (its true value is >= 2^64 -> saturate)
+//   bit 29      INM : v is in the meeting set M
+//   bit 28      OVF2: sigma2[v] (the expanding side's count at a meeting vertex) wrapped
+//   bits 0..27  level + 1  (0 in the whole word = unlabelled)
+#define KAD_SIDE 0x80000000u
+#define KAD_OVF 0x40000000u
+#define KAD_INM 0x20000000u
+#define KAD_OVF2 0x10000000u
+#define KAD_LVL 0x0FFFFFFFu
+#define KAD_KEY (KAD_SIDE | KAD_LVL)
+#define KAD_MAX_LEVEL (KAD_LVL - 2)
+
+#define KAD_U64MAX 0xffffffffffffffffull
+
+// sample-kernel output modes
+#define KAD_MODE_DIRECT 0 // increments go straight into a count array (calibration)
+#define KAD_MODE_RING 1   // paths into the epoch ring; the closer folds epochs in order
+#define KAD_MODE_RECORD 2 // full per-sample records (parity tests)
+
+// device error codes (KadCtl.err)
+#define KAD_DERR_CAP 1       // path longer than the buffer row (VD bound violated)
+#define KAD_DERR_REJECT 2    // bounded-draw rejection limit
+#define KAD_DERR_TRACE 3     // trace-back found no predecessor
+#define KAD_DERR_SELECT 4    // meeting draw found no vertex
+#define KAD_DERR_LEVEL 5     // level overflow
+#define KAD_DERR_FRONTIER 6  // list overflow
+
+// Control block of one adaptive run (device memory).
+struct KadCtl {
+    unsigned long long next;     // next sample index of the current launch
+    unsigned long long closed;   // epochs folded and checked so far
+    unsigned long long tau;      // samples used when stopped
+    unsigned long long overflow; // overflowed samples among the folded epochs
+    unsigned long long computed; // samples computed (all launches)
+    int stop;                    // 1 once the stop rule held
+    int closer;                  // closer role taken (0/1)
+    int err;                     // KAD_DERR_*, first error wins
+    int stopped_by_omega;
+};
+
+// Arguments of the sampling kernel.
+struct SampleArgs {
+    const int32_t *rp;
+    const int32_t *col;
+    const int32_t *comp;
+    int32_t n;
+    // per-slot scratch, slot-major: slot k uses [k*n, (k+1)*n)
+    uint32_t *label;
+    unsigned long long *sigma;
+    unsigned long long *sigma2;
+    int32_t *list;
+    // random stream
+    uint32_t key0, key1, domain;
+    // sample index range of this launch
+    unsigned long long i0, i1;
+    int mode;
+    int mcap;
+    // outputs (RING, RECORD)
+    int32_t *paths;
+    int32_t cap;
+    int32_t *plen;
+    uint8_t *pflag;
+    uint32_t epoch; // N
+    uint32_t ring;  // R
+    // DIRECT
+    uint32_t *dcount;
+    // RECORD extras
+    int32_t *rec_s, *rec_t, *rec_D;
+    unsigned long long *rec_sst;
+    // closer (RING)
+    KadCtl *ctl;
+    uint32_t *epoch_done; // [R]
+    uint32_t *cnt;        // [n]
+    const uint32_t *c0;   // [n]
+    int32_t *classmax;    // [nclass]
+    const double *ltab;   // [nclass]
+    int32_t nclass;
+    double eps;
+    unsigned long long omega;
+    unsigned long long k_end; // epochs of this launch end before k_end
+    // work counters [6] + samples [1]
+    unsigned long long *work;
+};
+
+// ----------------------------------------------------------------- helpers
+__device__ __forceinline__ unsigned long long kad_sat_add(unsigned long long a, unsigned long long b) {
+    unsigned long long s = a + b;
+    return (s < a) ? KAD_U64MAX : s;
+}
+
+__device__ __forceinline__ unsigned long long kad_sat_mul(unsigned long long a, unsigned long long b) {
+    return __umul64hi(a, b) ? KAD_U64MAX : a * b;
+}
+
+__device__ __forceinline__ uint32_t kad_ld_u32(const uint32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long kad_ld_u64(const unsigned long long *p) { return __ldcg(p); }
+
+__device__ __forceinline__ void kad_fence_sc() { asm volatile("fence.sc.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ void kad_set_err(KadCtl *ctl, int code) {
+    if (ctl) atomicCAS(&ctl->err, 0, code);
+}
+
+// f and g of Appendix B with a fixed operation order and correctly rounded
+// operations only (no contraction), so that host and device agree bit for bit:
+//   T = tau, W = omega, b = c/T, q = W/T, a = 1/3 -+ q, x = ((2b) W)/L,
+//   f|g = (L/T) (a + sqrt(a*a + x)).
+__device__ __forceinline__ double kad_fg_dev(unsigned long long c, double L, unsigned long long tau,
+                                             unsigned long long omega, bool upper) {
+    double T = (double)tau, W = (double)omega;
+    double b = __ddiv_rn((double)c, T);
+    double q = __ddiv_rn(W, T);
+    double third = 1.0 / 3.0;
+    double a = upper ? __dadd_rn(third, q) : __dsub_rn(third, q);
+    double x = __ddiv_rn(__dmul_rn(__dmul_rn(2.0, b), W), L);
+    return __dmul_rn(__ddiv_rn(L, T), __dadd_rn(a, __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), x))));
+}
+
+// Host-side launchers (defined in the .cu files).
+cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, cudaStream_t st);
+int kad_sample_max_blocks_per_sm(int threads);
+cudaError_t kad_launch_hist(const uint32_t *c0, int32_t n, uint32_t *hist, int32_t nclass, cudaStream_t st);
+cudaError_t kad_launch_finalize(const uint32_t *cnt, int32_t n, unsigned long long tau, double *bc, cudaStream_t st);
+cudaError_t kad_launch_fg(const uint32_t *counts, const uint32_t *c0, const double *ltab, int32_t n,
+                          unsigned long long tau, unsigned long long omega, double *f, double *g, cudaStream_t st);
+
+// graph set-up (kad_graph.cu)
+struct KadGraphDev {
+    int32_t n;
+    int64_t m;
+    int32_t *rp;
+    int32_t *col;
+    int32_t *comp;
+};
+kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int32_t *vd, int32_t *ncomp,
+                           cudaError_t *cerr);

@@ -1,0 +1,827 @@
+// The KADABRA sampling kernel and the per-epoch fold/stop check (sm_103a).
+//
+// One resident thread block owns one sampling slot and computes samples one
+// after another; sample indices are handed out by a device counter, and every
+// random number of sample i comes from Philox4x32-10 keyed by the run's seed at
+// counter (i, block, phase), so the result of a sample depends only on i.
+//
+// Per sample (Section 2.3 sample(), Appendix C.1):
+//   1. pair draw: s = U(n), t = U(n-1) (+1 if >= s), uniform over ordered pairs;
+//   2. same-component check (Appendix C.1);
+//   3. balanced bidirectional BFS with shortest-path counts sigma (uint64,
+//      saturating): each round expands the side whose frontier has the smaller
+//      degree sum (s on ties); the round that reaches the other side's frontier
+//      collects the meeting set M and the expanding side's counts at M;
+//   4. meeting draw: w in M with probability sigma_X(w) sigma_Y(w) / sigma_st,
+//      M walked in ascending vertex id;
+//   5. trace-back from w to s, then to t, rebuilt from G and the per-vertex
+//      level labels (no predecessor graph, Appendix C.1);
+//   6. output of the D-1 interior vertices.
+// A sample's labels, counts and frontier lists live in global scratch of its
+// slot and are cleared by walking the list of labelled vertices, so no Theta(n)
+// reset is needed (the purpose of Appendix C.1's timestamps).
+//
+// Epochs (Algorithm 2's consistency requirement, Section 3.1, with the fixed
+// sample-to-frame assignment of the indexed-frame algorithm, Appendix D.2):
+// epoch k is the index range [kN, (k+1)N).  The block that completes the last
+// sample of an epoch takes the closer role if free; the closer folds complete
+// epochs strictly in index order into the counts (the associative operation of
+// Algorithm 1 is integer addition) and evaluates the stop rule of Appendix B on
+// the state after each epoch, so every check sees an integral prefix of samples.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kad_internal.cuh"
+
+#define FULL_MASK 0xffffffffu
+#define KAD_MCAP_MAX 256
+
+namespace {
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011).
+__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// The random stream of one sample; used by a single thread.
+struct Stream {
+    uint32_t k0, k1, dom, blk;
+    unsigned long long idx, w0, w1;
+    int pos;
+
+    __device__ void init(uint32_t key0, uint32_t key1, unsigned long long index, uint32_t domain) {
+        k0 = key0;
+        k1 = key1;
+        idx = index;
+        dom = domain;
+        blk = 0;
+        pos = 2;
+    }
+    __device__ unsigned long long next() {
+        if (pos == 2) {
+            uint32_t c[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), blk, dom};
+            philox10(c, k0, k1);
+            w0 = (unsigned long long)c[0] | ((unsigned long long)c[1] << 32);
+            w1 = (unsigned long long)c[2] | ((unsigned long long)c[3] << 32);
+            blk++;
+            pos = 0;
+        }
+        return (pos++ == 0) ? w0 : w1;
+    }
+    // Uniform in [0, m), m >= 1: Lemire's multiply-and-reject.  The rejection
+    // loop is bounded; 64 rejections in a row have probability below 2^-64.
+    __device__ unsigned long long uniform(unsigned long long m, KadCtl *ctl) {
+        unsigned long long x = next();
+        unsigned long long lo = x * m, hi = __umul64hi(x, m);
+        if (lo < m) {
+            const unsigned long long th = (0ull - m) % m;
+            int guard = 0;
+            while (lo < th) {
+                if (++guard > 64) {
+                    kad_set_err(ctl, KAD_DERR_REJECT);
+                    break;
+                }
+                x = next();
+                lo = x * m;
+                hi = __umul64hi(x, m);
+            }
+        }
+        return hi;
+    }
+};
+
+// ---------------------------------------------------------------- block helpers
+template <int BLOCK>
+struct Smem {
+    int32_t rs[BLOCK];
+    int32_t off[BLOCK];
+    unsigned long long sig[BLOCK];
+    int32_t m_id[KAD_MCAP_MAX];
+    unsigned long long m_w[KAD_MCAP_MAX];
+    int32_t wtmp[BLOCK / 32];
+    unsigned long long wtmp64[BLOCK / 32];
+    unsigned long long bin_lo[16], bin_hi[16];
+    int tail[2], fb[2], fe[2], lev[2];
+    unsigned long long dsum[2];
+    unsigned long long next_dsum;
+    volatile int met;
+    int mcount;
+    int mid;
+    int D;
+    int s, t;
+    int try_close;
+    int action;
+    unsigned int prefix;
+    unsigned long long P;
+    unsigned long long r;
+    unsigned long long sst;
+    unsigned long long idx;
+    unsigned long long k;
+    unsigned long long ovf_acc;
+};
+
+template <int BLOCK>
+__device__ __forceinline__ int block_excl_scan(int v, int *wtmp, int &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wtmp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = (lane < BLOCK / 32) ? wtmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL_MASK, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < BLOCK / 32) wtmp[lane] = w;
+    }
+    __syncthreads();
+    const int res = ((wid > 0) ? wtmp[wid - 1] : 0) + x - v;
+    total = wtmp[BLOCK / 32 - 1];
+    __syncthreads();
+    return res;
+}
+
+// Saturating sum over the block (saturating addition is associative and
+// commutative on [0, 2^64-1], so any order gives min(exact sum, 2^64-1)).
+template <int BLOCK>
+__device__ __forceinline__ unsigned long long block_sat_sum(unsigned long long v, unsigned long long *tmp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = kad_sat_add(v, __shfl_xor_sync(FULL_MASK, v, o));
+    if (lane == 0) tmp[wid] = v;
+    __syncthreads();
+    unsigned long long r = 0;
+#pragma unroll
+    for (int i = 0; i < BLOCK / 32; i++) r = kad_sat_add(r, tmp[i]);
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_sat_scan(unsigned long long x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL_MASK, x, o);
+        if (lane >= o) x = kad_sat_add(y, x);
+    }
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL_MASK, x, o);
+    return x;
+}
+
+// Physical list position of the j-th vertex labelled on side z: the s side
+// fills the slot's list from the front, the t side from the back.
+__device__ __forceinline__ int phys(int z, int j, int n) { return z ? (n - 1 - j) : j; }
+
+// Write one interior vertex (at distance j from s, 1 <= j <= D-1).
+__device__ __forceinline__ void emit(const SampleArgs &a, int32_t *row, int D, int j, int v) {
+    if (j < 1 || j > D - 1) return;
+    if (a.mode == KAD_MODE_DIRECT) {
+        atomicAdd(a.dcount + v, 1u);
+    } else {
+        if (j - 1 < a.cap)
+            row[j - 1] = v;
+        else
+            kad_set_err(a.ctl, KAD_DERR_CAP);
+    }
+}
+
+// ---------------------------------------------------------------- closer
+// Fold epoch k (sample rows of ring slot k mod R) into the counts, then
+// evaluate the stop rule on the consistent state after k+1 epochs.
+template <int BLOCK>
+__device__ void close_epoch(const SampleArgs &a, Smem<BLOCK> &sm, unsigned long long k) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const size_t rb = (size_t)(k % a.ring) * a.epoch;
+    if (tid == 0) sm.ovf_acc = 0;
+    __syncthreads();
+    unsigned long long ovf = 0;
+    for (uint32_t j = wid; j < a.epoch; j += BLOCK / 32) {
+        const size_t row = rb + j;
+        const int len = __ldcg(a.plen + row);
+        if (lane == 0 && __ldcg(a.pflag + row)) ovf++;
+        for (int t = lane; t < len; t += 32) {
+            const int v = __ldcg(a.paths + row * (size_t)a.cap + t);
+            const unsigned int c = atomicAdd(a.cnt + v, 1u) + 1u;
+            atomicMax(a.classmax + __ldg(a.c0 + v), (int)c);
+        }
+    }
+    if (lane == 0 && ovf) atomicAdd(&sm.ovf_acc, ovf);
+    __threadfence();
+    __syncthreads();
+    const unsigned long long tau = (k + 1) * (unsigned long long)a.epoch;
+    int pass = 1;
+    if (tau < a.omega) {
+        // Appendix B: stop iff f <= eps and g <= eps for every vertex.  f and g
+        // are non-decreasing in the count for a fixed L (every operation in
+        // kad_fg_dev is correctly rounded, hence monotone), and L depends only on
+        // the calibration count, so the largest count of each calibration class
+        // decides for the whole class.
+        for (int j = tid; j < a.nclass; j += BLOCK) {
+            const int cm = __ldcg(a.classmax + j);
+            if (cm >= 0) {
+                const double L = __ldg(a.ltab + j);
+                const double f = kad_fg_dev((unsigned long long)cm, L, tau, a.omega, false);
+                const double g = kad_fg_dev((unsigned long long)cm, L, tau, a.omega, true);
+                if (!(f <= a.eps && g <= a.eps)) pass = 0;
+            }
+        }
+    }
+    const int all = __syncthreads_and(pass);
+    if (tid == 0) {
+        a.ctl->overflow += sm.ovf_acc;
+        a.epoch_done[k % a.ring] = 0;
+        if (tau >= a.omega || all) {
+            a.ctl->tau = tau;
+            a.ctl->stopped_by_omega = (tau >= a.omega) ? 1 : 0;
+            __threadfence();
+            *(volatile int *)&a.ctl->stop = 1;
+        }
+        __threadfence();
+        *(volatile unsigned long long *)&a.ctl->closed = k + 1;
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool epoch_ready(const SampleArgs &a, unsigned long long k) {
+    return k < a.k_end && *(volatile int *)&a.ctl->stop == 0 &&
+           *(volatile uint32_t *)&a.epoch_done[k % a.ring] == a.epoch;
+}
+
+// The closer role: at most one block holds it.  After releasing it the holder
+// looks once more for a complete epoch, so a completion that raced with the
+// release is never lost.  No thread ever waits for another block.
+template <int BLOCK>
+__device__ void run_closer(const SampleArgs &a, Smem<BLOCK> &sm) {
+    bool holding = false;
+    if (threadIdx.x == 0) holding = (atomicCAS(&a.ctl->closer, 0, 1) == 0);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int action = 0;
+            for (int guard = 0; holding && guard < 4; guard++) {
+                kad_fence_sc();
+                unsigned long long k = *(volatile unsigned long long *)&a.ctl->closed;
+                if (epoch_ready(a, k)) {
+                    action = 1;
+                    sm.k = k;
+                    break;
+                }
+                atomicExch(&a.ctl->closer, 0);
+                holding = false;
+                kad_fence_sc();
+                k = *(volatile unsigned long long *)&a.ctl->closed;
+                if (epoch_ready(a, k) && atomicCAS(&a.ctl->closer, 0, 1) == 0) holding = true;
+            }
+            if (holding && action == 0) { // guard ran out: give the role back
+                atomicExch(&a.ctl->closer, 0);
+                holding = false;
+            }
+            sm.action = action;
+        }
+        __syncthreads();
+        if (sm.action == 0) break;
+        close_epoch<BLOCK>(a, sm, sm.k);
+    }
+}
+
+// ---------------------------------------------------------------- the kernel
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
+    __shared__ Smem<BLOCK> sm;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int32_t n = a.n;
+    const size_t soff = (size_t)blockIdx.x * (size_t)n;
+    uint32_t *const label = a.label + soff;
+    unsigned long long *const sigma = a.sigma + soff;
+    unsigned long long *const sigma2 = a.sigma2 + soff;
+    int32_t *const list = a.list + soff;
+    const int mcap = (a.mcap < KAD_MCAP_MAX) ? a.mcap : KAD_MCAP_MAX;
+
+    // work counters (thread 0 except pred, which every thread counts)
+    unsigned long long w_exp = 0, w_scan = 0, w_lab = 0, w_trace = 0, w_inc = 0, w_smp = 0, w_pred = 0;
+    Stream st;
+
+    for (;;) {
+        // ---------------------------------------------------- next sample index
+        if (tid == 0) {
+            unsigned long long idx = ~0ull;
+            const bool stopped = (a.mode == KAD_MODE_RING) && (*(volatile int *)&a.ctl->stop != 0);
+            if (!stopped) {
+                const unsigned long long i = atomicAdd(&a.ctl->next, 1ull);
+                if (i < a.i1) idx = i;
+            }
+            sm.idx = idx;
+        }
+        __syncthreads();
+        const unsigned long long idx = sm.idx;
+        if (idx == ~0ull) break;
+
+        // ---------------------------------------------------- pair draw
+        if (tid == 0) {
+            st.init(a.key0, a.key1, idx, a.domain);
+            const int s = (int)st.uniform((unsigned long long)n, a.ctl);
+            int t = (int)st.uniform((unsigned long long)(n - 1), a.ctl);
+            if (t >= s) t++;
+            sm.s = s;
+            sm.t = t;
+            sm.tail[0] = sm.tail[1] = 0;
+            sm.D = 0;
+            if (__ldg(a.comp + s) == __ldg(a.comp + t)) {
+                label[s] = 1u;            // s side, level 0
+                label[t] = KAD_SIDE | 1u; // t side, level 0
+                sigma[s] = 1ull;
+                sigma[t] = 1ull;
+                list[0] = s;
+                list[n - 1] = t;
+                sm.tail[0] = sm.tail[1] = 1;
+                sm.fb[0] = sm.fb[1] = 0;
+                sm.fe[0] = sm.fe[1] = 1;
+                sm.lev[0] = sm.lev[1] = 0;
+                sm.dsum[0] = (unsigned long long)(__ldg(a.rp + s + 1) - __ldg(a.rp + s));
+                sm.dsum[1] = (unsigned long long)(__ldg(a.rp + t + 1) - __ldg(a.rp + t));
+                sm.D = -1; // searching
+            }
+            __threadfence_block();
+        }
+        __syncthreads();
+
+        // ---------------------------------------------------- balanced bidirectional BFS
+        int X = 0;
+        while (sm.D < 0) {
+            X = (sm.dsum[0] <= sm.dsum[1]) ? 0 : 1;
+            const int Y = 1 - X;
+            const int fb = sm.fb[X], fe = sm.fe[X];
+            const int levX = sm.lev[X];
+            const int tailY = sm.tail[Y];
+            __syncthreads();
+            if (fb == fe || levX + 2 > (int)KAD_LVL) {
+                if (tid == 0) {
+                    if (fb != fe) kad_set_err(a.ctl, KAD_DERR_LEVEL);
+                    sm.D = 0; // no path
+                }
+                __syncthreads();
+                break;
+            }
+            const uint32_t sideX = X ? KAD_SIDE : 0u;
+            const uint32_t keyNext = sideX | (uint32_t)(levX + 2);
+            if (tid == 0) {
+                w_exp += (unsigned long long)(fe - fb);
+                w_scan += sm.dsum[X];
+                sm.met = 0;
+                sm.next_dsum = 0;
+            }
+            __syncthreads();
+            unsigned long long pred_next = 0, pred_m = 0;
+            for (int cb = fb; cb < fe; cb += BLOCK) {
+                const int cnt = min(BLOCK, fe - cb);
+                int d = 0;
+                if (tid < cnt) {
+                    const int u = __ldcg(list + phys(X, cb + tid, n));
+                    const int rs = __ldg(a.rp + u), re = __ldg(a.rp + u + 1);
+                    const uint32_t lu = kad_ld_u32(label + u);
+                    sm.rs[tid] = rs;
+                    sm.sig[tid] = (lu & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + u);
+                    d = re - rs;
+                }
+                int total;
+                const int excl = block_excl_scan<BLOCK>(d, sm.wtmp, total);
+                if (tid < cnt) sm.off[tid] = excl;
+                __syncthreads();
+                for (int base = 0; base < total; base += BLOCK) {
+                    const int e = base + tid;
+                    const bool valid = e < total;
+                    bool claimed = false;
+                    int v = 0, vdeg = 0;
+                    if (valid) {
+                        // frontier entry owning arc e: last j with off[j] <= e
+                        int lo = 0, hi = cnt - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (sm.off[mid] <= e)
+                                lo = mid;
+                            else
+                                hi = mid - 1;
+                        }
+                        v = __ldg(a.col + sm.rs[lo] + (e - sm.off[lo]));
+                        const unsigned long long su = sm.sig[lo];
+                        uint32_t lv = kad_ld_u32(label + v);
+                        if (lv == 0u && !sm.met) {
+                            const uint32_t old = atomicCAS(label + v, 0u, keyNext);
+                            if (old == 0u) {
+                                claimed = true;
+                                lv = keyNext;
+                            } else {
+                                lv = old;
+                            }
+                        }
+                        if (lv != 0u) {
+                            if ((lv & KAD_KEY) == keyNext) {
+                                pred_next++;
+                                const unsigned long long old = atomicAdd(sigma + v, su);
+                                if (old + su < old) atomicOr(label + v, KAD_OVF);
+                            } else if ((lv & KAD_SIDE) != sideX) {
+                                // v is on the other side's frontier: the searches meet.
+                                pred_m++;
+                                sm.met = 1;
+                                if (!(lv & KAD_INM)) atomicOr(label + v, KAD_INM);
+                                const unsigned long long old = atomicAdd(sigma2 + v, su);
+                                if (old + su < old) atomicOr(label + v, KAD_OVF2);
+                            }
+                        }
+                        if (claimed) vdeg = __ldg(a.rp + v + 1) - __ldg(a.rp + v);
+                    }
+                    const unsigned mask = __ballot_sync(FULL_MASK, claimed);
+                    if (mask) {
+                        const int leader = __ffs(mask) - 1;
+                        int pos0 = 0;
+                        if (lane == leader) pos0 = atomicAdd(&sm.tail[X], __popc(mask));
+                        pos0 = __shfl_sync(FULL_MASK, pos0, leader);
+                        if (claimed) {
+                            const int pos = pos0 + __popc(mask & lanemask_lt());
+                            if (pos + tailY < n)
+                                list[phys(X, pos, n)] = v;
+                            else
+                                kad_set_err(a.ctl, KAD_DERR_FRONTIER);
+                        }
+                        const unsigned long long ds = warp_sum_u64((unsigned long long)vdeg);
+                        if (lane == 0) atomicAdd(&sm.next_dsum, ds);
+                    }
+                }
+                __syncthreads();
+            }
+            const int met = sm.met;
+            w_pred += met ? pred_m : pred_next;
+            __syncthreads();
+            if (tid == 0) {
+                if (met) {
+                    sm.D = sm.lev[X] + 1 + sm.lev[Y];
+                } else {
+                    const int tl = min(sm.tail[X], n - tailY);
+                    w_lab += (unsigned long long)(tl - fe);
+                    sm.fb[X] = fe;
+                    sm.fe[X] = tl;
+                    sm.lev[X] = levX + 1;
+                    sm.dsum[X] = sm.next_dsum;
+                }
+            }
+            __syncthreads();
+        }
+
+        const int D = sm.D;
+        unsigned long long sst = 0;
+        // ---------------------------------------------------- meeting draw
+        if (D > 0) {
+            const int Y = 1 - X;
+            const int yb = sm.fb[Y], ye = sm.fe[Y];
+            if (tid == 0) sm.mcount = 0;
+            __syncthreads();
+            unsigned long long part = 0;
+            for (int j = yb + tid; j < ye; j += BLOCK) {
+                const int v = __ldcg(list + phys(Y, j, n));
+                const uint32_t lv = kad_ld_u32(label + v);
+                if (lv & KAD_INM) {
+                    const unsigned long long sx = (lv & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + v);
+                    const unsigned long long sy = (lv & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + v);
+                    const unsigned long long w = kad_sat_mul(sx, sy);
+                    part = kad_sat_add(part, w);
+                    const int slot = atomicAdd(&sm.mcount, 1);
+                    if (slot < mcap) {
+                        sm.m_id[slot] = v;
+                        sm.m_w[slot] = w;
+                    }
+                }
+            }
+            sst = block_sat_sum<BLOCK>(part, sm.wtmp64);
+            if (tid == 0) {
+                sm.sst = sst;
+                sm.r = st.uniform(sst ? sst : 1ull, a.ctl);
+                sm.mid = -1;
+            }
+            __syncthreads();
+            const int mc = sm.mcount;
+            const unsigned long long r = sm.r;
+            if (mc <= mcap) {
+                // Small M: the exclusive prefix of each member in id order is the
+                // sum of the weights of the members with smaller ids.
+                for (int i = tid; i < mc; i += BLOCK) {
+                    const int id = sm.m_id[i];
+                    const unsigned long long w = sm.m_w[i];
+                    unsigned long long ex = 0;
+                    for (int j = 0; j < mc; j++)
+                        if (sm.m_id[j] < id) ex = kad_sat_add(ex, sm.m_w[j]);
+                    if (ex <= r && kad_sat_add(ex, w) > r) sm.mid = id;
+                }
+            } else {
+                // Large M: select by id digits, 4 bits per pass from the top,
+                // with exact 128-bit bin sums.
+                const int nb = 32 - __clz(max(n - 1, 1));
+                const int top = ((nb + 3) / 4) * 4;
+                unsigned int prefix = 0;
+                unsigned long long P = 0;
+                for (int shift = top - 4; shift >= 0; shift -= 4) {
+                    if (tid < 16) {
+                        sm.bin_lo[tid] = 0;
+                        sm.bin_hi[tid] = 0;
+                    }
+                    __syncthreads();
+                    for (int j = yb + tid; j < ye; j += BLOCK) {
+                        const int v = __ldcg(list + phys(Y, j, n));
+                        const uint32_t lv = kad_ld_u32(label + v);
+                        if (!(lv & KAD_INM)) continue;
+                        if (((unsigned long long)(unsigned)v >> (shift + 4)) !=
+                            ((unsigned long long)prefix >> (shift + 4)))
+                            continue;
+                        const unsigned long long sx = (lv & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + v);
+                        const unsigned long long sy = (lv & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + v);
+                        const unsigned long long w = kad_sat_mul(sx, sy);
+                        const int b = ((unsigned)v >> shift) & 15;
+                        const unsigned long long old = atomicAdd(&sm.bin_lo[b], w);
+                        if (old + w < old) atomicAdd(&sm.bin_hi[b], 1ull);
+                    }
+                    __syncthreads();
+                    if (tid == 0) {
+                        unsigned long long cum = P;
+                        int chosen = -1;
+                        for (int b = 0; b < 16; b++) {
+                            const unsigned long long bw = sm.bin_hi[b] ? KAD_U64MAX : sm.bin_lo[b];
+                            const unsigned long long nc = kad_sat_add(cum, bw);
+                            if (nc > r) {
+                                chosen = b;
+                                break;
+                            }
+                            cum = nc;
+                        }
+                        if (chosen < 0) {
+                            kad_set_err(a.ctl, KAD_DERR_SELECT);
+                            chosen = 0;
+                        }
+                        sm.P = cum;
+                        sm.prefix = prefix | ((unsigned)chosen << shift);
+                    }
+                    __syncthreads();
+                    P = sm.P;
+                    prefix = sm.prefix;
+                }
+                if (tid == 0) sm.mid = (int)prefix;
+            }
+            __syncthreads();
+        }
+
+        // ---------------------------------------------------- trace-back + output
+        size_t row = 0;
+        if (a.mode == KAD_MODE_RING)
+            row = (size_t)((idx / a.epoch) % a.ring) * a.epoch + (size_t)(idx % a.epoch);
+        else if (a.mode == KAD_MODE_RECORD)
+            row = (size_t)(idx - a.i0);
+        int32_t *const out = (a.mode == KAD_MODE_DIRECT) ? nullptr : a.paths + row * (size_t)a.cap;
+        if (D > 0 && wid == 0) {
+            const int Y = 1 - X;
+            const int mid = sm.mid;
+            if (mid < 0 || mid >= n) {
+                if (lane == 0) kad_set_err(a.ctl, KAD_DERR_SELECT);
+            } else {
+                // distance and path count of the meeting vertex on each side:
+                // side X reaches it at level lev[X]+1 (count in sigma2), side Y
+                // holds it at level lev[Y] (count in sigma)
+                const uint32_t lm = kad_ld_u32(label + mid);
+                const int dX = sm.lev[X] + 1, dY = sm.lev[Y];
+                const unsigned long long gX = (lm & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + mid);
+                const unsigned long long gY = (lm & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + mid);
+                if (lane == 0) emit(a, out, D, (X == 0) ? dX : dY, mid);
+                for (int z = 0; z < 2; z++) {
+                    int cur = mid, d = (z == X) ? dX : dY;
+                    unsigned long long sc = (z == X) ? gX : gY;
+                    while (d >= 1) {
+                        unsigned long long r = 0;
+                        if (lane == 0) r = st.uniform(sc, a.ctl);
+                        r = __shfl_sync(FULL_MASK, r, 0);
+                        const uint32_t key = (z ? KAD_SIDE : 0u) | (uint32_t)d; // level d-1
+                        const int rs = __ldg(a.rp + cur), re = __ldg(a.rp + cur + 1);
+                        unsigned long long carry = 0, s_sel = 0;
+                        int p_sel = -1;
+                        for (int base = rs; base < re; base += 32) {
+                            const int e = base + lane;
+                            const bool valid = e < re;
+                            const int p = valid ? __ldg(a.col + e) : 0;
+                            unsigned long long wgt = 0;
+                            if (valid) {
+                                const uint32_t lp = kad_ld_u32(label + p);
+                                if ((lp & KAD_KEY) == key) wgt = (lp & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + p);
+                            }
+                            const unsigned long long incl = warp_incl_sat_scan(wgt);
+                            const unsigned long long cum = kad_sat_add(carry, incl);
+                            const unsigned hit = __ballot_sync(FULL_MASK, valid && cum > r);
+                            if (hit) {
+                                const int fl = __ffs(hit) - 1;
+                                p_sel = __shfl_sync(FULL_MASK, p, fl);
+                                s_sel = __shfl_sync(FULL_MASK, wgt, fl);
+                                if (lane == 0) w_trace += (unsigned long long)(base + fl - rs + 1);
+                                break;
+                            }
+                            carry = kad_sat_add(carry, __shfl_sync(FULL_MASK, incl, 31));
+                        }
+                        if (p_sel < 0) {
+                            if (lane == 0) kad_set_err(a.ctl, KAD_DERR_TRACE);
+                            break;
+                        }
+                        d--;
+                        if (lane == 0 && d >= 1) emit(a, out, D, z == 0 ? d : D - d, p_sel);
+                        cur = p_sel;
+                        sc = s_sel;
+                    }
+                }
+            }
+        }
+        if (tid == 0) {
+            const int inc = (D > 0) ? D - 1 : 0;
+            w_inc += (unsigned long long)inc;
+            w_smp++;
+            if (a.mode != KAD_MODE_DIRECT) {
+                a.plen[row] = (inc <= a.cap) ? inc : a.cap;
+                a.pflag[row] = (sst == KAD_U64MAX) ? 1 : 0;
+            }
+            if (a.mode == KAD_MODE_RECORD) {
+                a.rec_s[row] = sm.s;
+                a.rec_t[row] = sm.t;
+                a.rec_D[row] = D;
+                a.rec_sst[row] = sst;
+            }
+        }
+        __syncthreads();
+
+        // ---------------------------------------------------- reset the slot
+        {
+            const int t0 = min(sm.tail[0], n), t1 = min(sm.tail[1], n - t0);
+            for (int j = tid; j < t0 + t1; j += BLOCK) {
+                const int pos = (j < t0) ? j : n - 1 - (j - t0);
+                const int v = __ldcg(list + pos);
+                const uint32_t lv = kad_ld_u32(label + v);
+                label[v] = 0u;
+                sigma[v] = 0ull;
+                if (lv & KAD_INM) sigma2[v] = 0ull;
+            }
+        }
+        __threadfence_block();
+        __syncthreads();
+
+        // ---------------------------------------------------- epoch bookkeeping
+        if (a.mode == KAD_MODE_RING) {
+            if (tid == 0) {
+                __threadfence();
+                const unsigned long long e = idx / a.epoch;
+                const unsigned int old = atomicAdd(&a.epoch_done[e % a.ring], 1u);
+                kad_fence_sc();
+                sm.try_close = (old + 1u == a.epoch) ? 1 : 0;
+            }
+            __syncthreads();
+            if (sm.try_close) run_closer<BLOCK>(a, sm);
+        }
+    }
+
+    // ---------------------------------------------------- work counters
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w_pred += __shfl_xor_sync(FULL_MASK, w_pred, o);
+    if (lane == 0 && w_pred) atomicAdd(a.work + 3, w_pred);
+    if (tid == 0) {
+        if (w_exp) atomicAdd(a.work + 0, w_exp);
+        if (w_scan) atomicAdd(a.work + 1, w_scan);
+        if (w_lab) atomicAdd(a.work + 2, w_lab);
+        if (w_trace) atomicAdd(a.work + 4, w_trace);
+        if (w_inc) atomicAdd(a.work + 5, w_inc);
+        if (w_smp) atomicAdd(a.work + 6, w_smp);
+    }
+}
+
+// ---------------------------------------------------------------- small kernels
+// Histogram of the calibration counts: hist[c] = |{v : c0[v] = c}|.
+__global__ void k_hist(const uint32_t *__restrict__ c0, int32_t n, uint32_t *__restrict__ hist, int32_t nclass) {
+    extern __shared__ uint32_t sh[];
+    const bool use_sh = nclass <= 8192;
+    if (use_sh)
+        for (int i = threadIdx.x; i < nclass; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const uint32_t c = __ldg(c0 + v);
+        if (c < (uint32_t)nclass) {
+            if (use_sh)
+                atomicAdd(sh + c, 1u);
+            else
+                atomicAdd(hist + c, 1u);
+        }
+    }
+    __syncthreads();
+    if (use_sh)
+        for (int i = threadIdx.x; i < nclass; i += blockDim.x)
+            if (sh[i]) atomicAdd(hist + i, sh[i]);
+}
+
+// b~(v) = c(v)/tau (Section 2.3), correctly rounded division.
+__global__ void k_finalize(const uint32_t *__restrict__ cnt, int32_t n, unsigned long long tau, double *__restrict__ bc) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        bc[v] = __ddiv_rn((double)__ldg(cnt + v), (double)tau);
+}
+
+__global__ void k_fg(const uint32_t *__restrict__ counts, const uint32_t *__restrict__ c0,
+                     const double *__restrict__ ltab, int32_t n, unsigned long long tau, unsigned long long omega,
+                     double *__restrict__ f, double *__restrict__ g) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const double L = ltab[c0[v]];
+        f[v] = kad_fg_dev(counts[v], L, tau, omega, false);
+        g[v] = kad_fg_dev(counts[v], L, tau, omega, true);
+    }
+}
+
+} // namespace
+
+// ---------------------------------------------------------------- launchers
+cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    switch (threads) {
+    case 128:
+        k_sample<128><<<blocks, 128, 0, st>>>(a);
+        break;
+    case 512:
+        k_sample<512><<<blocks, 512, 0, st>>>(a);
+        break;
+    default:
+        k_sample<256><<<blocks, 256, 0, st>>>(a);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+int kad_sample_max_blocks_per_sm(int threads) {
+    int nb = 0;
+    cudaError_t e;
+    switch (threads) {
+    case 128:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<128>, 128, 0);
+        break;
+    case 512:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<512>, 512, 0);
+        break;
+    default:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<256>, 256, 0);
+        break;
+    }
+    return (e == cudaSuccess) ? nb : 0;
+}
+
+cudaError_t kad_launch_hist(const uint32_t *c0, int32_t n, uint32_t *hist, int32_t nclass, cudaStream_t st) {
+    const int threads = 512;
+    int blocks = (n + threads - 1) / threads;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    const size_t sh = (nclass <= 8192) ? (size_t)nclass * sizeof(uint32_t) : 0;
+    k_hist<<<blocks, threads, sh, st>>>(c0, n, hist, nclass);
+    return cudaGetLastError();
+}
+
+cudaError_t kad_launch_finalize(const uint32_t *cnt, int32_t n, unsigned long long tau, double *bc, cudaStream_t st) {
+    const int threads = 256;
+    int blocks = (n + threads - 1) / threads;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_finalize<<<blocks, threads, 0, st>>>(cnt, n, tau, bc);
+    return cudaGetLastError();
+}
+
+cudaError_t kad_launch_fg(const uint32_t *counts, const uint32_t *c0, const double *ltab, int32_t n,
+                          unsigned long long tau, unsigned long long omega, double *f, double *g, cudaStream_t st) {
+    const int threads = 256;
+    int blocks = (n + threads - 1) / threads;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_fg<<<blocks, threads, 0, st>>>(counts, c0, ltab, n, tau, omega, f, g);
+    return cudaGetLastError();
+}

@@ -1,0 +1,268 @@
+"""Python binding of libkad (include/kad.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; this module
+converts arrays, passes the CUDA stream (PyTorch's current stream by default)
+and turns status codes into exceptions.  It has no CPU fallback: if
+libkad.so is missing, importing the binding fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkad.so")
+
+KAD_GRAPH_TRUSTED = 1
+KAD_RUN_TIMING = 1
+WORK_NAMES = ("expanded", "scanned", "labelled", "pred_arcs", "trace_arcs", "increments")
+
+
+class KadError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})" if what else status_string(status))
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("epoch_size", ctypes.c_uint32), ("calib_div", ctypes.c_uint32), ("ring_epochs", ctypes.c_uint32),
+                ("slots", ctypes.c_int32), ("mcap", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("bc", ctypes.c_void_p), ("counts", ctypes.c_void_p), ("c0", ctypes.c_void_p),
+                ("ltab", ctypes.c_void_p), ("ltab_cap", ctypes.c_int64),
+                ("tau", ctypes.c_uint64), ("omega", ctypes.c_uint64), ("calib_samples", ctypes.c_uint64),
+                ("samples_computed", ctypes.c_uint64), ("overflow_samples", ctypes.c_uint64),
+                ("epochs", ctypes.c_uint32), ("vd_bound", ctypes.c_int32), ("sigma_overflow", ctypes.c_int32),
+                ("stopped_by_omega", ctypes.c_int32), ("tau_star", ctypes.c_double),
+                ("work", ctypes.c_uint64 * 6),
+                ("t_total_ms", ctypes.c_double), ("t_calib_ms", ctypes.c_double), ("t_ads_ms", ctypes.c_double),
+                ("t_ads_kernel_ms", ctypes.c_double), ("ads_launches", ctypes.c_uint32),
+                ("slots_used", ctypes.c_int32), ("kernel_launches", ctypes.c_uint32),
+                ("reserved_", ctypes.c_uint32)]
+
+
+EXPORTS = ("kad_graph_create", "kad_graph_create_device", "kad_graph_free", "kad_graph_info", "kad_options_default",
+           "kad_run", "kad_run_device", "kad_sample_records", "kad_eval_fg", "kad_status_string", "kad_version")
+
+_lib = None
+
+
+def load():
+    """Load libkad.so (raises ImportError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u32, u64, dbl = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64,
+                                   ctypes.c_double)
+    st = ctypes.c_int
+    lib.kad_graph_create.argtypes = [i32, vp, vp, u32, vp, ctypes.POINTER(vp)]
+    lib.kad_graph_create.restype = st
+    lib.kad_graph_create_device.argtypes = [i32, i64, vp, vp, u32, vp, ctypes.POINTER(vp)]
+    lib.kad_graph_create_device.restype = st
+    lib.kad_graph_free.argtypes = [vp]
+    lib.kad_graph_free.restype = None
+    lib.kad_graph_info.argtypes = [vp, vp, vp, vp, vp]
+    lib.kad_graph_info.restype = st
+    lib.kad_options_default.argtypes = [ctypes.POINTER(Options)]
+    lib.kad_options_default.restype = None
+    lib.kad_run.argtypes = [vp, dbl, dbl, u64, vp, ctypes.POINTER(Options), ctypes.POINTER(Result)]
+    lib.kad_run.restype = st
+    lib.kad_run_device.argtypes = [vp, dbl, dbl, u64, vp, ctypes.POINTER(Options), vp, vp, ctypes.POINTER(Result)]
+    lib.kad_run_device.restype = st
+    lib.kad_sample_records.argtypes = [vp, u64, u32, u64, i64, vp, ctypes.POINTER(Options), vp, vp, vp, vp, vp, vp,
+                                       i32, vp]
+    lib.kad_sample_records.restype = st
+    lib.kad_eval_fg.argtypes = [i32, vp, vp, vp, i32, u64, u64, vp, vp]
+    lib.kad_eval_fg.restype = st
+    lib.kad_status_string.argtypes = [st]
+    lib.kad_status_string.restype = ctypes.c_char_p
+    lib.kad_version.argtypes = []
+    lib.kad_version.restype = u32
+    _lib = lib
+    return lib
+
+
+def status_string(s):
+    return load().kad_status_string(s).decode()
+
+
+def _check(s, what):
+    if s != 0:
+        raise KadError(s, what)
+
+
+def _stream_handle(stream):
+    """cudaStream_t of `stream` (a torch.cuda.Stream, an int handle, or None =
+    PyTorch's current stream)."""
+    if isinstance(stream, int):
+        return stream
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def options(**kw):
+    o = Options()
+    load().kad_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class Graph:
+    """A graph resident on the current CUDA device (kad_graph)."""
+
+    def __init__(self, row_ptr, col, trusted=False, stream=None, _handle=None):
+        lib = load()
+        self._h = None
+        if _handle is not None:
+            self._h = _handle
+        else:
+            rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            cl = np.ascontiguousarray(col, dtype=np.int32)
+            if cl.size == 0:
+                cl = np.zeros(1, np.int32)
+            h = ctypes.c_void_p()
+            _check(lib.kad_graph_create(rp.size - 1, rp.ctypes.data, cl.ctypes.data,
+                                        KAD_GRAPH_TRUSTED if trusted else 0, _stream_handle(stream), ctypes.byref(h)),
+                   "kad_graph_create")
+            self._h = h
+        n, m, vd, nc = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.kad_graph_info(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(vd), ctypes.byref(nc)),
+               "kad_graph_info")
+        self.n, self.m, self.vd_bound, self.components = n.value, m.value, vd.value, nc.value
+
+    @classmethod
+    def from_csr(cls, csr, **kw):
+        return cls(csr.row_ptr, csr.col, **kw)
+
+    @classmethod
+    def from_device(cls, d_row_ptr, d_col, trusted=False, stream=None):
+        """From device tensors (torch, int32, contiguous); copied device-to-device."""
+        lib = load()
+        h = ctypes.c_void_p()
+        n = d_row_ptr.numel() - 1
+        _check(lib.kad_graph_create_device(n, d_col.numel(), d_row_ptr.data_ptr(), d_col.data_ptr(),
+                                           KAD_GRAPH_TRUSTED if trusted else 0, _stream_handle(stream),
+                                           ctypes.byref(h)), "kad_graph_create_device")
+        return cls(None, None, _handle=h)
+
+    @property
+    def path_cap(self):
+        return max(self.vd_bound - 2, 1)
+
+    def close(self):
+        if self._h:
+            load().kad_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- runs
+    def run(self, eps, delta, seed, stream=None, bc=True, counts=True, c0=False, ltab=False, timing=False, **opt):
+        """kad_run: returns a dict with the scalars of kad_result and the requested arrays."""
+        lib = load()
+        o = options(**opt)
+        if timing:
+            o.flags |= KAD_RUN_TIMING
+        r = Result()
+        out = {}
+        if bc:
+            out["bc"] = np.zeros(self.n, np.float64)
+            r.bc = out["bc"].ctypes.data
+        if counts:
+            out["counts"] = np.zeros(self.n, np.uint32)
+            r.counts = out["counts"].ctypes.data
+        if c0:
+            out["c0"] = np.zeros(self.n, np.uint32)
+            r.c0 = out["c0"].ctypes.data
+        if ltab:
+            cap = 1 << 22
+            out["L"] = np.zeros(cap, np.float64)
+            r.ltab = out["L"].ctypes.data
+            r.ltab_cap = cap
+        _check(lib.kad_run(self._h, eps, delta, seed, _stream_handle(stream), ctypes.byref(o), ctypes.byref(r)),
+               "kad_run")
+        out.update(_result_scalars(r))
+        if ltab:
+            out["L"] = out["L"][: r.calib_samples + 1].copy()
+        return out
+
+    def run_device(self, eps, delta, seed, d_bc=None, d_counts=None, stream=None, timing=False, **opt):
+        """kad_run_device: per-vertex outputs into device tensors (float64 / int32-sized)."""
+        lib = load()
+        o = options(**opt)
+        if timing:
+            o.flags |= KAD_RUN_TIMING
+        r = Result()
+        _check(lib.kad_run_device(self._h, eps, delta, seed, _stream_handle(stream), ctypes.byref(o),
+                                  d_bc.data_ptr() if d_bc is not None else None,
+                                  d_counts.data_ptr() if d_counts is not None else None, ctypes.byref(r)),
+               "kad_run_device")
+        return _result_scalars(r)
+
+    def sample_records(self, seed, i0, count, domain=0, cap=None, stream=None, **opt):
+        """Per-sample records of samples [i0, i0+count) (same layout as the oracle's)."""
+        lib = load()
+        cap = self.path_cap if cap is None else cap
+        o = options(**opt)
+        s = np.zeros(count, np.int32)
+        t = np.zeros(count, np.int32)
+        D = np.zeros(count, np.int32)
+        sst = np.zeros(count, np.uint64)
+        ovf = np.zeros(count, np.int32)
+        paths = np.zeros((count, cap), np.int32)
+        work = np.zeros(6, np.uint64)
+        _check(lib.kad_sample_records(self._h, seed, domain, i0, count, _stream_handle(stream), ctypes.byref(o),
+                                      s.ctypes.data, t.ctypes.data, D.ctypes.data, sst.ctypes.data, ovf.ctypes.data,
+                                      paths.ctypes.data, cap, work.ctypes.data), "kad_sample_records")
+        return dict(s=s, t=t, D=D, sigma_st=sst, overflow=ovf, paths=paths, cap=cap,
+                    counters=dict(zip(WORK_NAMES, (int(x) for x in work))))
+
+
+def _result_scalars(r):
+    d = {k: getattr(r, k) for k in ("tau", "omega", "calib_samples", "samples_computed", "overflow_samples", "epochs",
+                                    "vd_bound", "sigma_overflow", "stopped_by_omega", "tau_star", "t_total_ms",
+                                    "t_calib_ms", "t_ads_ms", "t_ads_kernel_ms", "ads_launches", "slots_used",
+                                    "kernel_launches")}
+    d["counters"] = dict(zip(WORK_NAMES, (int(x) for x in r.work)))
+    return d
+
+
+def eval_fg(counts, c0, ltab, tau, omega):
+    """The device stop-check arithmetic (Appendix B f and g) for every vertex."""
+    lib = load()
+    counts = np.ascontiguousarray(counts, np.uint32)
+    c0 = np.ascontiguousarray(c0, np.uint32)
+    ltab = np.ascontiguousarray(ltab, np.float64)
+    f = np.zeros(counts.size, np.float64)
+    g = np.zeros(counts.size, np.float64)
+    _check(lib.kad_eval_fg(counts.size, counts.ctypes.data, c0.ctypes.data, ltab.ctypes.data, ltab.size, tau, omega,
+                           f.ctypes.data, g.ctypes.data), "kad_eval_fg")
+    return f, g
+
+
+def version():
+    v = load().kad_version()
+    return (v >> 16, v & 0xffff)

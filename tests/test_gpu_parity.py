@@ -1,0 +1,181 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Integer results (pairs, distances, sigma_st, paths, counts, tau, epochs,
+calibration counts, overflow flags, work counters) must match bit for bit; f, g
+and the L table must agree within 1e-12 relative (expected: bit-exact, both
+sides use the same correctly rounded operation order).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1903_09422_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kad():
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1903_09422_gb300 import build, kad as K
+    build.build()
+    return K
+
+
+def diamond_chain(k, width=2):
+    edges, nxt, prev = [], 1, 0
+    for _ in range(k):
+        for m in range(nxt, nxt + width):
+            edges += [(prev, m), (m, nxt + width)]
+        prev, nxt = nxt + width, nxt + width + 1
+    return gen.from_edges(prev + 1, edges)
+
+
+GRAPHS = {
+    "rmat12": lambda: gen.rmat(12, 8, seed=1),
+    "rmat10_s5": lambda: gen.rmat(10, 4, seed=5),
+    "er60": lambda: gen.er(60, 0.1, seed=2),
+    "er200": lambda: gen.er(200, 0.1, seed=4),
+    "grid9x13": lambda: gen.grid_plain(9, 13),
+    "grid64": lambda: gen.grid(64, seed=3),
+    "path40": lambda: gen.path_graph(40),
+    "star50": lambda: gen.star_graph(50),
+    "diamond70": lambda: diamond_chain(70),
+    "two_comp": lambda: gen.from_edges(12, [(0, 1), (1, 2), (2, 3), (3, 0), (4, 5), (5, 6), (6, 7), (7, 8), (8, 9),
+                                            (9, 10), (10, 11)]),
+    "isolated": lambda: gen.from_edges(6, [(0, 1), (1, 2)]),
+}
+
+
+def compare_records(rec, orc):
+    for k in ("s", "t", "D", "sigma_st", "overflow"):
+        np.testing.assert_array_equal(rec[k], orc[k], err_msg=k)
+    np.testing.assert_array_equal(rec["paths"], orc["paths"], err_msg="paths")
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+@pytest.mark.parametrize("domain", [0, 1])
+def test_sample_records_match_oracle(kad, name, domain):
+    g = GRAPHS[name]()
+    count = 1500
+    with kad.Graph.from_csr(g) as G:
+        assert G.vd_bound == O.vd_bound(g)
+        rec = G.sample_records(seed=7, i0=123, count=count, domain=domain)
+    orc = O.samples(g, 7, 123, count, domain=domain)
+    compare_records(rec, orc)
+    assert rec["counters"] == orc["counters"]
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_full_run_matches_oracle(kad, name):
+    g = GRAPHS[name]()
+    eps, delta, seed = 0.05, 0.1, 3
+    ref = O.kadabra(g, eps, delta, seed)
+    with kad.Graph.from_csr(g) as G:
+        r = G.run(eps, delta, seed, c0=True, ltab=True)
+    assert (r["tau"], r["epochs"], r["omega"], r["calib_samples"], r["vd_bound"]) == \
+        (ref["tau"], ref["epochs"], ref["omega"], ref["calib_samples"], ref["vd"])
+    np.testing.assert_array_equal(r["c0"], ref["c0"])
+    np.testing.assert_array_equal(r["L"], ref["L"])
+    assert r["tau_star"] == ref["tau_star"]
+    np.testing.assert_array_equal(r["counts"], ref["counts"])
+    np.testing.assert_array_equal(r["bc"], ref["bc"])
+    assert r["overflow_samples"] == ref["overflow_samples"]
+    assert r["stopped_by_omega"] == int(ref["stopped_by_omega"])
+    assert r["samples_computed"] >= r["tau"]
+
+
+@pytest.mark.parametrize("opt", [dict(block_threads=128), dict(block_threads=512), dict(slots=1), dict(slots=7),
+                                 dict(mcap=0), dict(mcap=1), dict(ring_epochs=2), dict(slots=3, ring_epochs=2),
+                                 dict(epoch_size=250)])
+def test_result_independent_of_launch_configuration(kad, opt):
+    g = gen.rmat(12, 8, seed=1)
+    eps, delta, seed = 0.03, 0.1, 11
+    N = opt.get("epoch_size", 1000)
+    ref = O.kadabra(g, eps, delta, seed, epoch=N)
+    with kad.Graph.from_csr(g) as G:
+        r = G.run(eps, delta, seed, **opt)
+        rec = G.sample_records(seed, 0, 700, **{k: v for k, v in opt.items() if k != "epoch_size"})
+    assert r["tau"] == ref["tau"] and r["epochs"] == ref["epochs"]
+    np.testing.assert_array_equal(r["counts"], ref["counts"])
+    compare_records(rec, O.samples(g, seed, 0, 700))
+
+
+def test_meeting_selection_paths_agree_on_hub_graph(kad):
+    # Many-member meeting sets: force the general (digit-wise) selection and the
+    # small-set path; both must give the oracle's records.
+    g = gen.rmat(14, 16, seed=2)
+    orc = O.samples(g, 5, 0, 800)
+    with kad.Graph.from_csr(g) as G:
+        a = G.sample_records(5, 0, 800, mcap=0)
+        b = G.sample_records(5, 0, 800, mcap=256)
+    compare_records(a, orc)
+    compare_records(b, orc)
+
+
+def test_fg_kernel_matches_oracle(kad):
+    g = gen.rmat(12, 8, seed=1)
+    ref = O.kadabra(g, 0.05, 0.1, 1)
+    tau, om = ref["tau"], ref["omega"]
+    f, gg = kad.eval_fg(ref["counts"], ref["c0"], ref["L"], tau, om)
+    fo = np.array([O.f(int(c), float(ref["L"][k]), tau, om) for c, k in zip(ref["counts"], ref["c0"])])
+    go = np.array([O.g(int(c), float(ref["L"][k]), tau, om) for c, k in zip(ref["counts"], ref["c0"])])
+    np.testing.assert_allclose(f, fo, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(gg, go, rtol=1e-12, atol=0)
+    assert np.array_equal(f, fo) and np.array_equal(gg, go)  # expected bit-exact
+
+
+def test_repeated_runs_and_graph_reuse(kad):
+    g = gen.rmat(11, 8, seed=9)
+    with kad.Graph.from_csr(g) as G:
+        r1 = G.run(0.05, 0.1, 5)
+        r2 = G.run(0.02, 0.1, 6)
+        r3 = G.run(0.05, 0.1, 5)
+    np.testing.assert_array_equal(r1["counts"], r3["counts"])
+    ref = O.kadabra(g, 0.02, 0.1, 6)
+    np.testing.assert_array_equal(r2["counts"], ref["counts"])
+
+
+def test_device_outputs_and_device_graph(kad):
+    import torch
+    g = gen.rmat(12, 8, seed=1)
+    ref = O.kadabra(g, 0.05, 0.1, 2)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    with kad.Graph.from_device(rp, col) as G:
+        d_bc = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        d_cnt = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        r = G.run_device(0.05, 0.1, 2, d_bc=d_bc, d_counts=d_cnt)
+        torch.cuda.synchronize()
+    assert r["tau"] == ref["tau"]
+    np.testing.assert_array_equal(d_cnt.cpu().numpy().view(np.uint32), ref["counts"])
+    np.testing.assert_array_equal(d_bc.cpu().numpy(), ref["bc"])
+
+
+def test_bad_csr_is_rejected(kad):
+    g = gen.er(30, 0.2, seed=1)
+    col = g.col.copy()
+    col[0], col[1] = col[1], col[0]  # unsorted row
+    with pytest.raises(kad.KadError) as e:
+        kad.Graph(g.row_ptr, col)
+    assert e.value.status == 2
+    # asymmetric: drop one arc's reverse by pointing it elsewhere
+    h = gen.path_graph(10)
+    col = h.col.copy()
+    col[-1] = 7  # last row (vertex 9) now points to 7 instead of 8
+    with pytest.raises(kad.KadError):
+        kad.Graph(h.row_ptr, col)
+    with pytest.raises(kad.KadError):
+        kad.Graph(np.array([0, 1], np.int32), np.array([0], np.int32))  # n = 1
+
+
+def test_invalid_run_arguments(kad):
+    g = gen.path_graph(10)
+    with kad.Graph.from_csr(g) as G:
+        for eps, delta in [(0, 0.1), (1.0, 0.1), (0.1, 0), (0.1, 1.5)]:
+            with pytest.raises(kad.KadError) as e:
+                G.run(eps, delta, 1)
+            assert e.value.status == 1
+        r = G.run(0.1, 0.1, 1)  # the handle stays usable
+        assert r["tau"] > 0
