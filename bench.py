@@ -37,9 +37,9 @@ UNIT = "samples/s"
 # Algorithmic bytes per unit of the adaptive-phase work counters: 8 B row-offset
 # pair per expanded frontier vertex; 4 B column + 4 B neighbour state per scanned
 # arc; 12 B state + sigma per labelled vertex; 8 B sigma per arc into the next
-# level (or meeting set); 8 B (column + state) per arc read by the trace-back;
-# 4 B per path increment.
-BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=8, increments=4)
+# level (or meeting set); 4 B per path increment.  The trace-back's reads are not
+# counted: they depend on how the predecessors are found, not on the sample.
+BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=0, increments=4)
 
 # DRAM traffic of the adaptive-phase sampling kernel measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), bytes per computed sample, for
@@ -157,6 +157,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from paper_1903_09422_gb300 import gen
     g, w = graph_for(args.workload)
     import oracle
     oracle.build()
@@ -173,8 +174,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: R-MAT scale 20 ef 16 LCC n={g.n} arcs={g.m}, "
-                                   f"eps={w['eps']} delta={w['delta']} seed={w['seed']}"},
+            "config": {"workload": f"{args.workload}: {gen.describe(args.workload)}; n={g.n} arcs={g.m}"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "per step: calibration + first adaptive epoch of the query, "
                                        "single-threaded C oracle"},
@@ -211,6 +211,7 @@ def main():
         dist.barrier()
     kad.load()
 
+    from paper_1903_09422_gb300 import gen
     g, w = graph_for(args.workload)
     eps, delta, seed = w["eps"], w["delta"], w["seed"]
     opts = dict(block_threads=args.block_threads or None, slots=args.slots or None)
@@ -322,8 +323,7 @@ def main():
             "metric": METRIC, "value": samples_all / (total_ms_all / 1000.0), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: R-MAT scale 20 ef 16 (a,b,c=.57,.19,.19) undirected LCC, "
-                                   f"n={g.n} arcs={g.m}; eps={eps} delta={delta} seed={seed}",
+            "config": {"workload": f"{args.workload}: {gen.describe(args.workload)}; n={g.n} arcs={g.m}",
                        "step": "one full KADABRA query (calibration + adaptive sampling to stop + b~)",
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
             "time_to_stop_ms": statistics.median(step_ms),

@@ -85,12 +85,13 @@ typedef struct {
     int32_t slots;       /* concurrent samples = resident sampling blocks (0 = automatic) */
     int32_t mcap;        /* meeting-set size handled by the fast selection path (-1 = default;
                             0 forces the general path; results do not depend on it) */
-    int32_t block_threads; /* threads per sampling block: 128, 256 or 512 (0 = 256) */
+    int32_t block_threads; /* threads per sampling block: 128, 256 or 512 (0 = 512) */
     uint32_t flags;      /* KAD_RUN_* */
-    uint32_t reserved;
+    uint32_t debug;      /* KAD_DEBUG_* (tests only; results do not depend on it) */
 } kad_options;
 
-#define KAD_RUN_TIMING 1u /* fill kad_result.t_* with CUDA-event times of each phase */
+#define KAD_RUN_TIMING 1u      /* fill kad_result.t_* with CUDA-event times of each phase */
+#define KAD_DEBUG_TRACE_SCAN 1u /* trace-back always scans the current vertex's adjacency */
 
 /* Initialises *opt to the defaults above. */
 void kad_options_default(kad_options *opt);

@@ -294,7 +294,7 @@ int device_sms(int dev) {
 }
 
 int resolve_threads(const kad_options &o) {
-    return (o.block_threads == 128 || o.block_threads == 512) ? o.block_threads : 256;
+    return (o.block_threads == 128 || o.block_threads == 256) ? o.block_threads : 512;
 }
 
 // Number of sampling slots: all resident blocks, capped by a share of free memory.
@@ -419,6 +419,7 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     if ((e = cudaMemsetAsync(w.work, 0, 8 * sizeof(unsigned long long), st)) != cudaSuccess) return fail(g, e);
     SampleArgs a = base_args(g, seed);
     a.mcap = (o.mcap < 0) ? kDefaultMcap : o.mcap;
+    a.debug = o.debug;
     a.domain = 1;
     a.i0 = 0;
     a.i1 = tau0;
@@ -690,6 +691,7 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
     {
         SampleArgs a = base_args(g, seed);
         a.mcap = (o.mcap < 0) ? kDefaultMcap : o.mcap;
+        a.debug = o.debug;
         a.domain = domain;
         a.i0 = i0;
         a.i1 = i0 + c;

@@ -67,6 +67,7 @@ struct SampleArgs {
     unsigned long long i0, i1;
     int mode;
     int mcap;
+    uint32_t debug; // KAD_DEBUG_*
     // outputs (RING, RECORD)
     int32_t *paths;
     int32_t cap;

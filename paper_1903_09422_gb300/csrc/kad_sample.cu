@@ -35,6 +35,10 @@
 
 #define FULL_MASK 0xffffffffu
 #define KAD_MCAP_MAX 256
+#define KAD_ITEMS 4     // arcs per thread per expansion pass
+#define KAD_MAXLV 62    // levels whose list ranges are kept for the trace-back
+#define KAD_LCAP 64     // largest predecessor level searched from its list
+#define KAD_DEG_SCAN 64 // adjacency lists up to this length are always scanned
 
 namespace {
 
@@ -120,6 +124,7 @@ struct Smem {
     unsigned long long wtmp64[BLOCK / 32];
     unsigned long long bin_lo[16], bin_hi[16];
     int tail[2], fb[2], fe[2], lev[2];
+    int lvs[2][KAD_MAXLV + 2]; // logical list start of level l, l <= KAD_MAXLV + 1
     unsigned long long dsum[2];
     unsigned long long next_dsum;
     volatile int met;
@@ -212,6 +217,123 @@ __device__ __forceinline__ void emit(const SampleArgs &a, int32_t *row, int D, i
         else
             kad_set_err(a.ctl, KAD_DERR_CAP);
     }
+}
+
+// ---------------------------------------------------------------- trace-back
+// One trace-back step at `cur` (on side z, distance d): among the neighbours p
+// at distance d-1, in ascending id (CSR) order, pick the first whose running
+// sum of sigma(p) exceeds r (Appendix C.1: the path is rebuilt from G and the
+// distance labels).  Called by one warp; every lane returns the same choice.
+
+// Scan adj(cur) 4 x 32 arcs per pass (all loads of a pass issued first).
+__device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *label,
+                                           const unsigned long long *sigma, int z, int d, int rsC, int reC,
+                                           unsigned long long r, int &p_sel, unsigned long long &s_sel,
+                                           unsigned long long &w_trace) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t key = (z ? KAD_SIDE : 0u) | (uint32_t)d; // level d-1
+    unsigned long long carry = 0;
+    for (int base = rsC; base < reC; base += 128) {
+        int pp[4];
+        uint32_t lp[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int e = base + 32 * k + lane;
+            pp[k] = (e < reC) ? __ldg(a.col + e) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? kad_ld_u32(label + pp[k]) : 0u;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            unsigned long long wgt = 0;
+            if (pp[k] >= 0 && (lp[k] & KAD_KEY) == key)
+                wgt = (lp[k] & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + pp[k]);
+            const unsigned long long incl = warp_incl_sat_scan(wgt);
+            const unsigned long long cum = kad_sat_add(carry, incl);
+            const unsigned hit = __ballot_sync(FULL_MASK, pp[k] >= 0 && cum > r);
+            if (hit) {
+                const int fl = __ffs(hit) - 1;
+                p_sel = __shfl_sync(FULL_MASK, pp[k], fl);
+                s_sel = __shfl_sync(FULL_MASK, wgt, fl);
+                if (lane == 0) w_trace += (unsigned long long)(base + 32 * k + fl - rsC + 1);
+                return;
+            }
+            carry = kad_sat_add(carry, __shfl_sync(FULL_MASK, incl, 31));
+        }
+    }
+}
+
+__device__ __forceinline__ bool row_contains(const int32_t *col, int lo, int hi, int key, int &probes) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const int v = __ldg(col + mid);
+        probes++;
+        if (v < key)
+            lo = mid + 1;
+        else if (v > key)
+            hi = mid;
+        else
+            return true;
+    }
+    return false;
+}
+
+// When cur has many neighbours but level d-1 of side z has at most KAD_LCAP
+// vertices, test each of those for adjacency to cur (binary search in the
+// shorter of the two sorted rows) and select among the adjacent ones in
+// ascending id order: the same candidates, order and choice as the scan.
+template <int BLOCK>
+__device__ __forceinline__ void trace_from_level(const SampleArgs &a, const uint32_t *label,
+                                                 const unsigned long long *sigma, const int32_t *list, int n, int z,
+                                                 int ls, int lcnt, int cur, int rsC, int reC, unsigned long long r,
+                                                 int &p_sel, unsigned long long &s_sel, unsigned long long &w_trace) {
+    const int lane = threadIdx.x & 31;
+    int pc[2];
+    unsigned long long wc[2];
+    int probes = 0;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int j = lane + 32 * k;
+        pc[k] = -1;
+        wc[k] = 0;
+        if (j < lcnt) {
+            const int p = __ldcg(list + phys(z, ls + j, n));
+            const int rsP = __ldg(a.rp + p), reP = __ldg(a.rp + p + 1);
+            const bool adj = (reP - rsP <= reC - rsC) ? row_contains(a.col, rsP, reP, cur, probes)
+                                                      : row_contains(a.col, rsC, reC, p, probes);
+            if (adj) {
+                const uint32_t lp = kad_ld_u32(label + p);
+                pc[k] = p;
+                wc[k] = (lp & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + p);
+            }
+        }
+    }
+    // exclusive prefix of each candidate in id order
+    unsigned long long ex[2] = {0ull, 0ull};
+#pragma unroll
+    for (int slot = 0; slot < 2; slot++) {
+        for (int q = 0; q < 32; q++) {
+            const int pq = __shfl_sync(FULL_MASK, pc[slot], q);
+            const unsigned long long wq = __shfl_sync(FULL_MASK, wc[slot], q);
+#pragma unroll
+            for (int k = 0; k < 2; k++)
+                if (pq >= 0 && pc[k] >= 0 && pq < pc[k]) ex[k] = kad_sat_add(ex[k], wq);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const bool win = pc[k] >= 0 && ex[k] <= r && kad_sat_add(ex[k], wc[k]) > r;
+        const unsigned hit = __ballot_sync(FULL_MASK, win);
+        if (hit) {
+            const int fl = __ffs(hit) - 1;
+            p_sel = __shfl_sync(FULL_MASK, pc[k], fl);
+            s_sel = __shfl_sync(FULL_MASK, wc[k], fl);
+        }
+    }
+    unsigned long long pr = probes;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pr += __shfl_xor_sync(FULL_MASK, pr, o);
+    if (lane == 0) w_trace += pr;
 }
 
 // ---------------------------------------------------------------- closer
@@ -367,6 +489,8 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
                 sm.fb[0] = sm.fb[1] = 0;
                 sm.fe[0] = sm.fe[1] = 1;
                 sm.lev[0] = sm.lev[1] = 0;
+                sm.lvs[0][0] = sm.lvs[1][0] = 0;
+                sm.lvs[0][1] = sm.lvs[1][1] = 1;
                 sm.dsum[0] = (unsigned long long)(__ldg(a.rp + s + 1) - __ldg(a.rp + s));
                 sm.dsum[1] = (unsigned long long)(__ldg(a.rp + t + 1) - __ldg(a.rp + t));
                 sm.D = -1; // searching
@@ -417,64 +541,83 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
                 const int excl = block_excl_scan<BLOCK>(d, sm.wtmp, total);
                 if (tid < cnt) sm.off[tid] = excl;
                 __syncthreads();
-                for (int base = 0; base < total; base += BLOCK) {
-                    const int e = base + tid;
-                    const bool valid = e < total;
-                    bool claimed = false;
-                    int v = 0, vdeg = 0;
-                    if (valid) {
-                        // frontier entry owning arc e: last j with off[j] <= e
-                        int lo = 0, hi = cnt - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (sm.off[mid] <= e)
-                                lo = mid;
-                            else
-                                hi = mid - 1;
-                        }
-                        v = __ldg(a.col + sm.rs[lo] + (e - sm.off[lo]));
-                        const unsigned long long su = sm.sig[lo];
-                        uint32_t lv = kad_ld_u32(label + v);
-                        if (lv == 0u && !sm.met) {
-                            const uint32_t old = atomicCAS(label + v, 0u, keyNext);
-                            if (old == 0u) {
-                                claimed = true;
-                                lv = keyNext;
-                            } else {
-                                lv = old;
+                // KAD_ITEMS arcs per thread and pass: all neighbour ids are loaded
+                // before any label, and all labels before any atomic, so each
+                // thread keeps several independent loads in flight.
+                for (int base = 0; base < total; base += BLOCK * KAD_ITEMS) {
+                    int vv[KAD_ITEMS];
+                    unsigned long long ss[KAD_ITEMS];
+                    uint32_t ll[KAD_ITEMS];
+#pragma unroll
+                    for (int k = 0; k < KAD_ITEMS; k++) {
+                        const int e = base + k * BLOCK + tid;
+                        vv[k] = -1;
+                        ss[k] = 0;
+                        if (e < total) {
+                            // frontier entry owning arc e: last j with off[j] <= e
+                            int lo = 0, hi = cnt - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (sm.off[mid] <= e)
+                                    lo = mid;
+                                else
+                                    hi = mid - 1;
                             }
+                            vv[k] = __ldg(a.col + sm.rs[lo] + (e - sm.off[lo]));
+                            ss[k] = sm.sig[lo];
                         }
-                        if (lv != 0u) {
-                            if ((lv & KAD_KEY) == keyNext) {
-                                pred_next++;
-                                const unsigned long long old = atomicAdd(sigma + v, su);
-                                if (old + su < old) atomicOr(label + v, KAD_OVF);
-                            } else if ((lv & KAD_SIDE) != sideX) {
-                                // v is on the other side's frontier: the searches meet.
-                                pred_m++;
-                                sm.met = 1;
-                                if (!(lv & KAD_INM)) atomicOr(label + v, KAD_INM);
-                                const unsigned long long old = atomicAdd(sigma2 + v, su);
-                                if (old + su < old) atomicOr(label + v, KAD_OVF2);
-                            }
-                        }
-                        if (claimed) vdeg = __ldg(a.rp + v + 1) - __ldg(a.rp + v);
                     }
-                    const unsigned mask = __ballot_sync(FULL_MASK, claimed);
-                    if (mask) {
-                        const int leader = __ffs(mask) - 1;
-                        int pos0 = 0;
-                        if (lane == leader) pos0 = atomicAdd(&sm.tail[X], __popc(mask));
-                        pos0 = __shfl_sync(FULL_MASK, pos0, leader);
-                        if (claimed) {
-                            const int pos = pos0 + __popc(mask & lanemask_lt());
-                            if (pos + tailY < n)
-                                list[phys(X, pos, n)] = v;
-                            else
-                                kad_set_err(a.ctl, KAD_DERR_FRONTIER);
+#pragma unroll
+                    for (int k = 0; k < KAD_ITEMS; k++) ll[k] = (vv[k] >= 0) ? kad_ld_u32(label + vv[k]) : 0u;
+#pragma unroll
+                    for (int k = 0; k < KAD_ITEMS; k++) {
+                        const int v = vv[k];
+                        bool claimed = false;
+                        int vdeg = 0;
+                        if (v >= 0) {
+                            const unsigned long long su = ss[k];
+                            uint32_t lv = ll[k];
+                            if (lv == 0u && !sm.met) {
+                                const uint32_t old = atomicCAS(label + v, 0u, keyNext);
+                                if (old == 0u) {
+                                    claimed = true;
+                                    lv = keyNext;
+                                } else {
+                                    lv = old;
+                                }
+                            }
+                            if (lv != 0u) {
+                                if ((lv & KAD_KEY) == keyNext) {
+                                    pred_next++;
+                                    const unsigned long long old = atomicAdd(sigma + v, su);
+                                    if (old + su < old) atomicOr(label + v, KAD_OVF);
+                                } else if ((lv & KAD_SIDE) != sideX) {
+                                    // v is on the other side's frontier: the searches meet.
+                                    pred_m++;
+                                    sm.met = 1;
+                                    if (!(lv & KAD_INM)) atomicOr(label + v, KAD_INM);
+                                    const unsigned long long old = atomicAdd(sigma2 + v, su);
+                                    if (old + su < old) atomicOr(label + v, KAD_OVF2);
+                                }
+                            }
+                            if (claimed) vdeg = __ldg(a.rp + v + 1) - __ldg(a.rp + v);
                         }
-                        const unsigned long long ds = warp_sum_u64((unsigned long long)vdeg);
-                        if (lane == 0) atomicAdd(&sm.next_dsum, ds);
+                        const unsigned mask = __ballot_sync(FULL_MASK, claimed);
+                        if (mask) {
+                            const int leader = __ffs(mask) - 1;
+                            int pos0 = 0;
+                            if (lane == leader) pos0 = atomicAdd(&sm.tail[X], __popc(mask));
+                            pos0 = __shfl_sync(FULL_MASK, pos0, leader);
+                            if (claimed) {
+                                const int pos = pos0 + __popc(mask & lanemask_lt());
+                                if (pos + tailY < n)
+                                    list[phys(X, pos, n)] = v;
+                                else
+                                    kad_set_err(a.ctl, KAD_DERR_FRONTIER);
+                            }
+                            const unsigned long long ds = warp_sum_u64((unsigned long long)vdeg);
+                            if (lane == 0) atomicAdd(&sm.next_dsum, ds);
+                        }
                     }
                 }
                 __syncthreads();
@@ -491,6 +634,7 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
                     sm.fb[X] = fe;
                     sm.fe[X] = tl;
                     sm.lev[X] = levX + 1;
+                    if (levX + 2 <= KAD_MAXLV + 1) sm.lvs[X][levX + 2] = tl;
                     sm.dsum[X] = sm.next_dsum;
                 }
             }
@@ -625,30 +769,20 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
                         unsigned long long r = 0;
                         if (lane == 0) r = st.uniform(sc, a.ctl);
                         r = __shfl_sync(FULL_MASK, r, 0);
-                        const uint32_t key = (z ? KAD_SIDE : 0u) | (uint32_t)d; // level d-1
-                        const int rs = __ldg(a.rp + cur), re = __ldg(a.rp + cur + 1);
-                        unsigned long long carry = 0, s_sel = 0;
                         int p_sel = -1;
-                        for (int base = rs; base < re; base += 32) {
-                            const int e = base + lane;
-                            const bool valid = e < re;
-                            const int p = valid ? __ldg(a.col + e) : 0;
-                            unsigned long long wgt = 0;
-                            if (valid) {
-                                const uint32_t lp = kad_ld_u32(label + p);
-                                if ((lp & KAD_KEY) == key) wgt = (lp & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + p);
-                            }
-                            const unsigned long long incl = warp_incl_sat_scan(wgt);
-                            const unsigned long long cum = kad_sat_add(carry, incl);
-                            const unsigned hit = __ballot_sync(FULL_MASK, valid && cum > r);
-                            if (hit) {
-                                const int fl = __ffs(hit) - 1;
-                                p_sel = __shfl_sync(FULL_MASK, p, fl);
-                                s_sel = __shfl_sync(FULL_MASK, wgt, fl);
-                                if (lane == 0) w_trace += (unsigned long long)(base + fl - rs + 1);
-                                break;
-                            }
-                            carry = kad_sat_add(carry, __shfl_sync(FULL_MASK, incl, 31));
+                        unsigned long long s_sel = 0;
+                        const int rsC = __ldg(a.rp + cur), reC = __ldg(a.rp + cur + 1);
+                        const int ls = (d <= KAD_MAXLV) ? sm.lvs[z][d - 1] : 0;
+                        const int lcnt = (d <= KAD_MAXLV) ? sm.lvs[z][d] - ls : KAD_LCAP + 1;
+                        if (d == 1) {
+                            // the only vertex at distance 0 is the root
+                            p_sel = z ? sm.t : sm.s;
+                            s_sel = 1ull;
+                        } else if (!(a.debug & KAD_DEBUG_TRACE_SCAN) && reC - rsC > KAD_DEG_SCAN && lcnt <= KAD_LCAP) {
+                            trace_from_level<BLOCK>(a, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel,
+                                                    s_sel, w_trace);
+                        } else {
+                            trace_scan(a, label, sigma, z, d, rsC, reC, r, p_sel, s_sel, w_trace);
                         }
                         if (p_sel < 0) {
                             if (lane == 0) kad_set_err(a.ctl, KAD_DERR_TRACE);

@@ -161,10 +161,22 @@ def grid_plain(rows: int, cols: int) -> CSR:
 # Named workloads: graph recipe plus the (eps, delta, seed) each is run at.
 WORKLOADS = {
     "rmat12": dict(kind="rmat", scale=12, edge_factor=8, eps=0.05, delta=0.1, seed=1),
+    "rmat18": dict(kind="rmat", scale=18, edge_factor=16, eps=0.01, delta=0.1, seed=1),
     "rmat20": dict(kind="rmat", scale=20, edge_factor=16, eps=0.01, delta=0.1, seed=1),
     "grid2048": dict(kind="grid", side=2048, eps=0.01, delta=0.1, seed=1),
     "hyp4m": dict(kind="hyperbolic", n=4 * (1 << 20), eps=0.005, delta=0.1, seed=1),
 }
+
+
+def describe(name: str) -> str:
+    w = WORKLOADS[name]
+    if w["kind"] == "rmat":
+        g = f"R-MAT scale {w['scale']} ef {w['edge_factor']} (a,b,c=.57,.19,.19) undirected LCC"
+    elif w["kind"] == "grid":
+        g = f"{w['side']}x{w['side']} grid, 5% edges removed, 0.1% shortcuts, LCC"
+    else:
+        g = f"threshold hyperbolic n={w['n']} avg deg 20 gamma 2.5, LCC"
+    return f"{g}; eps={w['eps']} delta={w['delta']} seed={w['seed']}"
 
 
 def workload_graph(name: str, graph_seed: int = 1) -> CSR:
