@@ -159,6 +159,43 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
                               uint64_t *sigma_st, int32_t *overflow, int32_t *paths, int32_t cap, uint64_t *work);
 
 /*
+ * kad_sample_records_noalloc -- kad_sample_records for callers that may not
+ * allocate device memory.  The paper has no counterpart to this entry point.
+ *
+ * Some callers own all device memory through their own pool (a framework's
+ * caching allocator, a serving process held to a fixed memory budget) and cannot
+ * let a library call cudaMalloc or cudaFree: those calls can synchronise the
+ * device, stall the caller's other streams, and take memory the pool does not
+ * account for.  This entry point allocates nothing.  The caller passes the graph
+ * and every output as device pointers; the sampling kernel's scratch (labels,
+ * path counts and labelled lists of up to 64 concurrent sampling slots, a
+ * control block, work counters) lives in one fixed 48 MiB device array in the
+ * library, which every GPU that loads the library holds until the process exits.
+ *
+ * Inputs (device): d_row_ptr[n+1], d_col[m], a symmetric sorted CSR as for
+ * kad_graph_create (not validated here); d_comp[n] component labels (any value
+ * equal within a component) or NULL, in which case pairs in different
+ * components are found disconnected by the search itself (same records).
+ * Outputs (device, count entries each): d_s, d_t, d_D, d_sigma_st, d_overflow
+ * (0/1), and d_paths[count * cap] (interior vertices in order of distance from
+ * s, -1 padding), exactly as kad_sample_records.
+ * Limits: n <= 1,600,000 (the scratch holds at least one slot; smaller graphs
+ * get up to 64 slots), count <= 1,048,576 per call; larger values return
+ * KAD_ERR_INVALID_ARG before any device work.  A path longer than cap returns
+ * KAD_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  Every call shares the one array and leaves it as
+ * it was at its end: the call clears what must start at zero, but calls whose
+ * work overlaps on the GPU (different streams or host threads) race on it --
+ * serialise them.  Returns after synchronising `stream`.
+ */
+kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row_ptr, const int32_t *d_col,
+                                      const int32_t *d_comp, uint64_t seed, uint32_t domain, uint64_t i0,
+                                      int64_t count, kad_stream_t stream, int32_t *d_s, int32_t *d_t, int32_t *d_D,
+                                      uint64_t *d_sigma_st, uint8_t *d_overflow, int32_t *d_paths, int32_t cap);
+
+/*
  * kad_eval_fg -- the stop-check kernel's f and g (Appendix B) for n vertices on
  * the device: f[v] = f(counts[v]/tau, exp(-ltab[c0[v]]), omega, tau), same for g.
  * All arrays host; ltab has nclass entries; every c0[v] < nclass.

@@ -45,7 +45,8 @@ class Result(ctypes.Structure):
 
 
 EXPORTS = ("kad_graph_create", "kad_graph_create_device", "kad_graph_free", "kad_graph_info", "kad_options_default",
-           "kad_run", "kad_run_device", "kad_sample_records", "kad_eval_fg", "kad_status_string", "kad_version")
+           "kad_run", "kad_run_device", "kad_sample_records", "kad_sample_records_noalloc", "kad_eval_fg",
+           "kad_status_string", "kad_version")
 
 _lib = None
 
@@ -78,6 +79,9 @@ def load():
     lib.kad_sample_records.argtypes = [vp, u64, u32, u64, i64, vp, ctypes.POINTER(Options), vp, vp, vp, vp, vp, vp,
                                        i32, vp]
     lib.kad_sample_records.restype = st
+    lib.kad_sample_records_noalloc.argtypes = [i32, vp, vp, vp, u64, u32, u64, i64, vp, vp, vp, vp, vp, vp, vp,
+                                               i32]
+    lib.kad_sample_records_noalloc.restype = st
     lib.kad_eval_fg.argtypes = [i32, vp, vp, vp, i32, u64, u64, vp, vp]
     lib.kad_eval_fg.restype = st
     lib.kad_status_string.argtypes = [st]
@@ -248,6 +252,23 @@ def _result_scalars(r):
                                     "kernel_launches")}
     d["counters"] = dict(zip(WORK_NAMES, (int(x) for x in r.work)))
     return d
+
+
+def sample_records_noalloc(d_row_ptr, d_col, seed, i0, count, out, cap, domain=0, d_comp=None, stream=None):
+    """kad_sample_records_noalloc: every array is a caller-owned device tensor.
+
+    `out` holds device tensors s, t, D (int32), sigma_st (int64/uint64),
+    overflow (uint8) with `count` entries and paths (int32, count x cap).
+    The library allocates nothing; its scratch is a fixed device array.
+    """
+    lib = load()
+    n = d_row_ptr.numel() - 1
+    _check(lib.kad_sample_records_noalloc(n, d_row_ptr.data_ptr(), d_col.data_ptr(),
+                                          d_comp.data_ptr() if d_comp is not None else None, seed, domain, i0,
+                                          count, _stream_handle(stream), out["s"].data_ptr(), out["t"].data_ptr(),
+                                          out["D"].data_ptr(), out["sigma_st"].data_ptr(),
+                                          out["overflow"].data_ptr(), out["paths"].data_ptr(), cap),
+           "kad_sample_records_noalloc")
 
 
 def eval_fg(counts, c0, ltab, tau, omega):
