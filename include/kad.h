@@ -85,7 +85,7 @@ typedef struct {
     int32_t slots;       /* concurrent samples = resident sampling blocks (0 = automatic) */
     int32_t mcap;        /* meeting-set size handled by the fast selection path (-1 = default;
                             0 forces the general path; results do not depend on it) */
-    int32_t block_threads; /* threads per sampling block: 128, 256 or 512 (0 = 512) */
+    int32_t block_threads; /* threads per sampling block: 128, 256, 512 or 1024 (0 = 512) */
     uint32_t flags;      /* KAD_RUN_* */
     uint32_t debug;      /* KAD_DEBUG_* (tests only; results do not depend on it) */
 } kad_options;

@@ -32,6 +32,7 @@ struct Workspace {
     uint32_t *label = nullptr;
     unsigned long long *sigma = nullptr, *sigma2 = nullptr;
     int32_t *list = nullptr;
+    uint32_t *bits = nullptr; // labelled-vertex bitmap, nw words per slot
     // epoch ring (or record buffer)
     size_t rows = 0;
     int32_t cap = 0;
@@ -70,9 +71,11 @@ void ws_free_slots(Workspace &w) {
     cudaFree(w.sigma);
     cudaFree(w.sigma2);
     cudaFree(w.list);
+    cudaFree(w.bits);
     w.label = nullptr;
     w.sigma = w.sigma2 = nullptr;
     w.list = nullptr;
+    w.bits = nullptr;
     w.slots = 0;
 }
 
@@ -99,7 +102,10 @@ template <typename T> cudaError_t dalloc(T **p, size_t count) {
 }
 
 // bytes of sampling scratch per slot and vertex: label 4, sigma 8, sigma2 8, list 4
-const size_t kSlotBytesPerVertex = 24;
+// (plus one bit of the labelled-vertex bitmap)
+const size_t kSlotBytesPerVertex = 25;
+
+size_t nwords(int32_t n) { return ((size_t)n + 31) / 32; }
 
 kad_status map_err(cudaError_t e) {
     if (e == cudaSuccess) return KAD_OK;
@@ -125,7 +131,8 @@ kad_status ensure_slots(kad_graph *g, int slots, cudaStream_t st) {
         ws_free_slots(w);
         const size_t cnt = (size_t)slots * n;
         if (dalloc(&w.label, cnt) != cudaSuccess || dalloc(&w.sigma, cnt) != cudaSuccess ||
-            dalloc(&w.sigma2, cnt) != cudaSuccess || dalloc(&w.list, cnt) != cudaSuccess) {
+            dalloc(&w.sigma2, cnt) != cudaSuccess || dalloc(&w.list, cnt) != cudaSuccess ||
+            dalloc(&w.bits, (size_t)slots * nwords(g->gd.n)) != cudaSuccess) {
             cudaGetLastError();
             ws_free_slots(w);
             return KAD_ERR_OOM;
@@ -137,6 +144,7 @@ kad_status ensure_slots(kad_graph *g, int slots, cudaStream_t st) {
     if ((e = cudaMemsetAsync(w.label, 0, cnt * 4, st)) != cudaSuccess) return fail(g, e);
     if ((e = cudaMemsetAsync(w.sigma, 0, cnt * 8, st)) != cudaSuccess) return fail(g, e);
     if ((e = cudaMemsetAsync(w.sigma2, 0, cnt * 8, st)) != cudaSuccess) return fail(g, e);
+    if ((e = cudaMemsetAsync(w.bits, 0, (size_t)w.slots * nwords(g->gd.n) * 4, st)) != cudaSuccess) return fail(g, e);
     w.dirty = false;
     return KAD_OK;
 }
@@ -294,7 +302,7 @@ int device_sms(int dev) {
 }
 
 int resolve_threads(const kad_options &o) {
-    return (o.block_threads == 128 || o.block_threads == 256) ? o.block_threads : 512;
+    return (o.block_threads == 128 || o.block_threads == 256 || o.block_threads == 1024) ? o.block_threads : 512;
 }
 
 // Number of sampling slots: all resident blocks, capped by a share of free memory.
@@ -349,6 +357,8 @@ SampleArgs base_args(kad_graph *g, uint64_t seed) {
     a.sigma = g->ws.sigma;
     a.sigma2 = g->ws.sigma2;
     a.list = g->ws.list;
+    a.bits = g->ws.bits;
+    a.nw = (int32_t)nwords(g->gd.n);
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
     a.ctl = g->ws.ctl;

@@ -58,6 +58,10 @@ struct SampleArgs {
     int32_t n;
     // per-slot scratch, slot-major: slot k uses [k*n, (k+1)*n)
     uint32_t *label;
+    // per-slot bitmap of labelled vertices, slot k uses words [k*nw, (k+1)*nw);
+    // small enough to stay in L2, it spares most label reads
+    uint32_t *bits;
+    int32_t nw;
     unsigned long long *sigma;
     unsigned long long *sigma2;
     int32_t *list;

@@ -44,10 +44,13 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Bytes the slot area needs for n vertices and `slots` sampling slots: a zero
 // component array (used when the caller passes none), then label (4 B), sigma
-// (8 B), sigma2 (8 B) and list (4 B) per vertex and slot.
+// (8 B), sigma2 (8 B) and list (4 B) per vertex and slot, and a bitmap of
+// labelled vertices (1 bit per vertex and slot).
+size_t nwords(int64_t n) { return ((size_t)n + 31) / 32; }
+
 size_t slot_area_bytes(int64_t n, int64_t slots) {
     return align256((size_t)n * 4) + align256((size_t)(slots * n) * 4) + 2 * align256((size_t)(slots * n) * 8) +
-           align256((size_t)(slots * n) * 4);
+           align256((size_t)(slots * n) * 4) + align256((size_t)slots * nwords(n) * 4);
 }
 
 kad_status scratch_for_device(int dev, unsigned char **out) {
@@ -124,6 +127,9 @@ extern "C" kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row
     unsigned long long *sigma2 = (unsigned long long *)p;
     p += align256(sn * 8);
     int32_t *list = (int32_t *)p;
+    p += align256(sn * 4);
+    uint32_t *bits = (uint32_t *)p;
+    const size_t bw = (size_t)slots * nwords(n);
 
     // The array keeps the previous call's contents.  Labels and path counts must
     // start at zero (the kernel restores zeros after every sample it finishes,
@@ -135,6 +141,7 @@ extern "C" kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row
     if (e == cudaSuccess) e = cudaMemsetAsync(label, 0, sn * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sigma, 0, sn * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sigma2, 0, sn * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bits, 0, bw * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_paths, 0xff, (size_t)count * (size_t)cap * 4, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -152,6 +159,8 @@ extern "C" kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row
     a.sigma = sigma;
     a.sigma2 = sigma2;
     a.list = list;
+    a.bits = bits;
+    a.nw = (int32_t)nwords(n);
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
     a.domain = domain;

@@ -226,7 +226,7 @@ __device__ __forceinline__ void emit(const SampleArgs &a, int32_t *row, int D, i
 // distance labels).  Called by one warp; every lane returns the same choice.
 
 // Scan adj(cur) 4 x 32 arcs per pass (all loads of a pass issued first).
-__device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *label,
+__device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *label, const uint32_t *bits,
                                            const unsigned long long *sigma, int z, int d, int rsC, int reC,
                                            unsigned long long r, int &p_sel, unsigned long long &s_sel,
                                            unsigned long long &w_trace) {
@@ -242,7 +242,10 @@ __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *
             pp[k] = (e < reC) ? __ldg(a.col + e) : -1;
         }
 #pragma unroll
-        for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? kad_ld_u32(label + pp[k]) : 0u;
+        for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? __ldcg(bits + (pp[k] >> 5)) : 0u;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            lp[k] = (pp[k] >= 0 && ((lp[k] >> (pp[k] & 31)) & 1u)) ? kad_ld_u32(label + pp[k]) : 0u;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             unsigned long long wgt = 0;
@@ -447,6 +450,7 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
     unsigned long long *const sigma = a.sigma + soff;
     unsigned long long *const sigma2 = a.sigma2 + soff;
     int32_t *const list = a.list + soff;
+    uint32_t *const bits = a.bits + (size_t)blockIdx.x * (size_t)a.nw;
     const int mcap = (a.mcap < KAD_MCAP_MAX) ? a.mcap : KAD_MCAP_MAX;
 
     // work counters (thread 0 except pred, which every thread counts)
@@ -481,6 +485,8 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
             if (__ldg(a.comp + s) == __ldg(a.comp + t)) {
                 label[s] = 1u;            // s side, level 0
                 label[t] = KAD_SIDE | 1u; // t side, level 0
+                atomicOr(bits + (s >> 5), 1u << (s & 31));
+                atomicOr(bits + (t >> 5), 1u << (t & 31));
                 sigma[s] = 1ull;
                 sigma[t] = 1ull;
                 list[0] = s;
@@ -568,7 +574,11 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
                         }
                     }
 #pragma unroll
-                    for (int k = 0; k < KAD_ITEMS; k++) ll[k] = (vv[k] >= 0) ? kad_ld_u32(label + vv[k]) : 0u;
+                    for (int k = 0; k < KAD_ITEMS; k++) ll[k] = (vv[k] >= 0) ? __ldcg(bits + (vv[k] >> 5)) : 0u;
+                    // only vertices whose bit is set carry a label worth reading
+#pragma unroll
+                    for (int k = 0; k < KAD_ITEMS; k++)
+                        ll[k] = (vv[k] >= 0 && ((ll[k] >> (vv[k] & 31)) & 1u)) ? kad_ld_u32(label + vv[k]) : 0u;
 #pragma unroll
                     for (int k = 0; k < KAD_ITEMS; k++) {
                         const int v = vv[k];
@@ -581,6 +591,7 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
                                 const uint32_t old = atomicCAS(label + v, 0u, keyNext);
                                 if (old == 0u) {
                                     claimed = true;
+                                    atomicOr(bits + (v >> 5), 1u << (v & 31));
                                     lv = keyNext;
                                 } else {
                                     lv = old;
@@ -782,7 +793,7 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
                             trace_from_level<BLOCK>(a, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel,
                                                     s_sel, w_trace);
                         } else {
-                            trace_scan(a, label, sigma, z, d, rsC, reC, r, p_sel, s_sel, w_trace);
+                            trace_scan(a, label, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, w_trace);
                         }
                         if (p_sel < 0) {
                             if (lane == 0) kad_set_err(a.ctl, KAD_DERR_TRACE);
@@ -822,6 +833,7 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
                 const uint32_t lv = kad_ld_u32(label + v);
                 label[v] = 0u;
                 sigma[v] = 0ull;
+                bits[v >> 5] = 0u; // every set bit of this word belongs to a listed vertex
                 if (lv & KAD_INM) sigma2[v] = 0ull;
             }
         }
@@ -907,6 +919,9 @@ cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, cuda
     case 512:
         k_sample<512><<<blocks, 512, 0, st>>>(a);
         break;
+    case 1024:
+        k_sample<1024><<<blocks, 1024, 0, st>>>(a);
+        break;
     default:
         k_sample<256><<<blocks, 256, 0, st>>>(a);
         break;
@@ -923,6 +938,9 @@ int kad_sample_max_blocks_per_sm(int threads) {
         break;
     case 512:
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<512>, 512, 0);
+        break;
+    case 1024:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<1024>, 1024, 0);
         break;
     default:
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<256>, 256, 0);
