@@ -51,6 +51,24 @@ def alg_bytes(counters):
     return sum(BYTES_PER[k] * int(v) for k, v in counters.items())
 
 
+def phase_total(results):
+    tot = {}
+    for r in results:
+        for k, v in r.get("phase_cycles", {}).items():
+            tot[k] = tot.get(k, 0) + v
+    return tot
+
+
+def phase_share(results):
+    """Share of the sampling blocks' cycles per stage of a sample (adaptive phase)."""
+    tot = {}
+    for r in results:
+        for k, v in r.get("phase_cycles", {}).items():
+            tot[k] = tot.get(k, 0) + v
+    s = sum(tot.values()) or 1
+    return {k: round(v / s, 4) for k, v in tot.items()}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -194,6 +212,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--slots", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
+    ap.add_argument("--eps", type=float, default=None, help="override the workload's eps (experiments)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -214,7 +235,10 @@ def main():
     from paper_1903_09422_gb300 import gen
     g, w = graph_for(args.workload)
     eps, delta, seed = w["eps"], w["delta"], w["seed"]
-    opts = dict(block_threads=args.block_threads or None, slots=args.slots or None)
+    if args.eps:
+        eps = args.eps
+    opts = dict(block_threads=args.block_threads or None, slots=args.slots or None,
+                blocks_per_sm=args.blocks_per_sm or None)
     stream = torch.cuda.current_stream()
 
     # inputs resident in HBM before timing
@@ -225,7 +249,7 @@ def main():
     torch.cuda.synchronize()
     setup_ms = 1000 * (time.perf_counter() - t0)
     d_bc = torch.empty(g.n, dtype=torch.float64, device=dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
 
     for _ in range(args.warmup):
         G.run_device(eps, delta, seed, d_bc=d_bc, timing=True, **opts)
@@ -257,7 +281,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     samples = sum(r["tau"] + r["calib_samples"] for r in results)
-    computed = sum(r["samples_computed"] + r["calib_samples"] for r in results)
+    computed = sum(r["samples_computed"] for r in results)  # calibration + adaptive
     if dist:
         t = torch.tensor([total_ms, float(samples), float(computed)], dtype=torch.float64, device=dev)
         mx = t.clone()
@@ -325,7 +349,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {gen.describe(args.workload)}; n={g.n} arcs={g.m}",
                        "step": "one full KADABRA query (calibration + adaptive sampling to stop + b~)",
-                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+                       "l2": f"flushed between steps ({args.flush_mb} MB write)", "parallelism": f"replicas x{world}"},
             "time_to_stop_ms": statistics.median(step_ms),
             "time_to_stop_ads_ms": statistics.median(r["t_ads_ms"] for r in results),
             "samples_computed_per_s": computed_all / (total_ms_all / 1000.0),
@@ -341,6 +365,9 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.m),
                     "d2h_bytes_per_step": int(8 * g.n), "steps": args.e2e_steps,
                     "ms_per_step": 1000 * statistics.mean(e2e_times)},
+            "phase_share": phase_share(results),
+            "phase_cycles_per_sample": {k: round(v / max(1, sum(r["samples_computed"] for r in results)))
+                                        for k, v in phase_total(results).items()},
             "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
             "clocks": clk,
             "cpu_baseline": cpu,

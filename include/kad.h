@@ -86,6 +86,8 @@ typedef struct {
     int32_t mcap;        /* meeting-set size handled by the fast selection path (-1 = default;
                             0 forces the general path; results do not depend on it) */
     int32_t block_threads; /* threads per sampling block: 128, 256, 512 or 1024 (0 = 512) */
+    int32_t blocks_per_sm; /* resident sampling blocks per SM the kernel is built for: 128 threads 4|8,
+                              256: 2|4, 512: 1|2, 1024: 1 (0 = the first of these) */
     uint32_t flags;      /* KAD_RUN_* */
     uint32_t debug;      /* KAD_DEBUG_* (tests only; results do not depend on it) */
 } kad_options;
@@ -107,23 +109,31 @@ typedef struct {
     uint64_t tau;              /* samples used (= epochs * N) */
     uint64_t omega;            /* maximal number of samples (Section 2.3) */
     uint64_t calib_samples;    /* tau0 */
-    uint64_t samples_computed; /* adaptive-phase samples computed, including speculative ones */
+    uint64_t samples_computed; /* samples computed: calibration + adaptive, including speculative ones */
     uint64_t overflow_samples; /* used samples whose shortest-path count saturated at 2^64-1 */
     uint32_t epochs;           /* stop-check epochs used */
     int32_t vd_bound;
     int32_t sigma_overflow;    /* 1 if any used sample saturated */
     int32_t stopped_by_omega;  /* 1 if the run stopped because tau >= omega */
     double tau_star;           /* calibration's bisection result */
-    /* work of the adaptive phase (all samples computed): frontier vertices expanded,
-       arcs scanned, vertices labelled, arcs into the next level or meeting set,
-       arcs scanned by the trace-back, path increments */
+    /* work of all samples computed (calibration and adaptive): frontier vertices
+       expanded, arcs scanned, vertices labelled, arcs into the next level or
+       meeting set, arcs read by the trace-back, path increments */
     uint64_t work[6];
-    /* KAD_RUN_TIMING: milliseconds, CUDA events on the run's stream */
+    /* KAD_RUN_TIMING, milliseconds: t_total (CUDA events around the whole call's
+       device work), t_calib (host wall time from the first launch until the
+       calibration histogram arrived; sampling continues meanwhile), t_ads (events
+       from the first sampling launch to the end), t_ads_kernel (events around the
+       first sampling launch, which runs calibration and adaptive samples) */
     double t_total_ms, t_calib_ms, t_ads_ms, t_ads_kernel_ms;
-    uint32_t ads_launches;     /* adaptive-phase sampling-kernel launches */
+    uint32_t ads_launches;     /* sampling-kernel launches */
     int32_t slots_used;        /* concurrent samples (resident sampling blocks) */
     uint32_t kernel_launches;  /* kernels this call launched (all phases) */
     uint32_t reserved_;
+    /* SM cycles the sampling blocks spent per stage of a sample, summed over
+       blocks and samples: pair draw and set-up, BFS, meeting draw, trace-back
+       and output, slot reset, epoch bookkeeping and close */
+    uint64_t phase_cycles[6];
 } kad_result;
 
 /*

@@ -16,6 +16,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 #include <new>
 
@@ -50,8 +51,17 @@ struct Workspace {
     KadCtl *ctl = nullptr;
     uint32_t *epoch_done = nullptr;
     size_t ring_cap = 0;
-    unsigned long long *work = nullptr; // [8]
+    unsigned long long *work = nullptr; // [KAD_WORK_WORDS]
     bool dirty = false;                 // scratch must be re-zeroed
+    // calibration hand-off: mapped pinned page (histogram + flag), pinned L table
+    // and class presence for the upload, a side stream and two events
+    KadHostPage *hpage = nullptr;
+    KadHostPage *dpage = nullptr; // device-visible address of hpage
+    size_t hpage_cap = 0;         // nclass the page and buffers hold
+    double *h_ltab = nullptr;
+    int32_t *h_cmax = nullptr;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_launch = nullptr, ev_aux = nullptr;
 };
 
 } // namespace
@@ -92,6 +102,12 @@ void ws_free_all(Workspace &w) {
     cudaFree(w.ctl);
     cudaFree(w.epoch_done);
     cudaFree(w.work);
+    if (w.hpage) cudaFreeHost(w.hpage);
+    if (w.h_ltab) cudaFreeHost(w.h_ltab);
+    if (w.h_cmax) cudaFreeHost(w.h_cmax);
+    if (w.aux) cudaStreamDestroy(w.aux);
+    if (w.ev_launch) cudaEventDestroy(w.ev_launch);
+    if (w.ev_aux) cudaEventDestroy(w.ev_aux);
     w = Workspace();
 }
 
@@ -180,7 +196,7 @@ kad_status ensure_fixed(kad_graph *g, size_t nclass, size_t ring) {
     const size_t n = (size_t)g->gd.n;
     if (!w.cnt) {
         if (dalloc(&w.cnt, n) != cudaSuccess || dalloc(&w.c0, n) != cudaSuccess || dalloc(&w.ctl, 1) != cudaSuccess ||
-            dalloc(&w.work, 8) != cudaSuccess) {
+            dalloc(&w.work, KAD_WORK_WORDS) != cudaSuccess) {
             cudaGetLastError();
             return KAD_ERR_OOM;
         }
@@ -199,6 +215,33 @@ kad_status ensure_fixed(kad_graph *g, size_t nclass, size_t ring) {
             return KAD_ERR_OOM;
         }
         w.nclass_cap = nclass;
+    }
+    if (!w.aux) {
+        if (cudaStreamCreateWithFlags(&w.aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&w.ev_launch, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&w.ev_aux, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return KAD_ERR_CUDA;
+        }
+    }
+    if (w.hpage_cap < nclass) {
+        if (w.hpage) cudaFreeHost(w.hpage);
+        if (w.h_ltab) cudaFreeHost(w.h_ltab);
+        if (w.h_cmax) cudaFreeHost(w.h_cmax);
+        w.hpage = w.dpage = nullptr;
+        w.h_ltab = nullptr;
+        w.h_cmax = nullptr;
+        w.hpage_cap = 0;
+        void *dp = nullptr;
+        if (cudaHostAlloc((void **)&w.hpage, sizeof(KadHostPage) + nclass * 4, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(&dp, w.hpage, 0) != cudaSuccess ||
+            cudaHostAlloc((void **)&w.h_ltab, nclass * 8, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc((void **)&w.h_cmax, nclass * 4, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return KAD_ERR_OOM;
+        }
+        w.dpage = (KadHostPage *)dp;
+        w.hpage_cap = nclass;
     }
     if (w.ring_cap < ring) {
         cudaFree(w.epoch_done);
@@ -301,15 +344,26 @@ int device_sms(int dev) {
     return sms > 0 ? sms : 1;
 }
 
-int resolve_threads(const kad_options &o) {
-    return (o.block_threads == 128 || o.block_threads == 256 || o.block_threads == 1024) ? o.block_threads : 512;
+struct LaunchCfg {
+    int threads;
+    int per_sm; // resident blocks per SM the kernel variant is compiled for
+};
+
+// Threads per block and blocks per SM.  Unknown combinations fall back to the
+// variant with the same block size and the default occupancy.
+LaunchCfg resolve_cfg(const kad_options &o) {
+    LaunchCfg c;
+    c.threads = (o.block_threads == 128 || o.block_threads == 256 || o.block_threads == 1024) ? o.block_threads : 512;
+    const int def = (c.threads == 128) ? 4 : (c.threads == 256) ? 2 : 1;
+    c.per_sm = (o.blocks_per_sm > 0 && kad_sample_variant_exists(c.threads, o.blocks_per_sm)) ? o.blocks_per_sm : def;
+    return c;
 }
 
 // Number of sampling slots: all resident blocks, capped by a share of free memory.
-int resolve_slots(kad_graph *g, const kad_options &o, int threads) {
+int resolve_slots(kad_graph *g, const kad_options &o, const LaunchCfg &cfg) {
     int slots = o.slots;
     if (slots <= 0) {
-        const int per_sm = kad_sample_max_blocks_per_sm(threads);
+        const int per_sm = kad_sample_max_blocks_per_sm(cfg.threads, cfg.per_sm);
         slots = device_sms(g->device) * (per_sm > 0 ? per_sm : 1);
     }
     size_t fr = 0, tot = 0;
@@ -332,16 +386,31 @@ void fill_defaults(kad_options *o) {
     o->slots = 0;
     o->mcap = -1;
     o->block_threads = 0;
+    o->blocks_per_sm = 0;
     o->flags = 0;
 }
 
 __global__ void k_set_ctl(KadCtl *c, unsigned long long next) { c->next = next; }
 
-kad_status launch_phase(kad_graph *g, const SampleArgs &a, int blocks, int threads, cudaStream_t st) {
-    k_set_ctl<<<1, 1, 0, st>>>(a.ctl, a.i0);
+__global__ void k_hist_init(uint32_t *hist, uint32_t n) {
+    if (threadIdx.x == 0) hist[0] = n;
+}
+
+const double kCalibWaitMs = 600000.0; // a run's calibration never takes this long
+
+double now_ms() {
+    struct timespec t;
+    clock_gettime(CLOCK_MONOTONIC, &t);
+    return (double)t.tv_sec * 1e3 + (double)t.tv_nsec * 1e-6;
+}
+
+kad_status launch_phase(kad_graph *g, const SampleArgs &a, int blocks, const LaunchCfg &cfg,
+                        unsigned long long next0, cudaStream_t st) {
+    k_set_ctl<<<1, 1, 0, st>>>(a.ctl, next0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(g, e);
-    e = kad_launch_sample(a, blocks, threads, st);
+    e = kad_launch_sample(a, blocks, cfg.threads, cfg.per_sm, st);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ws.ev_launch, st);
     if (e != cudaSuccess) return fail(g, e);
     return KAD_OK;
 }
@@ -400,8 +469,8 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     const uint64_t max_epochs = (omega + N - 1) / N; // the stop rule holds at tau >= omega
     const size_t nclass = (size_t)tau0 + 1;
     if (nclass > (size_t)0x7fffffff || omega > ((uint64_t)1 << 40)) return KAD_ERR_INVALID_ARG;
-    const int threads = resolve_threads(o);
-    const int slots = resolve_slots(g, o, threads);
+    const LaunchCfg cfg = resolve_cfg(o);
+    const int slots = resolve_slots(g, o, cfg);
     const int32_t cap = path_cap(g);
     // Epoch ring: enough to hold the whole run when it fits in about 1 GiB of
     // path rows, else as many epochs as fit (at least 2).
@@ -423,62 +492,29 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     cudaError_t e;
     ev.record(0, st);
 
-    // ---- calibration (phase 1 of the stream): c0[v] = path counts of tau0 samples
+    // ---- one launch: calibration samples (phase 1), then adaptive samples (phase 0)
     if ((e = cudaMemsetAsync(w.c0, 0, (size_t)n * 4, st)) != cudaSuccess) return fail(g, e);
+    if ((e = cudaMemsetAsync(w.cnt, 0, (size_t)n * 4, st)) != cudaSuccess) return fail(g, e);
+    if ((e = cudaMemsetAsync(w.hist, 0, nclass * 4, st)) != cudaSuccess) return fail(g, e);
     if ((e = cudaMemsetAsync(w.ctl, 0, sizeof(KadCtl), st)) != cudaSuccess) return fail(g, e);
-    if ((e = cudaMemsetAsync(w.work, 0, 8 * sizeof(unsigned long long), st)) != cudaSuccess) return fail(g, e);
+    if ((e = cudaMemsetAsync(w.epoch_done, 0, ring * 4, st)) != cudaSuccess) return fail(g, e);
+    if ((e = cudaMemsetAsync(w.work, 0, KAD_WORK_WORDS * sizeof(unsigned long long), st)) != cudaSuccess)
+        return fail(g, e);
+    k_hist_init<<<1, 32, 0, st>>>(w.hist, (uint32_t)n); // every vertex starts with count 0
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(g, e);
+    *(volatile int *)&w.hpage->calib_flag = 0;
+    w.hpage->one = 1;
+
     SampleArgs a = base_args(g, seed);
     a.mcap = (o.mcap < 0) ? kDefaultMcap : o.mcap;
     a.debug = o.debug;
-    a.domain = 1;
-    a.i0 = 0;
-    a.i1 = tau0;
-    a.mode = KAD_MODE_DIRECT;
-    a.dcount = w.c0;
+    a.mode = KAD_MODE_RING;
+    a.calib_n = tau0;
+    a.c0w = w.c0;
+    a.hist = w.hist;
+    a.hpage = w.dpage;
     a.epoch = N;
     a.ring = (uint32_t)ring;
-    if ((s = launch_phase(g, a, slots, threads, st)) != KAD_OK) return s;
-    if ((e = cudaMemsetAsync(w.hist, 0, nclass * 4, st)) != cudaSuccess) return fail(g, e);
-    if ((e = kad_launch_hist(w.c0, n, w.hist, (int32_t)nclass, st)) != cudaSuccess) return fail(g, e);
-    uint32_t *hist = (uint32_t *)malloc(nclass * 4);
-    double *ltab = (double *)malloc(nclass * 8);
-    int32_t *cmax = (int32_t *)malloc(nclass * 4);
-    if (!hist || !ltab || !cmax) {
-        free(hist);
-        free(ltab);
-        free(cmax);
-        return KAD_ERR_OOM;
-    }
-    KadCtl hc;
-    if ((e = cudaMemcpyAsync(hist, w.hist, nclass * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (s = read_ctl(g, &hc, st)) != KAD_OK) {
-        free(hist);
-        free(ltab);
-        free(cmax);
-        return (e != cudaSuccess) ? fail(g, e) : s;
-    }
-    // ---- host: tau* by bisection, L table, class presence
-    const double ts = run_tau_star(hist, tau0, eps, delta, omega);
-    for (size_t c = 0; c < nclass; c++) {
-        ltab[c] = run_L((double)c / (double)tau0, ts, eps, omega);
-        cmax[c] = hist[c] ? 0 : -1;
-    }
-    e = cudaMemcpyAsync(w.ltab, ltab, nclass * 8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(w.classmax, cmax, nclass * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st); // host buffers are freed next
-    free(hist);
-    free(ltab);
-    free(cmax);
-    if (e != cudaSuccess) return fail(g, e);
-    ev.record(1, st);
-
-    // ---- adaptive sampling
-    if ((e = cudaMemsetAsync(w.cnt, 0, (size_t)n * 4, st)) != cudaSuccess) return fail(g, e);
-    if ((e = cudaMemsetAsync(w.ctl, 0, sizeof(KadCtl), st)) != cudaSuccess) return fail(g, e);
-    if ((e = cudaMemsetAsync(w.epoch_done, 0, ring * 4, st)) != cudaSuccess) return fail(g, e);
-    a.domain = 0;
-    a.mode = KAD_MODE_RING;
-    a.dcount = nullptr;
     a.paths = w.paths;
     a.cap = cap;
     a.plen = w.plen;
@@ -491,28 +527,71 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     a.nclass = (int32_t)nclass;
     a.eps = eps;
     a.omega = omega;
-    uint64_t closed = 0;
-    uint32_t launches = 0;
+    a.i0 = 0;
+    a.i1 = (uint64_t)((ring < max_epochs) ? ring : max_epochs) * N;
+    a.k_end = a.i1 / N;
+    ev.record(2, st);
+    if ((s = launch_phase(g, a, slots, cfg, 0, st)) != KAD_OK) return s;
+    ev.record(3, st);
+    uint32_t launches = 1;
+    uint64_t issued = a.i1; // adaptive samples handed to launches so far
+
+    // ---- host: wait for the calibration histogram (the kernel keeps sampling),
+    // then tau* by bisection, the L table and class presence, uploaded on a side
+    // stream; the kernel's closer starts once ltab_ready is set.
+    const double t_wait0 = now_ms();
     for (;;) {
-        const uint64_t k_end = (closed + ring < max_epochs) ? closed + ring : max_epochs;
-        a.i0 = closed * N;
-        a.i1 = k_end * N;
-        a.k_end = k_end;
-        if (launches == 0) ev.record(2, st);
-        if ((s = launch_phase(g, a, slots, threads, st)) != KAD_OK) return s;
-        launches++;
-        if (launches == 1) ev.record(3, st);
+        if (*(volatile int *)&w.hpage->calib_flag) break;
+        const cudaError_t q = cudaEventQuery(w.ev_launch);
+        if (q == cudaSuccess) { // the launch ended; the flag must be set by now
+            if (*(volatile int *)&w.hpage->calib_flag) break;
+            KadCtl hc0;
+            kad_status s0 = read_ctl(g, &hc0, st);
+            g->ws.dirty = true;
+            return (s0 != KAD_OK) ? s0 : KAD_ERR_INTERNAL;
+        }
+        if (q != cudaErrorNotReady) return fail(g, q);
+        if (now_ms() - t_wait0 > kCalibWaitMs) {
+            cudaStreamSynchronize(st);
+            g->ws.dirty = true;
+            return KAD_ERR_TIMEOUT;
+        }
+    }
+    __sync_synchronize();
+    const double t_calib = now_ms() - t_wait0;
+    const double ts = run_tau_star(w.hpage->hist, tau0, eps, delta, omega);
+    for (size_t c = 0; c < nclass; c++) {
+        w.h_ltab[c] = run_L((double)c / (double)tau0, ts, eps, omega);
+        w.h_cmax[c] = w.hpage->hist[c] ? 0 : -1;
+    }
+    e = cudaMemcpyAsync(w.ltab, w.h_ltab, nclass * 8, cudaMemcpyHostToDevice, w.aux);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.classmax, w.h_cmax, nclass * 4, cudaMemcpyHostToDevice, w.aux);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&w.ctl->ltab_ready, &w.hpage->one, sizeof(int), cudaMemcpyHostToDevice, w.aux);
+    if (e == cudaSuccess) e = cudaEventRecord(w.ev_aux, w.aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, w.ev_aux, 0); // later launches see the table
+    if (e != cudaSuccess) return fail(g, e);
+
+    // ---- further launches only if the ring filled up (or the table arrived
+    // after the last sample): each continues the index space and first closes
+    // what is pending
+    KadCtl hc;
+    for (;;) {
         if ((s = read_ctl(g, &hc, st)) != KAD_OK) return s;
         if (hc.stop) break;
-        if (hc.closed != k_end) { // every epoch of the window must have been closed
-            g->ws.dirty = true;
-            return KAD_ERR_INTERNAL;
-        }
-        closed = hc.closed;
-        if (closed >= max_epochs) return KAD_ERR_INTERNAL; // unreachable: tau >= omega stops
+        if (launches > 4 * max_epochs + 8) return KAD_ERR_INTERNAL; // cannot happen: tau >= omega stops
+        const uint64_t closed = hc.closed;
+        uint64_t i1 = (closed + ring < max_epochs ? closed + ring : max_epochs) * N;
+        if (i1 < issued) i1 = issued;
+        a.calib_n = 0;
+        a.i0 = issued;
+        a.i1 = i1;
+        a.k_end = i1 / N;
+        if ((s = launch_phase(g, a, slots, cfg, 0, st)) != KAD_OK) return s;
+        launches++;
+        issued = i1;
     }
     const uint64_t tau = hc.tau;
-    unsigned long long work[8];
+    unsigned long long work[KAD_WORK_WORDS];
     if ((e = cudaMemcpyAsync(work, w.work, sizeof(work), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(g, e);
 
     // ---- outputs
@@ -553,14 +632,15 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     out->stopped_by_omega = hc.stopped_by_omega;
     out->tau_star = ts;
     for (int i = 0; i < 6; i++) out->work[i] = work[i];
+    for (int i = 0; i < 6; i++) out->phase_cycles[i] = work[8 + i];
     out->ads_launches = launches;
     out->slots_used = slots;
-    // per phase launch: k_set_ctl + k_sample; plus k_hist, and k_finalize if bc was wanted
-    out->kernel_launches = 2u * (1u + launches) + 1u + (bc_dst ? 1u : 0u);
+    // k_hist_init, then k_set_ctl + k_sample per launch, and k_finalize if b~ was wanted
+    out->kernel_launches = 1u + 2u * launches + (bc_dst ? 1u : 0u);
     if (ev.on) {
         out->t_total_ms = ev.ms(0, 4);
-        out->t_calib_ms = ev.ms(0, 1);
-        out->t_ads_ms = ev.ms(1, 4);
+        out->t_calib_ms = t_calib; // host wall time from launch to the histogram (sampling continues meanwhile)
+        out->t_ads_ms = ev.ms(2, 4);
         out->t_ads_kernel_ms = ev.ms(2, 3);
     }
     return KAD_OK;
@@ -679,8 +759,8 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
         o = *opt;
     else
         fill_defaults(&o);
-    const int threads = resolve_threads(o);
-    int slots = resolve_slots(g, o, threads);
+    const LaunchCfg cfg = resolve_cfg(o);
+    int slots = resolve_slots(g, o, cfg);
     if ((int64_t)slots > count) slots = (int)count;
     kad_status s;
     if ((s = ensure_fixed(g, 1, 2)) != KAD_OK) return s;
@@ -718,13 +798,13 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
         a.ring = 1;
         if ((e = cudaMemsetAsync(d_paths, 0xff, c * (size_t)cap * 4, st)) != cudaSuccess ||
             (e = cudaMemsetAsync(w.ctl, 0, sizeof(KadCtl), st)) != cudaSuccess ||
-            (e = cudaMemsetAsync(w.work, 0, 8 * 8, st)) != cudaSuccess) {
+            (e = cudaMemsetAsync(w.work, 0, KAD_WORK_WORDS * 8, st)) != cudaSuccess) {
             s = fail(g, e);
             goto out;
         }
-        if ((s = launch_phase(g, a, slots, threads, st)) != KAD_OK) goto out;
+        if ((s = launch_phase(g, a, slots, cfg, i0, st)) != KAD_OK) goto out;
         uint8_t *hflag = (uint8_t *)malloc(c);
-        unsigned long long hw[8];
+        unsigned long long hw[KAD_WORK_WORDS];
         if (!hflag) {
             s = KAD_ERR_OOM;
             goto out;

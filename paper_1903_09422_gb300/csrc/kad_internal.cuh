@@ -23,10 +23,12 @@
 #define KAD_MAX_LEVEL (KAD_LVL - 2)
 
 #define KAD_U64MAX 0xffffffffffffffffull
+#define KAD_WORK_WORDS 16
 
 // sample-kernel output modes
-#define KAD_MODE_DIRECT 0 // increments go straight into a count array (calibration)
-#define KAD_MODE_RING 1   // paths into the epoch ring; the closer folds epochs in order
+#define KAD_MODE_RING 1   // a KADABRA run: calibration samples first (counted into c0 and
+                          // its histogram), then adaptive samples whose paths go into the
+                          // epoch ring, folded and checked in order by the closer
 #define KAD_MODE_RECORD 2 // full per-sample records (parity tests)
 
 // device error codes (KadCtl.err)
@@ -44,10 +46,20 @@ struct KadCtl {
     unsigned long long tau;      // samples used when stopped
     unsigned long long overflow; // overflowed samples among the folded epochs
     unsigned long long computed; // samples computed (all launches)
+    unsigned long long calib_done; // calibration samples finished
     int stop;                    // 1 once the stop rule held
     int closer;                  // closer role taken (0/1)
     int err;                     // KAD_DERR_*, first error wins
     int stopped_by_omega;
+    int ltab_ready;              // 1 once the host has uploaded the L table and class presence
+};
+
+// Host-mapped page of a run (pinned host memory the kernel writes through).
+struct KadHostPage {
+    int calib_flag;  // set to 1 by the kernel once the histogram below is final
+    int one;         // constant 1, copied into KadCtl.ltab_ready by the host
+    int pad[2];
+    uint32_t hist[1]; // nclass entries: hist[c] = |{v : c0[v] = c}|
 };
 
 // Arguments of the sampling kernel.
@@ -67,7 +79,10 @@ struct SampleArgs {
     int32_t *list;
     // random stream
     uint32_t key0, key1, domain;
-    // sample index range of this launch
+    // index space of this launch: [0, calib_n) are calibration samples 0..calib_n-1
+    // (phase 1), then adaptive samples i0..i1-1 (phase 0); RECORD mode: [i0, i1)
+    // of phase `domain`
+    unsigned long long calib_n;
     unsigned long long i0, i1;
     int mode;
     int mcap;
@@ -79,8 +94,10 @@ struct SampleArgs {
     uint8_t *pflag;
     uint32_t epoch; // N
     uint32_t ring;  // R
-    // DIRECT
-    uint32_t *dcount;
+    // calibration (RING): counts, their histogram, and where to publish it
+    uint32_t *c0w;
+    uint32_t *hist;
+    KadHostPage *hpage; // device-visible pointer to the mapped host page
     // RECORD extras
     int32_t *rec_s, *rec_t, *rec_D;
     unsigned long long *rec_sst;
@@ -88,14 +105,14 @@ struct SampleArgs {
     KadCtl *ctl;
     uint32_t *epoch_done; // [R]
     uint32_t *cnt;        // [n]
-    const uint32_t *c0;   // [n]
+    const uint32_t *c0;   // [n] (written by this launch's calibration samples: read through L2)
     int32_t *classmax;    // [nclass]
     const double *ltab;   // [nclass]
     int32_t nclass;
     double eps;
     unsigned long long omega;
     unsigned long long k_end; // epochs of this launch end before k_end
-    // work counters [6] + samples [1]
+    // work counters [0..5], samples [6], SM cycles per phase [8..13] (KAD_WORK_WORDS)
     unsigned long long *work;
 };
 
@@ -134,9 +151,9 @@ __device__ __forceinline__ double kad_fg_dev(unsigned long long c, double L, uns
 }
 
 // Host-side launchers (defined in the .cu files).
-cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, cudaStream_t st);
-int kad_sample_max_blocks_per_sm(int threads);
-cudaError_t kad_launch_hist(const uint32_t *c0, int32_t n, uint32_t *hist, int32_t nclass, cudaStream_t st);
+cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, int per_sm, cudaStream_t st);
+bool kad_sample_variant_exists(int threads, int per_sm);
+int kad_sample_max_blocks_per_sm(int threads, int per_sm);
 cudaError_t kad_launch_finalize(const uint32_t *cnt, int32_t n, unsigned long long tau, double *bc, cudaStream_t st);
 cudaError_t kad_launch_fg(const uint32_t *counts, const uint32_t *c0, const double *ltab, int32_t n,
                           unsigned long long tau, unsigned long long omega, double *f, double *g, cudaStream_t st);

@@ -81,7 +81,7 @@ __global__ void k_noalloc_reset(KadCtl *ctl, unsigned long long *work, unsigned 
         ctl->closer = 0;
         ctl->err = 0;
         ctl->stopped_by_omega = 0;
-        for (int i = 0; i < 8; i++) work[i] = 0;
+        for (int i = 0; i < KAD_WORK_WORDS; i++) work[i] = 0;
     }
 }
 
@@ -181,7 +181,7 @@ extern "C" kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row
     a.ctl = ctl;
     a.work = work;
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = kad_launch_sample(a, (int)slots, kThreads, st);
+    if (e == cudaSuccess) e = kad_launch_sample(a, (int)slots, kThreads, 1, st);
     int derr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&derr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -134,6 +134,9 @@ struct Smem {
     int s, t;
     int try_close;
     int action;
+    int calib; // the current sample is a calibration sample
+    int publish;
+    uint32_t dom;
     unsigned int prefix;
     unsigned long long P;
     unsigned long long r;
@@ -141,6 +144,8 @@ struct Smem {
     unsigned long long idx;
     unsigned long long k;
     unsigned long long ovf_acc;
+    unsigned long long acc[KAD_WORK_WORDS];
+    long long tmark;
 };
 
 template <int BLOCK>
@@ -206,11 +211,14 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
 // fills the slot's list from the front, the t side from the back.
 __device__ __forceinline__ int phys(int z, int j, int n) { return z ? (n - 1 - j) : j; }
 
-// Write one interior vertex (at distance j from s, 1 <= j <= D-1).
+// Write one interior vertex (at distance j from s, 1 <= j <= D-1).  A null row
+// means a calibration sample: count v and move it one histogram bin up.
 __device__ __forceinline__ void emit(const SampleArgs &a, int32_t *row, int D, int j, int v) {
     if (j < 1 || j > D - 1) return;
-    if (a.mode == KAD_MODE_DIRECT) {
-        atomicAdd(a.dcount + v, 1u);
+    if (!row) {
+        const unsigned int c = atomicAdd(a.c0w + v, 1u);
+        atomicSub(a.hist + c, 1u);
+        atomicAdd(a.hist + c + 1, 1u);
     } else {
         if (j - 1 < a.cap)
             row[j - 1] = v;
@@ -356,7 +364,7 @@ __device__ void close_epoch(const SampleArgs &a, Smem<BLOCK> &sm, unsigned long 
         for (int t = lane; t < len; t += 32) {
             const int v = __ldcg(a.paths + row * (size_t)a.cap + t);
             const unsigned int c = atomicAdd(a.cnt + v, 1u) + 1u;
-            atomicMax(a.classmax + __ldg(a.c0 + v), (int)c);
+            atomicMax(a.classmax + __ldcg(a.c0 + v), (int)c);
         }
     }
     if (lane == 0 && ovf) atomicAdd(&sm.ovf_acc, ovf);
@@ -373,7 +381,7 @@ __device__ void close_epoch(const SampleArgs &a, Smem<BLOCK> &sm, unsigned long 
         for (int j = tid; j < a.nclass; j += BLOCK) {
             const int cm = __ldcg(a.classmax + j);
             if (cm >= 0) {
-                const double L = __ldg(a.ltab + j);
+                const double L = __ldcg(a.ltab + j); // uploaded while this launch runs
                 const double f = kad_fg_dev((unsigned long long)cm, L, tau, a.omega, false);
                 const double g = kad_fg_dev((unsigned long long)cm, L, tau, a.omega, true);
                 if (!(f <= a.eps && g <= a.eps)) pass = 0;
@@ -397,8 +405,10 @@ __device__ void close_epoch(const SampleArgs &a, Smem<BLOCK> &sm, unsigned long 
     __syncthreads();
 }
 
+// Epoch k can be closed once all its samples are written, no stop has been
+// decided, and the host has uploaded the L table (calibration's result).
 __device__ __forceinline__ bool epoch_ready(const SampleArgs &a, unsigned long long k) {
-    return k < a.k_end && *(volatile int *)&a.ctl->stop == 0 &&
+    return k < a.k_end && *(volatile int *)&a.ctl->stop == 0 && *(volatile int *)&a.ctl->ltab_ready != 0 &&
            *(volatile uint32_t *)&a.epoch_done[k % a.ring] == a.epoch;
 }
 
@@ -440,8 +450,8 @@ __device__ void run_closer(const SampleArgs &a, Smem<BLOCK> &sm) {
 }
 
 // ---------------------------------------------------------------- the kernel
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     __shared__ Smem<BLOCK> sm;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int32_t n = a.n;
@@ -454,27 +464,52 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
     const int mcap = (a.mcap < KAD_MCAP_MAX) ? a.mcap : KAD_MCAP_MAX;
 
     // work counters (thread 0 except pred, which every thread counts)
-    unsigned long long w_exp = 0, w_scan = 0, w_lab = 0, w_trace = 0, w_inc = 0, w_smp = 0, w_pred = 0;
+    // Work counters kept by thread 0 live in shared memory (sm.acc, laid out as
+    // the work buffer: expanded, scanned, labelled, -, trace arcs, increments,
+    // samples, -, then SM cycles per stage: draw+init, BFS, meeting draw,
+    // trace-back+output, reset, epoch close); every thread counts its own arcs
+    // into the next level or meeting set.
+    unsigned long long w_pred = 0;
+    if (tid < KAD_WORK_WORDS) sm.acc[tid] = 0;
     Stream st;
+
+    // A launch that continues a run first closes the epochs an earlier launch
+    // completed while the L table was not yet available.
+    if (a.mode == KAD_MODE_RING && blockIdx.x == 0) run_closer<BLOCK>(a, sm);
 
     for (;;) {
         // ---------------------------------------------------- next sample index
         if (tid == 0) {
             unsigned long long idx = ~0ull;
+            int calib = 0;
+            uint32_t dom = a.domain;
             const bool stopped = (a.mode == KAD_MODE_RING) && (*(volatile int *)&a.ctl->stop != 0);
             if (!stopped) {
-                const unsigned long long i = atomicAdd(&a.ctl->next, 1ull);
-                if (i < a.i1) idx = i;
+                const unsigned long long g = atomicAdd(&a.ctl->next, 1ull);
+                if (a.mode == KAD_MODE_RECORD) {
+                    if (g < a.i1) idx = g;
+                } else if (g < a.calib_n) {
+                    idx = g;
+                    calib = 1;
+                    dom = 1;
+                } else if (a.i0 + (g - a.calib_n) < a.i1) {
+                    idx = a.i0 + (g - a.calib_n);
+                    dom = 0;
+                }
             }
             sm.idx = idx;
+            sm.calib = calib;
+            sm.dom = dom;
         }
         __syncthreads();
         const unsigned long long idx = sm.idx;
         if (idx == ~0ull) break;
+        const bool calib = sm.calib != 0;
+        if (tid == 0) sm.tmark = clock64();
 
         // ---------------------------------------------------- pair draw
         if (tid == 0) {
-            st.init(a.key0, a.key1, idx, a.domain);
+            st.init(a.key0, a.key1, idx, sm.dom);
             const int s = (int)st.uniform((unsigned long long)n, a.ctl);
             int t = (int)st.uniform((unsigned long long)(n - 1), a.ctl);
             if (t >= s) t++;
@@ -505,6 +540,11 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
         }
         __syncthreads();
 
+        if (tid == 0) {
+            const long long now = clock64();
+            sm.acc[8] += (unsigned long long)(now - sm.tmark);
+            sm.tmark = now;
+        }
         // ---------------------------------------------------- balanced bidirectional BFS
         int X = 0;
         while (sm.D < 0) {
@@ -525,8 +565,8 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
             const uint32_t sideX = X ? KAD_SIDE : 0u;
             const uint32_t keyNext = sideX | (uint32_t)(levX + 2);
             if (tid == 0) {
-                w_exp += (unsigned long long)(fe - fb);
-                w_scan += sm.dsum[X];
+                sm.acc[0] += (unsigned long long)(fe - fb);
+                sm.acc[1] += sm.dsum[X];
                 sm.met = 0;
                 sm.next_dsum = 0;
             }
@@ -641,7 +681,7 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
                     sm.D = sm.lev[X] + 1 + sm.lev[Y];
                 } else {
                     const int tl = min(sm.tail[X], n - tailY);
-                    w_lab += (unsigned long long)(tl - fe);
+                    sm.acc[2] += (unsigned long long)(tl - fe);
                     sm.fb[X] = fe;
                     sm.fe[X] = tl;
                     sm.lev[X] = levX + 1;
@@ -652,6 +692,11 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
             __syncthreads();
         }
 
+        if (tid == 0) {
+            const long long now = clock64();
+            sm.acc[9] += (unsigned long long)(now - sm.tmark);
+            sm.tmark = now;
+        }
         const int D = sm.D;
         unsigned long long sst = 0;
         // ---------------------------------------------------- meeting draw
@@ -752,13 +797,18 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
             __syncthreads();
         }
 
+        if (tid == 0) {
+            const long long now = clock64();
+            sm.acc[10] += (unsigned long long)(now - sm.tmark);
+            sm.tmark = now;
+        }
         // ---------------------------------------------------- trace-back + output
         size_t row = 0;
         if (a.mode == KAD_MODE_RING)
             row = (size_t)((idx / a.epoch) % a.ring) * a.epoch + (size_t)(idx % a.epoch);
         else if (a.mode == KAD_MODE_RECORD)
             row = (size_t)(idx - a.i0);
-        int32_t *const out = (a.mode == KAD_MODE_DIRECT) ? nullptr : a.paths + row * (size_t)a.cap;
+        int32_t *const out = calib ? nullptr : a.paths + row * (size_t)a.cap;
         if (D > 0 && wid == 0) {
             const int Y = 1 - X;
             const int mid = sm.mid;
@@ -791,9 +841,9 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
                             s_sel = 1ull;
                         } else if (!(a.debug & KAD_DEBUG_TRACE_SCAN) && reC - rsC > KAD_DEG_SCAN && lcnt <= KAD_LCAP) {
                             trace_from_level<BLOCK>(a, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel,
-                                                    s_sel, w_trace);
+                                                    s_sel, sm.acc[4]);
                         } else {
-                            trace_scan(a, label, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, w_trace);
+                            trace_scan(a, label, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, sm.acc[4]);
                         }
                         if (p_sel < 0) {
                             if (lane == 0) kad_set_err(a.ctl, KAD_DERR_TRACE);
@@ -809,9 +859,9 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
         }
         if (tid == 0) {
             const int inc = (D > 0) ? D - 1 : 0;
-            w_inc += (unsigned long long)inc;
-            w_smp++;
-            if (a.mode != KAD_MODE_DIRECT) {
+            sm.acc[5] += (unsigned long long)inc;
+            sm.acc[6]++;
+            if (!calib) {
                 a.plen[row] = (inc <= a.cap) ? inc : a.cap;
                 a.pflag[row] = (sst == KAD_U64MAX) ? 1 : 0;
             }
@@ -824,6 +874,11 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
         }
         __syncthreads();
 
+        if (tid == 0) {
+            const long long now = clock64();
+            sm.acc[11] += (unsigned long long)(now - sm.tmark);
+            sm.tmark = now;
+        }
         // ---------------------------------------------------- reset the slot
         {
             const int t0 = min(sm.tail[0], n), t1 = min(sm.tail[1], n - t0);
@@ -840,17 +895,51 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
         __threadfence_block();
         __syncthreads();
 
+        if (tid == 0) {
+            const long long now = clock64();
+            sm.acc[12] += (unsigned long long)(now - sm.tmark);
+            sm.tmark = now;
+        }
         // ---------------------------------------------------- epoch bookkeeping
-        if (a.mode == KAD_MODE_RING) {
+        if (a.mode == KAD_MODE_RING && calib) {
+            // The block finishing the last calibration sample publishes the
+            // histogram to the mapped host page and raises the flag the host
+            // waits for; the host then computes the L table while sampling goes on.
+            if (tid == 0) {
+                __threadfence();
+                const unsigned long long done = atomicAdd(&a.ctl->calib_done, 1ull) + 1ull;
+                __threadfence();
+                sm.publish = (done == a.calib_n) ? 1 : 0;
+            }
+            __syncthreads();
+            if (sm.publish) {
+                for (int c = tid; c < a.nclass; c += BLOCK) a.hpage->hist[c] = __ldcg(a.hist + c);
+                __threadfence_system();
+                __syncthreads();
+                if (tid == 0) {
+                    *(volatile int *)&a.hpage->calib_flag = 1;
+                    __threadfence_system();
+                }
+            }
+        } else if (a.mode == KAD_MODE_RING) {
             if (tid == 0) {
                 __threadfence();
                 const unsigned long long e = idx / a.epoch;
                 const unsigned int old = atomicAdd(&a.epoch_done[e % a.ring], 1u);
                 kad_fence_sc();
-                sm.try_close = (old + 1u == a.epoch) ? 1 : 0;
+                int tc = (old + 1u == a.epoch) ? 1 : 0;
+                // epochs left unclosed while the L table was on its way
+                if (!tc && *(volatile int *)&a.ctl->ltab_ready && *(volatile int *)&a.ctl->closer == 0)
+                    tc = epoch_ready(a, *(volatile unsigned long long *)&a.ctl->closed) ? 1 : 0;
+                sm.try_close = tc;
             }
             __syncthreads();
             if (sm.try_close) run_closer<BLOCK>(a, sm);
+        }
+        if (tid == 0) {
+            const long long now = clock64();
+            sm.acc[13] += (unsigned long long)(now - sm.tmark);
+            sm.tmark = now;
         }
     }
 
@@ -859,38 +948,12 @@ __global__ void __launch_bounds__(BLOCK) k_sample(const SampleArgs a) {
     for (int o = 16; o > 0; o >>= 1) w_pred += __shfl_xor_sync(FULL_MASK, w_pred, o);
     if (lane == 0 && w_pred) atomicAdd(a.work + 3, w_pred);
     if (tid == 0) {
-        if (w_exp) atomicAdd(a.work + 0, w_exp);
-        if (w_scan) atomicAdd(a.work + 1, w_scan);
-        if (w_lab) atomicAdd(a.work + 2, w_lab);
-        if (w_trace) atomicAdd(a.work + 4, w_trace);
-        if (w_inc) atomicAdd(a.work + 5, w_inc);
-        if (w_smp) atomicAdd(a.work + 6, w_smp);
+        for (int i = 0; i < KAD_WORK_WORDS; i++)
+            if (i != 3 && sm.acc[i]) atomicAdd(a.work + i, sm.acc[i]);
     }
 }
 
 // ---------------------------------------------------------------- small kernels
-// Histogram of the calibration counts: hist[c] = |{v : c0[v] = c}|.
-__global__ void k_hist(const uint32_t *__restrict__ c0, int32_t n, uint32_t *__restrict__ hist, int32_t nclass) {
-    extern __shared__ uint32_t sh[];
-    const bool use_sh = nclass <= 8192;
-    if (use_sh)
-        for (int i = threadIdx.x; i < nclass; i += blockDim.x) sh[i] = 0;
-    __syncthreads();
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const uint32_t c = __ldg(c0 + v);
-        if (c < (uint32_t)nclass) {
-            if (use_sh)
-                atomicAdd(sh + c, 1u);
-            else
-                atomicAdd(hist + c, 1u);
-        }
-    }
-    __syncthreads();
-    if (use_sh)
-        for (int i = threadIdx.x; i < nclass; i += blockDim.x)
-            if (sh[i]) atomicAdd(hist + i, sh[i]);
-}
-
 // b~(v) = c(v)/tau (Section 2.3), correctly rounded division.
 __global__ void k_finalize(const uint32_t *__restrict__ cnt, int32_t n, unsigned long long tau, double *__restrict__ bc) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
@@ -910,53 +973,38 @@ __global__ void k_fg(const uint32_t *__restrict__ counts, const uint32_t *__rest
 } // namespace
 
 // ---------------------------------------------------------------- launchers
-cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, cudaStream_t st) {
+// Sampling-kernel variants: threads per block x resident blocks per SM the
+// register budget is sized for (64K registers per SM).
+#define KAD_VARIANTS(X) X(128, 4) X(128, 8) X(256, 2) X(256, 4) X(512, 1) X(512, 2) X(1024, 1)
+
+cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, int per_sm, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
-    switch (threads) {
-    case 128:
-        k_sample<128><<<blocks, 128, 0, st>>>(a);
-        break;
-    case 512:
-        k_sample<512><<<blocks, 512, 0, st>>>(a);
-        break;
-    case 1024:
-        k_sample<1024><<<blocks, 1024, 0, st>>>(a);
-        break;
-    default:
-        k_sample<256><<<blocks, 256, 0, st>>>(a);
-        break;
+#define KAD_LAUNCH(T, B)                                                                                              \
+    if (threads == T && per_sm == B) {                                                                                \
+        k_sample<T, B><<<blocks, T, 0, st>>>(a);                                                                      \
+        return cudaGetLastError();                                                                                    \
     }
-    return cudaGetLastError();
+    KAD_VARIANTS(KAD_LAUNCH)
+#undef KAD_LAUNCH
+    return cudaErrorInvalidConfiguration;
 }
 
-int kad_sample_max_blocks_per_sm(int threads) {
+bool kad_sample_variant_exists(int threads, int per_sm) {
+#define KAD_HAS(T, B)                                                                                                 \
+    if (threads == T && per_sm == B) return true;
+    KAD_VARIANTS(KAD_HAS)
+#undef KAD_HAS
+    return false;
+}
+
+int kad_sample_max_blocks_per_sm(int threads, int per_sm) {
     int nb = 0;
-    cudaError_t e;
-    switch (threads) {
-    case 128:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<128>, 128, 0);
-        break;
-    case 512:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<512>, 512, 0);
-        break;
-    case 1024:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<1024>, 1024, 0);
-        break;
-    default:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<256>, 256, 0);
-        break;
-    }
+    cudaError_t e = cudaErrorInvalidConfiguration;
+#define KAD_OCC(T, B)                                                                                                 \
+    if (threads == T && per_sm == B) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<T, B>, T, 0);
+    KAD_VARIANTS(KAD_OCC)
+#undef KAD_OCC
     return (e == cudaSuccess) ? nb : 0;
-}
-
-cudaError_t kad_launch_hist(const uint32_t *c0, int32_t n, uint32_t *hist, int32_t nclass, cudaStream_t st) {
-    const int threads = 512;
-    int blocks = (n + threads - 1) / threads;
-    if (blocks > 1024) blocks = 1024;
-    if (blocks < 1) blocks = 1;
-    const size_t sh = (nclass <= 8192) ? (size_t)nclass * sizeof(uint32_t) : 0;
-    k_hist<<<blocks, threads, sh, st>>>(c0, n, hist, nclass);
-    return cudaGetLastError();
 }
 
 cudaError_t kad_launch_finalize(const uint32_t *cnt, int32_t n, unsigned long long tau, double *bc, cudaStream_t st) {

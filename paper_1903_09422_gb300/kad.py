@@ -27,7 +27,7 @@ class KadError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("epoch_size", ctypes.c_uint32), ("calib_div", ctypes.c_uint32), ("ring_epochs", ctypes.c_uint32),
                 ("slots", ctypes.c_int32), ("mcap", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("debug", ctypes.c_uint32)]
+                ("blocks_per_sm", ctypes.c_int32), ("flags", ctypes.c_uint32), ("debug", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):
@@ -41,7 +41,9 @@ class Result(ctypes.Structure):
                 ("t_total_ms", ctypes.c_double), ("t_calib_ms", ctypes.c_double), ("t_ads_ms", ctypes.c_double),
                 ("t_ads_kernel_ms", ctypes.c_double), ("ads_launches", ctypes.c_uint32),
                 ("slots_used", ctypes.c_int32), ("kernel_launches", ctypes.c_uint32),
-                ("reserved_", ctypes.c_uint32)]
+                ("reserved_", ctypes.c_uint32), ("phase_cycles", ctypes.c_uint64 * 6)]
+
+PHASE_NAMES = ("draw", "bfs", "meet", "trace", "reset", "close")
 
 
 EXPORTS = ("kad_graph_create", "kad_graph_create_device", "kad_graph_free", "kad_graph_info", "kad_options_default",
@@ -251,6 +253,7 @@ def _result_scalars(r):
                                     "t_calib_ms", "t_ads_ms", "t_ads_kernel_ms", "ads_launches", "slots_used",
                                     "kernel_launches")}
     d["counters"] = dict(zip(WORK_NAMES, (int(x) for x in r.work)))
+    d["phase_cycles"] = dict(zip(PHASE_NAMES, (int(x) for x in r.phase_cycles)))
     return d
 
 

@@ -89,7 +89,8 @@ def test_full_run_matches_oracle(kad, name):
     assert r["samples_computed"] >= r["tau"]
 
 
-@pytest.mark.parametrize("opt", [dict(block_threads=128), dict(block_threads=256), dict(block_threads=1024), dict(slots=1), dict(slots=7),
+@pytest.mark.parametrize("opt", [dict(block_threads=128), dict(block_threads=256), dict(block_threads=1024),
+                                 dict(block_threads=512, blocks_per_sm=2), dict(block_threads=256, blocks_per_sm=4), dict(slots=1), dict(slots=7),
                                  dict(mcap=0), dict(mcap=1), dict(ring_epochs=2), dict(slots=3, ring_epochs=2),
                                  dict(epoch_size=250), dict(debug=1)])
 def test_result_independent_of_launch_configuration(kad, opt):
