@@ -87,13 +87,15 @@ typedef struct {
                             0 forces the general path; results do not depend on it) */
     int32_t block_threads; /* threads per sampling block: 128, 256, 512 or 1024 (0 = 512) */
     int32_t blocks_per_sm; /* resident sampling blocks per SM the kernel is built for: 128 threads 4|8,
-                              256: 2|4, 512: 1|2, 1024: 1 (0 = the first of these) */
+                              256: 2|4, 512: 1|2, 1024: 1 (0 = 4, 2, 2, 1 respectively) */
     uint32_t flags;      /* KAD_RUN_* */
     uint32_t debug;      /* KAD_DEBUG_* (tests only; results do not depend on it) */
 } kad_options;
 
 #define KAD_RUN_TIMING 1u      /* fill kad_result.t_* with CUDA-event times of each phase */
-#define KAD_DEBUG_TRACE_SCAN 1u /* trace-back always scans the current vertex's adjacency */
+#define KAD_DEBUG_TRACE_SCAN 1u    /* trace-back always scans the current vertex's adjacency */
+#define KAD_DEBUG_SMEM_BITMAP 2u /* keep the labelled-vertex bitmap in shared memory when it fits */
+#define KAD_DEBUG_FULL_SCAN 4u   /* the meeting round always scans the expanding side's rows */
 
 /* Initialises *opt to the defaults above. */
 void kad_options_default(kad_options *opt);

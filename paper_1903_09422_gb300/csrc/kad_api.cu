@@ -346,7 +346,8 @@ int device_sms(int dev) {
 
 struct LaunchCfg {
     int threads;
-    int per_sm; // resident blocks per SM the kernel variant is compiled for
+    int per_sm;      // resident blocks per SM the kernel variant is compiled for
+    size_t dyn_smem; // bytes of dynamic shared memory (the slot bitmap) or 0
 };
 
 // Threads per block and blocks per SM.  Unknown combinations fall back to the
@@ -354,16 +355,30 @@ struct LaunchCfg {
 LaunchCfg resolve_cfg(const kad_options &o) {
     LaunchCfg c;
     c.threads = (o.block_threads == 128 || o.block_threads == 256 || o.block_threads == 1024) ? o.block_threads : 512;
-    const int def = (c.threads == 128) ? 4 : (c.threads == 256) ? 2 : 1;
+    const int def = (c.threads == 128) ? 4 : (c.threads == 256) ? 2 : (c.threads == 512) ? 2 : 1;
     c.per_sm = (o.blocks_per_sm > 0 && kad_sample_variant_exists(c.threads, o.blocks_per_sm)) ? o.blocks_per_sm : def;
+    c.dyn_smem = 0;
     return c;
+}
+
+// The slot bitmap goes to shared memory when per_sm blocks of the variant,
+// each with the bitmap, still fit an SM's shared memory.
+void choose_bitmap_home(LaunchCfg &c, int32_t n, int dev) {
+    int per_sm_max = 0, per_block_max = 0;
+    cudaDeviceGetAttribute(&per_sm_max, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&per_block_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t stat = kad_sample_static_smem(c.threads, c.per_sm);
+    const size_t dyn = ((((size_t)n + 31) / 32) * 4 + 127) & ~(size_t)127;
+    const size_t reserve = 1024; // per-block system use
+    if (stat + dyn <= (size_t)per_block_max && (size_t)c.per_sm * (stat + dyn + reserve) <= (size_t)per_sm_max)
+        c.dyn_smem = dyn;
 }
 
 // Number of sampling slots: all resident blocks, capped by a share of free memory.
 int resolve_slots(kad_graph *g, const kad_options &o, const LaunchCfg &cfg) {
     int slots = o.slots;
     if (slots <= 0) {
-        const int per_sm = kad_sample_max_blocks_per_sm(cfg.threads, cfg.per_sm);
+        const int per_sm = kad_sample_max_blocks_per_sm(cfg.threads, cfg.per_sm, cfg.dyn_smem);
         slots = device_sms(g->device) * (per_sm > 0 ? per_sm : 1);
     }
     size_t fr = 0, tot = 0;
@@ -409,7 +424,9 @@ kad_status launch_phase(kad_graph *g, const SampleArgs &a, int blocks, const Lau
     k_set_ctl<<<1, 1, 0, st>>>(a.ctl, next0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(g, e);
-    e = kad_launch_sample(a, blocks, cfg.threads, cfg.per_sm, st);
+    SampleArgs b = a;
+    b.bits_smem = cfg.dyn_smem ? 1 : 0;
+    e = kad_launch_sample(b, blocks, cfg.threads, cfg.per_sm, cfg.dyn_smem, st);
     if (e == cudaSuccess) e = cudaEventRecord(g->ws.ev_launch, st);
     if (e != cudaSuccess) return fail(g, e);
     return KAD_OK;
@@ -469,7 +486,8 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     const uint64_t max_epochs = (omega + N - 1) / N; // the stop rule holds at tau >= omega
     const size_t nclass = (size_t)tau0 + 1;
     if (nclass > (size_t)0x7fffffff || omega > ((uint64_t)1 << 40)) return KAD_ERR_INVALID_ARG;
-    const LaunchCfg cfg = resolve_cfg(o);
+    LaunchCfg cfg = resolve_cfg(o);
+    if (o.debug & KAD_DEBUG_SMEM_BITMAP) choose_bitmap_home(cfg, g->gd.n, g->device);
     const int slots = resolve_slots(g, o, cfg);
     const int32_t cap = path_cap(g);
     // Epoch ring: enough to hold the whole run when it fits in about 1 GiB of
@@ -759,7 +777,8 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
         o = *opt;
     else
         fill_defaults(&o);
-    const LaunchCfg cfg = resolve_cfg(o);
+    LaunchCfg cfg = resolve_cfg(o);
+    if (o.debug & KAD_DEBUG_SMEM_BITMAP) choose_bitmap_home(cfg, g->gd.n, g->device);
     int slots = resolve_slots(g, o, cfg);
     if ((int64_t)slots > count) slots = (int)count;
     kad_status s;

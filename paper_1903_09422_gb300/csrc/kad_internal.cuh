@@ -74,6 +74,7 @@ struct SampleArgs {
     // small enough to stay in L2, it spares most label reads
     uint32_t *bits;
     int32_t nw;
+    int bits_smem; // 1: the bitmap is in dynamic shared memory (nw words), bits unused
     unsigned long long *sigma;
     unsigned long long *sigma2;
     int32_t *list;
@@ -151,9 +152,11 @@ __device__ __forceinline__ double kad_fg_dev(unsigned long long c, double L, uns
 }
 
 // Host-side launchers (defined in the .cu files).
-cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, int per_sm, cudaStream_t st);
+cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, int per_sm, size_t dyn_smem,
+                              cudaStream_t st);
 bool kad_sample_variant_exists(int threads, int per_sm);
-int kad_sample_max_blocks_per_sm(int threads, int per_sm);
+size_t kad_sample_static_smem(int threads, int per_sm);
+int kad_sample_max_blocks_per_sm(int threads, int per_sm, size_t dyn_smem);
 cudaError_t kad_launch_finalize(const uint32_t *cnt, int32_t n, unsigned long long tau, double *bc, cudaStream_t st);
 cudaError_t kad_launch_fg(const uint32_t *counts, const uint32_t *c0, const double *ltab, int32_t n,
                           unsigned long long tau, unsigned long long omega, double *f, double *g, cudaStream_t st);

@@ -181,7 +181,7 @@ extern "C" kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row
     a.ctl = ctl;
     a.work = work;
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = kad_launch_sample(a, (int)slots, kThreads, 1, st);
+    if (e == cudaSuccess) e = kad_launch_sample(a, (int)slots, kThreads, 1, 0, st);
     int derr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&derr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

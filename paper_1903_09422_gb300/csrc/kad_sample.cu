@@ -30,6 +30,7 @@
 // the state after each epoch, so every check sees an integral prefix of samples.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "kad_internal.cuh"
 
@@ -39,6 +40,8 @@
 #define KAD_MAXLV 62    // levels whose list ranges are kept for the trace-back
 #define KAD_LCAP 64     // largest predecessor level searched from its list
 #define KAD_DEG_SCAN 64 // adjacency lists up to this length are always scanned
+#define KAD_PAIR_MIN_ARCS 1024 // rounds with fewer arcs always expand by scanning
+#define KAD_PAIR_COST 16       // one pairwise adjacency test counts as this many arc reads
 
 namespace {
 
@@ -115,6 +118,7 @@ struct Stream {
 // ---------------------------------------------------------------- block helpers
 template <int BLOCK>
 struct Smem {
+    int32_t uid[BLOCK];
     int32_t rs[BLOCK];
     int32_t off[BLOCK];
     unsigned long long sig[BLOCK];
@@ -207,6 +211,27 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
     return x;
 }
 
+// The labelled-vertex bitmap of a slot lives in the block's dynamic shared
+// memory when it fits (every check then costs a shared-memory read), else in
+// global memory (read through L2).
+extern __shared__ uint32_t kad_dyn_bits[];
+
+__device__ __forceinline__ uint32_t bits_ld(bool sh, const uint32_t *g, int w) {
+    return sh ? kad_dyn_bits[w] : __ldcg(g + w);
+}
+__device__ __forceinline__ void bits_set(bool sh, uint32_t *g, int v) {
+    if (sh)
+        atomicOr(kad_dyn_bits + (v >> 5), 1u << (v & 31));
+    else
+        atomicOr(g + (v >> 5), 1u << (v & 31));
+}
+__device__ __forceinline__ void bits_clear_word(bool sh, uint32_t *g, int w) {
+    if (sh)
+        kad_dyn_bits[w] = 0u;
+    else
+        g[w] = 0u;
+}
+
 // Physical list position of the j-th vertex labelled on side z: the s side
 // fills the slot's list from the front, the t side from the back.
 __device__ __forceinline__ int phys(int z, int j, int n) { return z ? (n - 1 - j) : j; }
@@ -234,7 +259,7 @@ __device__ __forceinline__ void emit(const SampleArgs &a, int32_t *row, int D, i
 // distance labels).  Called by one warp; every lane returns the same choice.
 
 // Scan adj(cur) 4 x 32 arcs per pass (all loads of a pass issued first).
-__device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *label, const uint32_t *bits,
+__device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *label, bool bsh, const uint32_t *bits,
                                            const unsigned long long *sigma, int z, int d, int rsC, int reC,
                                            unsigned long long r, int &p_sel, unsigned long long &s_sel,
                                            unsigned long long &w_trace) {
@@ -250,7 +275,7 @@ __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *
             pp[k] = (e < reC) ? __ldg(a.col + e) : -1;
         }
 #pragma unroll
-        for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? __ldcg(bits + (pp[k] >> 5)) : 0u;
+        for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? bits_ld(bsh, bits, pp[k] >> 5) : 0u;
 #pragma unroll
         for (int k = 0; k < 4; k++)
             lp[k] = (pp[k] >= 0 && ((lp[k] >> (pp[k] & 31)) & 1u)) ? kad_ld_u32(label + pp[k]) : 0u;
@@ -461,6 +486,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     unsigned long long *const sigma2 = a.sigma2 + soff;
     int32_t *const list = a.list + soff;
     uint32_t *const bits = a.bits + (size_t)blockIdx.x * (size_t)a.nw;
+    const bool bsh = a.bits_smem != 0;
+    if (bsh) {
+        for (int w = tid; w < a.nw; w += BLOCK) kad_dyn_bits[w] = 0u;
+        __syncthreads();
+    }
     const int mcap = (a.mcap < KAD_MCAP_MAX) ? a.mcap : KAD_MCAP_MAX;
 
     // work counters (thread 0 except pred, which every thread counts)
@@ -520,8 +550,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             if (__ldg(a.comp + s) == __ldg(a.comp + t)) {
                 label[s] = 1u;            // s side, level 0
                 label[t] = KAD_SIDE | 1u; // t side, level 0
-                atomicOr(bits + (s >> 5), 1u << (s & 31));
-                atomicOr(bits + (t >> 5), 1u << (t & 31));
+                bits_set(bsh, bits, s);
+                bits_set(bsh, bits, t);
                 sigma[s] = 1ull;
                 sigma[t] = 1ull;
                 list[0] = s;
@@ -564,6 +594,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             }
             const uint32_t sideX = X ? KAD_SIDE : 0u;
             const uint32_t keyNext = sideX | (uint32_t)(levX + 2);
+            const int yb = sm.fb[Y], fy = sm.fe[Y] - yb, fx = fe - fb;
+            // Pairwise test: when both frontiers are small but X's rows are long,
+            // testing every (u in F_X, w in F_Y) for adjacency finds exactly the
+            // arcs from F_X into the other side's frontier -- M, and sigma_X on M
+            // -- without reading X's rows.  No adjacent pair means no meeting in
+            // this round, and the expansion below runs as usual.
+            const bool pairs = !(a.debug & KAD_DEBUG_FULL_SCAN) && fx <= BLOCK && sm.dsum[X] >= KAD_PAIR_MIN_ARCS &&
+                               (unsigned long long)fx * (unsigned long long)fy * KAD_PAIR_COST < sm.dsum[X];
             if (tid == 0) {
                 sm.acc[0] += (unsigned long long)(fe - fb);
                 sm.acc[1] += sm.dsum[X];
@@ -572,7 +610,39 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             }
             __syncthreads();
             unsigned long long pred_next = 0, pred_m = 0;
-            for (int cb = fb; cb < fe; cb += BLOCK) {
+            if (pairs) {
+                if (tid < fx) {
+                    const int u = __ldcg(list + phys(X, fb + tid, n));
+                    const uint32_t lu = kad_ld_u32(label + u);
+                    sm.uid[tid] = u;
+                    sm.rs[tid] = __ldg(a.rp + u);
+                    sm.off[tid] = __ldg(a.rp + u + 1);
+                    sm.sig[tid] = (lu & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + u);
+                }
+                __syncthreads();
+                const long long np = (long long)fx * (long long)fy;
+                int probes = 0;
+                for (long long p = tid; p < np; p += BLOCK) {
+                    const int i = (int)(p % fx), j = (int)(p / fx);
+                    const int w = __ldcg(list + phys(Y, yb + j, n));
+                    const int u = sm.uid[i], rsU = sm.rs[i], reU = sm.off[i];
+                    const int rsW = __ldg(a.rp + w), reW = __ldg(a.rp + w + 1);
+                    const bool adj = (reU - rsU <= reW - rsW) ? row_contains(a.col, rsU, reU, w, probes)
+                                                              : row_contains(a.col, rsW, reW, u, probes);
+                    if (adj) {
+                        pred_m++;
+                        sm.met = 1;
+                        const unsigned long long su = sm.sig[i];
+                        atomicOr(label + w, KAD_INM);
+                        const unsigned long long old = atomicAdd(sigma2 + w, su);
+                        if (old + su < old) atomicOr(label + w, KAD_OVF2);
+                    }
+                }
+                __syncthreads();
+            }
+            // a meeting found by the pairwise test completes the round
+            const int expand_end = (pairs && sm.met) ? fb : fe;
+            for (int cb = fb; cb < expand_end; cb += BLOCK) {
                 const int cnt = min(BLOCK, fe - cb);
                 int d = 0;
                 if (tid < cnt) {
@@ -614,7 +684,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                         }
                     }
 #pragma unroll
-                    for (int k = 0; k < KAD_ITEMS; k++) ll[k] = (vv[k] >= 0) ? __ldcg(bits + (vv[k] >> 5)) : 0u;
+                    for (int k = 0; k < KAD_ITEMS; k++) ll[k] = (vv[k] >= 0) ? bits_ld(bsh, bits, vv[k] >> 5) : 0u;
                     // only vertices whose bit is set carry a label worth reading
 #pragma unroll
                     for (int k = 0; k < KAD_ITEMS; k++)
@@ -631,7 +701,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                                 const uint32_t old = atomicCAS(label + v, 0u, keyNext);
                                 if (old == 0u) {
                                     claimed = true;
-                                    atomicOr(bits + (v >> 5), 1u << (v & 31));
+                                    bits_set(bsh, bits, v);
                                     lv = keyNext;
                                 } else {
                                     lv = old;
@@ -843,7 +913,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                             trace_from_level<BLOCK>(a, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel,
                                                     s_sel, sm.acc[4]);
                         } else {
-                            trace_scan(a, label, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, sm.acc[4]);
+                            trace_scan(a, label, bsh, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, sm.acc[4]);
                         }
                         if (p_sel < 0) {
                             if (lane == 0) kad_set_err(a.ctl, KAD_DERR_TRACE);
@@ -888,7 +958,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 const uint32_t lv = kad_ld_u32(label + v);
                 label[v] = 0u;
                 sigma[v] = 0ull;
-                bits[v >> 5] = 0u; // every set bit of this word belongs to a listed vertex
+                bits_clear_word(bsh, bits, v >> 5); // every set bit of this word belongs to a listed vertex
                 if (lv & KAD_INM) sigma2[v] = 0ull;
             }
         }
@@ -977,11 +1047,17 @@ __global__ void k_fg(const uint32_t *__restrict__ counts, const uint32_t *__rest
 // register budget is sized for (64K registers per SM).
 #define KAD_VARIANTS(X) X(128, 4) X(128, 8) X(256, 2) X(256, 4) X(512, 1) X(512, 2) X(1024, 1)
 
-cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, int per_sm, cudaStream_t st) {
+cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, int per_sm, size_t dyn_smem,
+                              cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
 #define KAD_LAUNCH(T, B)                                                                                              \
     if (threads == T && per_sm == B) {                                                                                \
-        k_sample<T, B><<<blocks, T, 0, st>>>(a);                                                                      \
+        if (dyn_smem > 0) {                                                                                           \
+            const cudaError_t e =                                                                                     \
+                cudaFuncSetAttribute(k_sample<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);     \
+            if (e != cudaSuccess) return e;                                                                           \
+        }                                                                                                             \
+        k_sample<T, B><<<blocks, T, dyn_smem, st>>>(a);                                                               \
         return cudaGetLastError();                                                                                    \
     }
     KAD_VARIANTS(KAD_LAUNCH)
@@ -997,11 +1073,25 @@ bool kad_sample_variant_exists(int threads, int per_sm) {
     return false;
 }
 
-int kad_sample_max_blocks_per_sm(int threads, int per_sm) {
+size_t kad_sample_static_smem(int threads, int per_sm) {
+    cudaFuncAttributes fa;
+    memset(&fa, 0, sizeof(fa));
+#define KAD_ATTR(T, B)                                                                                                \
+    if (threads == T && per_sm == B && cudaFuncGetAttributes(&fa, k_sample<T, B>) == cudaSuccess) return fa.sharedSizeBytes;
+    KAD_VARIANTS(KAD_ATTR)
+#undef KAD_ATTR
+    return 0;
+}
+
+int kad_sample_max_blocks_per_sm(int threads, int per_sm, size_t dyn_smem) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidConfiguration;
 #define KAD_OCC(T, B)                                                                                                 \
-    if (threads == T && per_sm == B) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<T, B>, T, 0);
+    if (threads == T && per_sm == B) {                                                                                \
+        if (dyn_smem > 0)                                                                                             \
+            cudaFuncSetAttribute(k_sample<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);         \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<T, B>, T, dyn_smem);                         \
+    }
     KAD_VARIANTS(KAD_OCC)
 #undef KAD_OCC
     return (e == cudaSuccess) ? nb : 0;

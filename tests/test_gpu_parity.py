@@ -92,7 +92,8 @@ def test_full_run_matches_oracle(kad, name):
 @pytest.mark.parametrize("opt", [dict(block_threads=128), dict(block_threads=256), dict(block_threads=1024),
                                  dict(block_threads=512, blocks_per_sm=2), dict(block_threads=256, blocks_per_sm=4), dict(slots=1), dict(slots=7),
                                  dict(mcap=0), dict(mcap=1), dict(ring_epochs=2), dict(slots=3, ring_epochs=2),
-                                 dict(epoch_size=250), dict(debug=1)])
+                                 dict(epoch_size=250), dict(debug=1), dict(debug=2), dict(debug=4),
+                                 dict(debug=2, block_threads=512, blocks_per_sm=2)])
 def test_result_independent_of_launch_configuration(kad, opt):
     g = gen.rmat(12, 8, seed=1)
     eps, delta, seed = 0.03, 0.1, 11
@@ -104,6 +105,20 @@ def test_result_independent_of_launch_configuration(kad, opt):
     assert r["tau"] == ref["tau"] and r["epochs"] == ref["epochs"]
     np.testing.assert_array_equal(r["counts"], ref["counts"])
     compare_records(rec, O.samples(g, seed, 0, 700))
+
+
+def test_meeting_round_methods_agree_on_hub_graph(kad):
+    # The pairwise frontier test and the full scan of the expanding side's rows
+    # must find the same meeting sets (hence the same records as the oracle).
+    g = gen.rmat(15, 16, seed=4)
+    orc = O.samples(g, 13, 0, 1500)
+    with kad.Graph.from_csr(g) as G:
+        a = G.sample_records(13, 0, 1500)
+        b = G.sample_records(13, 0, 1500, debug=4)
+    compare_records(a, orc)
+    compare_records(b, orc)
+    for k in ("expanded", "scanned", "labelled", "pred_arcs", "increments"):
+        assert a["counters"][k] == orc["counters"][k] == b["counters"][k], k
 
 
 def test_trace_methods_agree_on_hub_graph(kad):
