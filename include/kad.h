@@ -90,6 +90,9 @@ typedef struct {
                               256: 2|4, 512: 1|2, 1024: 1 (0 = 4, 2, 2, 1 respectively) */
     uint32_t flags;      /* KAD_RUN_* */
     uint32_t debug;      /* KAD_DEBUG_* (tests only; results do not depend on it) */
+    uint32_t max_epochs; /* > 0: stop after this many epochs even if the stop rule does not hold
+                            (a truncated run, for comparisons on large graphs); 0 = no limit */
+    uint32_t reserved;
 } kad_options;
 
 #define KAD_RUN_TIMING 1u      /* fill kad_result.t_* with CUDA-event times of each phase */
@@ -116,7 +119,7 @@ typedef struct {
     uint32_t epochs;           /* stop-check epochs used */
     int32_t vd_bound;
     int32_t sigma_overflow;    /* 1 if any used sample saturated */
-    int32_t stopped_by_omega;  /* 1 if the run stopped because tau >= omega */
+    int32_t stopped_by_omega;  /* 1 if the run stopped because tau >= omega, 2 if by max_epochs */
     double tau_star;           /* calibration's bisection result */
     /* work of all samples computed (calibration and adaptive): frontier vertices
        expanded, arcs scanned, vertices labelled, arcs into the next level or

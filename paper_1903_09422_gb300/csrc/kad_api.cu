@@ -483,7 +483,8 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     const uint32_t N = o.epoch_size;
     const uint64_t omega = run_omega(g->vd, eps, delta);
     const uint64_t tau0 = run_calib(omega, N, o.calib_div);
-    const uint64_t max_epochs = (omega + N - 1) / N; // the stop rule holds at tau >= omega
+    uint64_t max_epochs = (omega + N - 1) / N; // the stop rule holds at tau >= omega
+    if (o.max_epochs && o.max_epochs < max_epochs) max_epochs = o.max_epochs;
     const size_t nclass = (size_t)tau0 + 1;
     if (nclass > (size_t)0x7fffffff || omega > ((uint64_t)1 << 40)) return KAD_ERR_INVALID_ARG;
     LaunchCfg cfg = resolve_cfg(o);
@@ -545,6 +546,7 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     a.nclass = (int32_t)nclass;
     a.eps = eps;
     a.omega = omega;
+    a.max_epochs = o.max_epochs;
     a.i0 = 0;
     a.i1 = (uint64_t)((ring < max_epochs) ? ring : max_epochs) * N;
     a.k_end = a.i1 / N;

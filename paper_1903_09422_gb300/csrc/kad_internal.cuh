@@ -113,6 +113,7 @@ struct SampleArgs {
     double eps;
     unsigned long long omega;
     unsigned long long k_end; // epochs of this launch end before k_end
+    unsigned long long max_epochs; // forced stop after this many epochs (truncated runs); 0 = none
     // work counters [0..5], samples [6], SM cycles per phase [8..13] (KAD_WORK_WORDS)
     unsigned long long *work;
 };

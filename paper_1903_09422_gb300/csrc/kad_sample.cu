@@ -417,9 +417,10 @@ __device__ void close_epoch(const SampleArgs &a, Smem<BLOCK> &sm, unsigned long 
     if (tid == 0) {
         a.ctl->overflow += sm.ovf_acc;
         a.epoch_done[k % a.ring] = 0;
-        if (tau >= a.omega || all) {
+        const bool cut = a.max_epochs && k + 1 >= a.max_epochs;
+        if (tau >= a.omega || all || cut) {
             a.ctl->tau = tau;
-            a.ctl->stopped_by_omega = (tau >= a.omega) ? 1 : 0;
+            a.ctl->stopped_by_omega = (tau >= a.omega) ? 1 : (all ? 0 : 2);
             __threadfence();
             *(volatile int *)&a.ctl->stop = 1;
         }

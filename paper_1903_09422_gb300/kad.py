@@ -27,7 +27,8 @@ class KadError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("epoch_size", ctypes.c_uint32), ("calib_div", ctypes.c_uint32), ("ring_epochs", ctypes.c_uint32),
                 ("slots", ctypes.c_int32), ("mcap", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("flags", ctypes.c_uint32), ("debug", ctypes.c_uint32)]
+                ("blocks_per_sm", ctypes.c_int32), ("flags", ctypes.c_uint32), ("debug", ctypes.c_uint32),
+                ("max_epochs", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):

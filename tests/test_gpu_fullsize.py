@@ -1,0 +1,82 @@
+"""Parity at the full sizes of the configured workloads.
+
+R-MAT scale 20 (the benchmarked query) is compared end to end.  On the 2048^2
+grid and the 4M-vertex hyperbolic graph a full oracle run takes too long, so
+these compare (a) every per-sample record of a range of samples, and (b) a run
+truncated after the first epoch on both sides: calibration counts, the L table,
+and the counts, tau and epochs of the truncated run, all bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1903_09422_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+_cache = {}
+
+
+def workload(name):
+    if name not in _cache:
+        _cache[name] = gen.workload_graph(name)
+    return _cache[name]
+
+
+@pytest.fixture(scope="module")
+def kad():
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1903_09422_gb300 import build, kad as K
+    build.build()
+    return K
+
+
+def compare_records(rec, orc):
+    for k in ("s", "t", "D", "sigma_st", "overflow", "paths"):
+        np.testing.assert_array_equal(rec[k], orc[k], err_msg=k)
+    for k in ("expanded", "scanned", "labelled", "pred_arcs", "increments"):
+        assert rec["counters"][k] == orc["counters"][k], k
+
+
+@pytest.mark.parametrize("name,count", [("rmat20", 2000), ("grid2048", 400), ("hyp4m", 400)])
+def test_records_at_full_size(kad, name, count):
+    g = workload(name)
+    w = gen.WORKLOADS[name]
+    with kad.Graph.from_csr(g) as G:
+        assert G.vd_bound == O.vd_bound(g)
+        rec = G.sample_records(w["seed"], 5000, count)
+        cal = G.sample_records(w["seed"], 0, count // 2, domain=1)
+    compare_records(rec, O.samples(g, w["seed"], 5000, count))
+    compare_records(cal, O.samples(g, w["seed"], 0, count // 2, domain=1))
+
+
+def test_benchmarked_query_end_to_end(kad):
+    name = "rmat20"
+    g = workload(name)
+    w = gen.WORKLOADS[name]
+    ref = O.kadabra(g, w["eps"], w["delta"], w["seed"])
+    with kad.Graph.from_csr(g) as G:
+        r = G.run(w["eps"], w["delta"], w["seed"], c0=True, ltab=True)
+    assert (r["tau"], r["epochs"], r["omega"], r["calib_samples"]) == \
+        (ref["tau"], ref["epochs"], ref["omega"], ref["calib_samples"])
+    np.testing.assert_array_equal(r["c0"], ref["c0"])
+    np.testing.assert_array_equal(r["L"], ref["L"])
+    np.testing.assert_array_equal(r["counts"], ref["counts"])
+    np.testing.assert_array_equal(r["bc"], ref["bc"])
+    assert r["overflow_samples"] == ref["overflow_samples"]
+
+
+@pytest.mark.parametrize("name", ["grid2048", "hyp4m"])
+def test_truncated_run_at_full_size(kad, name):
+    g = workload(name)
+    w = gen.WORKLOADS[name]
+    ref = O.kadabra(g, w["eps"], w["delta"], w["seed"], max_epochs=1)
+    with kad.Graph.from_csr(g) as G:
+        r = G.run(w["eps"], w["delta"], w["seed"], c0=True, ltab=True, max_epochs=1)
+    assert (r["tau"], r["epochs"], r["omega"], r["calib_samples"]) == \
+        (ref["tau"], ref["epochs"], ref["omega"], ref["calib_samples"])
+    assert r["tau_star"] == ref["tau_star"]
+    np.testing.assert_array_equal(r["c0"], ref["c0"])
+    np.testing.assert_array_equal(r["L"], ref["L"])
+    np.testing.assert_array_equal(r["counts"], ref["counts"])

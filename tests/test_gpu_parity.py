@@ -146,6 +146,16 @@ def test_meeting_selection_paths_agree_on_hub_graph(kad):
     compare_records(b, orc)
 
 
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_truncated_run_matches_oracle(kad, k):
+    g = gen.rmat(12, 8, seed=1)
+    ref = O.kadabra(g, 0.01, 0.1, 4, max_epochs=k)
+    with kad.Graph.from_csr(g) as G:
+        r = G.run(0.01, 0.1, 4, max_epochs=k)
+    assert r["tau"] == ref["tau"] == 1000 * min(k, ref["epochs"])
+    np.testing.assert_array_equal(r["counts"], ref["counts"])
+
+
 def test_fg_kernel_matches_oracle(kad):
     g = gen.rmat(12, 8, seed=1)
     ref = O.kadabra(g, 0.05, 0.1, 1)
