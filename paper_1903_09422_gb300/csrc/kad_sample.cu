@@ -690,54 +690,71 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
 #pragma unroll
                     for (int k = 0; k < KAD_ITEMS; k++)
                         ll[k] = (vv[k] >= 0 && ((ll[k] >> (vv[k] & 31)) & 1u)) ? kad_ld_u32(label + vv[k]) : 0u;
+                    // Claims first (all CAS of the pass in flight together), then
+                    // the path-count pushes, then the new vertices' degrees: each
+                    // kind of access overlaps across the items instead of chaining.
+                    bool claimed[KAD_ITEMS];
+                    const bool meeting_seen = sm.met != 0;
 #pragma unroll
                     for (int k = 0; k < KAD_ITEMS; k++) {
-                        const int v = vv[k];
-                        bool claimed = false;
-                        int vdeg = 0;
-                        if (v >= 0) {
-                            const unsigned long long su = ss[k];
-                            uint32_t lv = ll[k];
-                            if (lv == 0u && !sm.met) {
-                                const uint32_t old = atomicCAS(label + v, 0u, keyNext);
-                                if (old == 0u) {
-                                    claimed = true;
-                                    bits_set(bsh, bits, v);
-                                    lv = keyNext;
-                                } else {
-                                    lv = old;
-                                }
-                            }
-                            if (lv != 0u) {
-                                if ((lv & KAD_KEY) == keyNext) {
-                                    pred_next++;
-                                    const unsigned long long old = atomicAdd(sigma + v, su);
-                                    if (old + su < old) atomicOr(label + v, KAD_OVF);
-                                } else if ((lv & KAD_SIDE) != sideX) {
-                                    // v is on the other side's frontier: the searches meet.
-                                    pred_m++;
-                                    sm.met = 1;
-                                    if (!(lv & KAD_INM)) atomicOr(label + v, KAD_INM);
-                                    const unsigned long long old = atomicAdd(sigma2 + v, su);
-                                    if (old + su < old) atomicOr(label + v, KAD_OVF2);
-                                }
-                            }
-                            if (claimed) vdeg = __ldg(a.rp + v + 1) - __ldg(a.rp + v);
+                        claimed[k] = false;
+                        if (vv[k] >= 0 && ll[k] == 0u && !meeting_seen) {
+                            const uint32_t old = atomicCAS(label + vv[k], 0u, keyNext);
+                            claimed[k] = (old == 0u);
+                            ll[k] = claimed[k] ? keyNext : old;
                         }
-                        const unsigned mask = __ballot_sync(FULL_MASK, claimed);
+                    }
+                    unsigned long long prev[KAD_ITEMS];
+                    int kind[KAD_ITEMS]; // 0 none, 1 next level of X, 2 other side's frontier
+#pragma unroll
+                    for (int k = 0; k < KAD_ITEMS; k++) {
+                        kind[k] = 0;
+                        prev[k] = 0;
+                        const int v = vv[k];
+                        const uint32_t lv = ll[k];
+                        if (v < 0 || lv == 0u) continue;
+                        if (claimed[k]) bits_set(bsh, bits, v);
+                        if ((lv & KAD_KEY) == keyNext) {
+                            kind[k] = 1;
+                            prev[k] = atomicAdd(sigma + v, ss[k]);
+                        } else if ((lv & KAD_SIDE) != sideX) {
+                            // v is on the other side's frontier: the searches meet.
+                            kind[k] = 2;
+                            if (!(lv & KAD_INM)) atomicOr(label + v, KAD_INM);
+                            prev[k] = atomicAdd(sigma2 + v, ss[k]);
+                        }
+                    }
+                    int vdeg[KAD_ITEMS];
+#pragma unroll
+                    for (int k = 0; k < KAD_ITEMS; k++)
+                        vdeg[k] = claimed[k] ? __ldg(a.rp + vv[k] + 1) - __ldg(a.rp + vv[k]) : 0;
+#pragma unroll
+                    for (int k = 0; k < KAD_ITEMS; k++) {
+                        if (kind[k] == 1) {
+                            pred_next++;
+                            if (prev[k] + ss[k] < prev[k]) atomicOr(label + vv[k], KAD_OVF);
+                        } else if (kind[k] == 2) {
+                            pred_m++;
+                            sm.met = 1;
+                            if (prev[k] + ss[k] < prev[k]) atomicOr(label + vv[k], KAD_OVF2);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < KAD_ITEMS; k++) {
+                        const unsigned mask = __ballot_sync(FULL_MASK, claimed[k]);
                         if (mask) {
                             const int leader = __ffs(mask) - 1;
                             int pos0 = 0;
                             if (lane == leader) pos0 = atomicAdd(&sm.tail[X], __popc(mask));
                             pos0 = __shfl_sync(FULL_MASK, pos0, leader);
-                            if (claimed) {
+                            if (claimed[k]) {
                                 const int pos = pos0 + __popc(mask & lanemask_lt());
                                 if (pos + tailY < n)
-                                    list[phys(X, pos, n)] = v;
+                                    list[phys(X, pos, n)] = vv[k];
                                 else
                                     kad_set_err(a.ctl, KAD_DERR_FRONTIER);
                             }
-                            const unsigned long long ds = warp_sum_u64((unsigned long long)vdeg);
+                            const unsigned long long ds = warp_sum_u64((unsigned long long)vdeg[k]);
                             if (lane == 0) atomicAdd(&sm.next_dsum, ds);
                         }
                     }
@@ -951,16 +968,30 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             sm.tmark = now;
         }
         // ---------------------------------------------------- reset the slot
+        // Every vertex this sample labelled is on the list: clear its label, path
+        // count and bitmap word.  sigma2 is nonzero only on the meeting set, which
+        // lies in the non-expanding side's final frontier.
         {
             const int t0 = min(sm.tail[0], n), t1 = min(sm.tail[1], n - t0);
-            for (int j = tid; j < t0 + t1; j += BLOCK) {
-                const int pos = (j < t0) ? j : n - 1 - (j - t0);
-                const int v = __ldcg(list + pos);
-                const uint32_t lv = kad_ld_u32(label + v);
-                label[v] = 0u;
-                sigma[v] = 0ull;
-                bits_clear_word(bsh, bits, v >> 5); // every set bit of this word belongs to a listed vertex
-                if (lv & KAD_INM) sigma2[v] = 0ull;
+            const int tot = t0 + t1;
+            for (int j0 = tid; j0 < tot; j0 += 4 * BLOCK) {
+                int vr[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int j = j0 + k * BLOCK;
+                    vr[k] = (j < tot) ? __ldcg(list + ((j < t0) ? j : n - 1 - (j - t0))) : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (vr[k] < 0) continue;
+                    label[vr[k]] = 0u;
+                    sigma[vr[k]] = 0ull;
+                    bits_clear_word(bsh, bits, vr[k] >> 5); // every set bit of the word is a listed vertex
+                }
+            }
+            if (D > 0) {
+                const int Y = 1 - X;
+                for (int j = sm.fb[Y] + tid; j < sm.fe[Y]; j += BLOCK) sigma2[__ldcg(list + phys(Y, j, n))] = 0ull;
             }
         }
         __threadfence_block();
