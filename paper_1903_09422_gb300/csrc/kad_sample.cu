@@ -258,13 +258,17 @@ __device__ __forceinline__ void emit(const SampleArgs &a, int32_t *row, int D, i
 // sum of sigma(p) exceeds r (Appendix C.1: the path is rebuilt from G and the
 // distance labels).  Called by one warp; every lane returns the same choice.
 
-// Scan adj(cur) 4 x 32 arcs per pass (all loads of a pass issued first).
+// Scan adj(cur) 4 x 32 arcs per pass (all loads of a pass issued first).  Rows
+// of up to 32 arcs read the labels directly; longer rows filter through the
+// bitmap first.  The chosen predecessor's row bounds are fetched together with
+// its path count, ready for the next step.
 __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *label, bool bsh, const uint32_t *bits,
                                            const unsigned long long *sigma, int z, int d, int rsC, int reC,
-                                           unsigned long long r, int &p_sel, unsigned long long &s_sel,
-                                           unsigned long long &w_trace) {
+                                           unsigned long long r, int &p_sel, unsigned long long &s_sel, int &rs_sel,
+                                           int &re_sel, unsigned long long &w_trace) {
     const int lane = threadIdx.x & 31;
     const uint32_t key = (z ? KAD_SIDE : 0u) | (uint32_t)d; // level d-1
+    const bool direct = reC - rsC <= 32;
     unsigned long long carry = 0;
     for (int base = rsC; base < reC; base += 128) {
         int pp[4];
@@ -274,23 +278,39 @@ __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *
             const int e = base + 32 * k + lane;
             pp[k] = (e < reC) ? __ldg(a.col + e) : -1;
         }
+        if (direct) {
 #pragma unroll
-        for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? bits_ld(bsh, bits, pp[k] >> 5) : 0u;
+            for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? kad_ld_u32(label + pp[k]) : 0u;
+        } else {
 #pragma unroll
-        for (int k = 0; k < 4; k++)
-            lp[k] = (pp[k] >= 0 && ((lp[k] >> (pp[k] & 31)) & 1u)) ? kad_ld_u32(label + pp[k]) : 0u;
+            for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? bits_ld(bsh, bits, pp[k] >> 5) : 0u;
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                lp[k] = (pp[k] >= 0 && ((lp[k] >> (pp[k] & 31)) & 1u)) ? kad_ld_u32(label + pp[k]) : 0u;
+        }
+        unsigned long long wk[4];
+        int rk[4], ek[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            unsigned long long wgt = 0;
-            if (pp[k] >= 0 && (lp[k] & KAD_KEY) == key)
-                wgt = (lp[k] & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + pp[k]);
-            const unsigned long long incl = warp_incl_sat_scan(wgt);
+            wk[k] = 0;
+            rk[k] = ek[k] = 0;
+            if (pp[k] >= 0 && (lp[k] & KAD_KEY) == key) {
+                wk[k] = (lp[k] & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + pp[k]);
+                rk[k] = __ldg(a.rp + pp[k]);
+                ek[k] = __ldg(a.rp + pp[k] + 1);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const unsigned long long incl = warp_incl_sat_scan(wk[k]);
             const unsigned long long cum = kad_sat_add(carry, incl);
             const unsigned hit = __ballot_sync(FULL_MASK, pp[k] >= 0 && cum > r);
             if (hit) {
                 const int fl = __ffs(hit) - 1;
                 p_sel = __shfl_sync(FULL_MASK, pp[k], fl);
-                s_sel = __shfl_sync(FULL_MASK, wgt, fl);
+                s_sel = __shfl_sync(FULL_MASK, wk[k], fl);
+                rs_sel = __shfl_sync(FULL_MASK, rk[k], fl);
+                re_sel = __shfl_sync(FULL_MASK, ek[k], fl);
                 if (lane == 0) w_trace += (unsigned long long)(base + 32 * k + fl - rsC + 1);
                 return;
             }
@@ -622,21 +642,68 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 }
                 __syncthreads();
                 const long long np = (long long)fx * (long long)fy;
-                int probes = 0;
-                for (long long p = tid; p < np; p += BLOCK) {
-                    const int i = (int)(p % fx), j = (int)(p / fx);
-                    const int w = __ldcg(list + phys(Y, yb + j, n));
-                    const int u = sm.uid[i], rsU = sm.rs[i], reU = sm.off[i];
-                    const int rsW = __ldg(a.rp + w), reW = __ldg(a.rp + w + 1);
-                    const bool adj = (reU - rsU <= reW - rsW) ? row_contains(a.col, rsU, reU, w, probes)
-                                                              : row_contains(a.col, rsW, reW, u, probes);
-                    if (adj) {
+                // four pairs per thread and step, their binary searches interleaved
+                for (long long p0 = tid; p0 < np; p0 += 4ll * BLOCK) {
+                    int pi[4], pw[4], lo[4], hi[4], key[4];
+                    bool hit[4];
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const long long p = p0 + (long long)k * BLOCK;
+                        pi[k] = -1;
+                        pw[k] = -1;
+                        hit[k] = false;
+                        lo[k] = hi[k] = key[k] = 0;
+                        if (p < np) {
+                            pi[k] = (int)(p % fx);
+                            pw[k] = __ldcg(list + phys(Y, yb + (int)(p / fx), n));
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        if (pw[k] < 0) continue;
+                        const int rsW = __ldg(a.rp + pw[k]), reW = __ldg(a.rp + pw[k] + 1);
+                        const int rsU = sm.rs[pi[k]], reU = sm.off[pi[k]];
+                        if (reU - rsU <= reW - rsW) { // search w in the row of u
+                            lo[k] = rsU;
+                            hi[k] = reU;
+                            key[k] = pw[k];
+                        } else { // search u in the row of w
+                            lo[k] = rsW;
+                            hi[k] = reW;
+                            key[k] = sm.uid[pi[k]];
+                        }
+                    }
+                    for (int step = 0; step < 32; step++) {
+                        bool any = false;
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {
+                            if (hit[k] || lo[k] >= hi[k]) continue;
+                            any = true;
+                            const int mid = (lo[k] + hi[k]) >> 1;
+                            const int v = __ldg(a.col + mid);
+                            if (v < key[k])
+                                lo[k] = mid + 1;
+                            else if (v > key[k])
+                                hi[k] = mid;
+                            else
+                                hit[k] = true;
+                        }
+                        if (!any) break;
+                    }
+                    unsigned long long prev[4];
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        prev[k] = 0;
+                        if (!hit[k]) continue;
+                        atomicOr(label + pw[k], KAD_INM);
+                        prev[k] = atomicAdd(sigma2 + pw[k], sm.sig[pi[k]]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        if (!hit[k]) continue;
                         pred_m++;
                         sm.met = 1;
-                        const unsigned long long su = sm.sig[i];
-                        atomicOr(label + w, KAD_INM);
-                        const unsigned long long old = atomicAdd(sigma2 + w, su);
-                        if (old + su < old) atomicOr(label + w, KAD_OVF2);
+                        if (prev[k] + sm.sig[pi[k]] < prev[k]) atomicOr(label + pw[k], KAD_OVF2);
                     }
                 }
                 __syncthreads();
@@ -911,16 +978,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 const unsigned long long gX = (lm & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + mid);
                 const unsigned long long gY = (lm & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + mid);
                 if (lane == 0) emit(a, out, D, (X == 0) ? dX : dY, mid);
+                const int rsM = __ldg(a.rp + mid), reM = __ldg(a.rp + mid + 1);
                 for (int z = 0; z < 2; z++) {
                     int cur = mid, d = (z == X) ? dX : dY;
                     unsigned long long sc = (z == X) ? gX : gY;
+                    int rsC = rsM, reC = reM;
                     while (d >= 1) {
                         unsigned long long r = 0;
                         if (lane == 0) r = st.uniform(sc, a.ctl);
                         r = __shfl_sync(FULL_MASK, r, 0);
-                        int p_sel = -1;
+                        int p_sel = -1, rs_sel = 0, re_sel = 0;
                         unsigned long long s_sel = 0;
-                        const int rsC = __ldg(a.rp + cur), reC = __ldg(a.rp + cur + 1);
                         const int ls = (d <= KAD_MAXLV) ? sm.lvs[z][d - 1] : 0;
                         const int lcnt = (d <= KAD_MAXLV) ? sm.lvs[z][d] - ls : KAD_LCAP + 1;
                         if (d == 1) {
@@ -930,8 +998,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                         } else if (!(a.debug & KAD_DEBUG_TRACE_SCAN) && reC - rsC > KAD_DEG_SCAN && lcnt <= KAD_LCAP) {
                             trace_from_level<BLOCK>(a, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel,
                                                     s_sel, sm.acc[4]);
+                            if (p_sel >= 0) {
+                                rs_sel = __ldg(a.rp + p_sel);
+                                re_sel = __ldg(a.rp + p_sel + 1);
+                            }
                         } else {
-                            trace_scan(a, label, bsh, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, sm.acc[4]);
+                            trace_scan(a, label, bsh, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, rs_sel, re_sel,
+                                       sm.acc[4]);
                         }
                         if (p_sel < 0) {
                             if (lane == 0) kad_set_err(a.ctl, KAD_DERR_TRACE);
@@ -941,6 +1014,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                         if (lane == 0 && d >= 1) emit(a, out, D, z == 0 ? d : D - d, p_sel);
                         cur = p_sel;
                         sc = s_sel;
+                        rsC = rs_sel;
+                        reC = re_sel;
                     }
                 }
             }
