@@ -44,7 +44,7 @@ BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=0, 
 # DRAM traffic of the adaptive-phase sampling kernel measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), bytes per computed sample, for
 # the kernel source it was taken on; None when not measured for the current kernel.
-NCU_TRAFFIC_PER_SAMPLE = {}
+NCU_TRAFFIC_PER_SAMPLE = {"rmat20": 342000}  # profiles/k_sample_rmat20_dram.md
 
 
 def alg_bytes(counters):

@@ -45,6 +45,14 @@
 
 namespace {
 
+// atomic add with release semantics at GPU scope: every write of this thread
+// before it is visible to whoever observes the new value
+__device__ __forceinline__ unsigned int atom_add_release(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -128,6 +136,7 @@ struct Smem {
     unsigned long long wtmp64[BLOCK / 32];
     unsigned long long bin_lo[16], bin_hi[16];
     int tail[2], fb[2], fe[2], lev[2];
+    int root_rs[2];
     int lvs[2][KAD_MAXLV + 2]; // logical list start of level l, l <= KAD_MAXLV + 1
     unsigned long long dsum[2];
     unsigned long long next_dsum;
@@ -583,8 +592,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 sm.lev[0] = sm.lev[1] = 0;
                 sm.lvs[0][0] = sm.lvs[1][0] = 0;
                 sm.lvs[0][1] = sm.lvs[1][1] = 1;
-                sm.dsum[0] = (unsigned long long)(__ldg(a.rp + s + 1) - __ldg(a.rp + s));
-                sm.dsum[1] = (unsigned long long)(__ldg(a.rp + t + 1) - __ldg(a.rp + t));
+                sm.root_rs[0] = __ldg(a.rp + s);
+                sm.root_rs[1] = __ldg(a.rp + t);
+                sm.dsum[0] = (unsigned long long)(__ldg(a.rp + s + 1) - sm.root_rs[0]);
+                sm.dsum[1] = (unsigned long long)(__ldg(a.rp + t + 1) - sm.root_rs[1]);
                 sm.D = -1; // searching
             }
             __threadfence_block();
@@ -713,7 +724,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             for (int cb = fb; cb < expand_end; cb += BLOCK) {
                 const int cnt = min(BLOCK, fe - cb);
                 int d = 0;
-                if (tid < cnt) {
+                if (levX == 0) {
+                    // level 0 is the root alone: its row is known and sigma = 1
+                    if (tid == 0) {
+                        sm.rs[0] = sm.root_rs[X];
+                        sm.sig[0] = 1ull;
+                        d = (int)sm.dsum[X];
+                    }
+                } else if (tid < cnt) {
                     const int u = __ldcg(list + phys(X, cb + tid, n));
                     const int rs = __ldg(a.rp + u), re = __ldg(a.rp + u + 1);
                     const uint32_t lu = kad_ld_u32(label + u);
@@ -1100,14 +1118,16 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             }
         } else if (a.mode == KAD_MODE_RING) {
             if (tid == 0) {
-                __threadfence();
+                // Publish this sample's path (release); the block completing an
+                // epoch tries the closer role.  Epochs completed before the L table
+                // arrived are closed by the next completion (or the next launch).
                 const unsigned long long e = idx / a.epoch;
-                const unsigned int old = atomicAdd(&a.epoch_done[e % a.ring], 1u);
-                kad_fence_sc();
-                int tc = (old + 1u == a.epoch) ? 1 : 0;
-                // epochs left unclosed while the L table was on its way
-                if (!tc && *(volatile int *)&a.ctl->ltab_ready && *(volatile int *)&a.ctl->closer == 0)
-                    tc = epoch_ready(a, *(volatile unsigned long long *)&a.ctl->closed) ? 1 : 0;
+                const unsigned int old = atom_add_release(&a.epoch_done[e % a.ring], 1u);
+                int tc = 0;
+                if (old + 1u == a.epoch) {
+                    kad_fence_sc();
+                    tc = 1;
+                }
                 sm.try_close = tc;
             }
             __syncthreads();
