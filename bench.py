@@ -44,7 +44,7 @@ BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=0, 
 # DRAM traffic of the adaptive-phase sampling kernel measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum), bytes per computed sample, for
 # the kernel source it was taken on; None when not measured for the current kernel.
-NCU_TRAFFIC_PER_SAMPLE = {"rmat20": 342000}  # profiles/k_sample_rmat20_dram.md
+NCU_TRAFFIC_PER_SAMPLE = {}
 
 
 def alg_bytes(counters):
@@ -201,6 +201,121 @@ def run_reference(args):
     return 0
 
 
+def serve_graphs(count, seed=20261203):
+    """count graphs: generator = idx mod 3 (R-MAT, grid + shortcuts, hyperbolic),
+    target size n = round(10^(4 + 2u)), u uniform in [0, 1) (log-uniform 1e4..1e6)."""
+    from paper_1903_09422_gb300 import gen
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n_t = int(round(10 ** (4 + 2 * rng.random())))
+        kind = i % 3
+        if kind == 0:
+            g = gen.rmat(max(4, int(round(np.log2(n_t)))), 16, seed=i + 1)
+        elif kind == 1:
+            g = gen.grid(max(8, int(round(np.sqrt(n_t)))), seed=i + 1)
+        else:
+            g = gen.hyperbolic(n_t, seed=i + 1)
+        out.append(g)
+    return out
+
+
+def open_loop(kad, graphs, workers, qg, qe, qseed, arrivals):
+    """Submit query q at arrivals[q] seconds (Poisson process) to a server with
+    `workers` workers; return (makespan s, latencies ms incl. queueing, samples)."""
+    import threading
+    Q = len(arrivals)
+    with kad.Server(workers=workers) as S:
+        gids = [S.add_graph(g, trusted=True) for g in graphs]
+        for q in range(min(5, Q)):  # warm-up
+            S.wait(S.submit(gids[qg[q]], qe[q], 0.1, int(qseed[q]), want_bc=False))
+        tickets = [None] * Q
+
+        def submitter():
+            start = time.perf_counter()
+            for q in range(Q):
+                dt = arrivals[q] - (time.perf_counter() - start)
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[q] = S.submit(gids[qg[q]], qe[q], 0.1, int(qseed[q]), want_bc=False)
+
+        t_start = time.perf_counter()
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, samples = [], 0
+        for q in range(Q):
+            while tickets[q] is None:
+                time.sleep(0.0002)
+            r = S.wait(tickets[q])
+            lat.append(r["latency_ms"])
+            samples += r["tau"] + r["calib_samples"]
+        makespan = time.perf_counter() - t_start
+        th.join()
+    return makespan, lat, samples
+
+
+def run_serve(args):
+    """Serving stream: resident graphs, Poisson arrivals at several loads.  Each
+    load runs the same arrival sequence twice: 'plain' (one query at a time with
+    every sampling slot of the GPU, first come first served) and 'served' (the
+    query server with several workers: queries overlap on the device)."""
+    import torch
+    from paper_1903_09422_gb300 import build, kad
+    torch.cuda.set_device(0)
+    build.build()
+    t0 = time.perf_counter()
+    graphs = serve_graphs(args.serve_graphs)
+    gen_s = time.perf_counter() - t0
+    rng = np.random.default_rng(7)
+    Q = args.serve_queries
+    qg = rng.integers(0, len(graphs), Q)
+    qe = np.array([0.05, 0.02, 0.01])[rng.integers(0, 3, Q)]
+    qseed = np.arange(1, Q + 1)
+
+    # capacity of plain: back-to-back queries, one at a time
+    plain_n = min(Q, args.serve_plain)
+    with kad.Server(workers=1) as P:
+        gids = [P.add_graph(g, trusted=True) for g in graphs]
+        for q in range(min(5, Q)):  # warm-up
+            P.wait(P.submit(gids[qg[q]], qe[q], 0.1, int(qseed[q]), want_bc=False))
+        t0 = time.perf_counter()
+        for q in range(plain_n):
+            P.wait(P.submit(gids[qg[q]], qe[q], 0.1, int(qseed[q]), want_bc=False))
+        plain_s = time.perf_counter() - t0
+    plain_qps = plain_n / plain_s
+
+    def summary(makespan, lat, samples):
+        return {"queries_per_s": Q / makespan, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "samples_per_s": samples / makespan}
+
+    sweep = []
+    for load in [float(x) for x in args.serve_load.split(",")]:
+        lam = load * plain_qps
+        arrivals = np.cumsum(np.random.default_rng(11).exponential(1.0 / lam, Q))
+        row = {"load": load, "arrival_qps": lam}
+        row["plain"] = summary(*open_loop(kad, graphs, 1, qg, qe, qseed, arrivals))
+        row["served"] = summary(*open_loop(kad, graphs, args.serve_workers, qg, qe, qseed, arrivals))
+        print(json.dumps({"load": load, "plain": row["plain"], "served": row["served"]}), file=sys.stderr, flush=True)
+        sweep.append(row)
+    top = sweep[-1]
+    line = {
+        "metric": METRIC, "value": top["served"]["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": Q,
+        "warmup": 5, "ms_per_step": 1000.0 / top["served"]["queries_per_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"serving stream: {len(graphs)} resident graphs (R-MAT / grid+shortcuts / hyperbolic, "
+                               f"n log-uniform 1e4..1e6), {Q} queries per arm and load, Poisson arrivals at "
+                               f"{args.serve_load} x the plain back-to-back throughput, eps in {{.05,.02,.01}}, "
+                               f"delta .1, seed = query index + 1",
+                   "workers": args.serve_workers,
+                   "value": "served queries/s at the highest load"},
+        "plain_capacity_qps": plain_qps,
+        "sweep": sweep,
+        "graph_generation_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,10 +330,17 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
     ap.add_argument("--eps", type=float, default=None, help="override the workload's eps (experiments)")
+    ap.add_argument("--serve-graphs", type=int, default=64)
+    ap.add_argument("--serve-queries", type=int, default=1000, help="queries per arm and load")
+    ap.add_argument("--serve-plain", type=int, default=400, help="queries timed for the one-at-a-time baseline")
+    ap.add_argument("--serve-load", default="0.5,1,2,4", help="arrival rates, as multiples of plain queries/s")
+    ap.add_argument("--serve-workers", type=int, default=4)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
     rank, world, dist = dist_setup(args.gpus)
@@ -368,6 +490,8 @@ def main():
             "phase_share": phase_share(results),
             "phase_cycles_per_sample": {k: round(v / max(1, sum(r["samples_computed"] for r in results)))
                                         for k, v in phase_total(results).items()},
+            "kernel_variant": f"{r0['block_threads_used']} threads x {r0['blocks_per_sm_used']} blocks/SM, "
+                              f"{r0['slots_used']} slots",
             "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
             "clocks": clk,
             "cpu_baseline": cpu,

@@ -87,7 +87,10 @@ typedef struct {
                             0 forces the general path; results do not depend on it) */
     int32_t block_threads; /* threads per sampling block: 128, 256, 512 or 1024 (0 = 512) */
     int32_t blocks_per_sm; /* resident sampling blocks per SM the kernel is built for: 128 threads 4|8,
-                              256: 2|4, 512: 1|2, 1024: 1 (0 = 4, 2, 2, 1 respectively) */
+                              256: 2|4, 512: 1|2, 1024: 1 (0 = 4, 2, 2, 1 respectively).  When both
+                              are 0 the graph's first run picks the fastest of 512x2, 256x4, 256x2
+                              and 1024x1 by timing the same query, truncated after 4 epochs, under
+                              each (the autotuner; graphs under 16384 vertices keep 512x2) */
     uint32_t flags;      /* KAD_RUN_* */
     uint32_t debug;      /* KAD_DEBUG_* (tests only; results do not depend on it) */
     uint32_t max_epochs; /* > 0: stop after this many epochs even if the stop rule does not hold
@@ -96,6 +99,8 @@ typedef struct {
 } kad_options;
 
 #define KAD_RUN_TIMING 1u      /* fill kad_result.t_* with CUDA-event times of each phase */
+#define KAD_RUN_NO_AUTOTUNE 2u /* keep the default kernel variant instead of timing the candidates on the
+                                  graph's first run (when block_threads and blocks_per_sm are both 0) */
 #define KAD_DEBUG_TRACE_SCAN 1u    /* trace-back always scans the current vertex's adjacency */
 #define KAD_DEBUG_SMEM_BITMAP 2u /* keep the labelled-vertex bitmap in shared memory when it fits */
 #define KAD_DEBUG_FULL_SCAN 4u   /* the meeting round always scans the expanding side's rows */
@@ -134,11 +139,14 @@ typedef struct {
     uint32_t ads_launches;     /* sampling-kernel launches */
     int32_t slots_used;        /* concurrent samples (resident sampling blocks) */
     uint32_t kernel_launches;  /* kernels this call launched (all phases) */
-    uint32_t reserved_;
+    int32_t block_threads_used, blocks_per_sm_used; /* sampling-kernel variant used */
     /* SM cycles the sampling blocks spent per stage of a sample, summed over
        blocks and samples: pair draw and set-up, BFS, meeting draw, trace-back
        and output, slot reset, epoch bookkeeping and close */
     uint64_t phase_cycles[6];
+    /* KAD_RUN_TIMING, host milliseconds: t_host (the whole call), t_setup (from
+       the call's entry until its first device work is enqueued) */
+    double t_host_ms, t_setup_ms;
 } kad_result;
 
 /*
@@ -217,6 +225,56 @@ kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row_ptr, const
  */
 kad_status kad_eval_fg(int32_t n, const uint32_t *counts, const uint32_t *c0, const double *ltab, int32_t nclass,
                        uint64_t tau, uint64_t omega, double *f, double *g);
+
+/* ------------------------------------------------------------------ serving
+ * A query server keeps many graphs resident and answers KADABRA queries on them
+ * concurrently: `workers` host threads each run one query at a time on their own
+ * CUDA stream, so queries overlap on the device.  A query starts with
+ * `slots_per_query` sampling blocks, or by default with the device's resident
+ * blocks divided by the number of queries running or waiting at that moment (at
+ * most `workers`): alone it gets the whole device, under load a share of it.  A submitted query waits until a worker is free and its device-memory
+ * footprint (slot scratch + epoch ring + per-vertex arrays) fits the budget next
+ * to the queries in flight; a smaller query may start before a larger one that
+ * is still waiting for memory (continuous batching).  A query's result does not
+ * depend on what else is running: it equals kad_run's on the same graph.
+ * The paper has no serving layer; this is the batched-query use of its method.
+ */
+typedef struct kad_server kad_server;
+
+typedef struct {
+    int32_t workers;         /* queries in flight at once (0 = 4) */
+    int32_t slots_per_query; /* sampling blocks per query (0 = adaptive share of the resident blocks) */
+    int64_t hbm_budget;      /* bytes the footprints of in-flight queries may add up to (0 = half of the
+                                device memory free at creation); a query larger than the budget runs alone */
+    int32_t block_threads;   /* sampling-kernel variant for every query (0 = 512 threads, 2 blocks/SM) */
+    int32_t blocks_per_sm;
+} kad_server_options;
+
+/* Starts the worker threads on the current CUDA device.  opt NULL = defaults. */
+kad_status kad_server_create(const kad_server_options *opt, kad_server **out);
+
+/* Copies a graph to the server's device (as kad_graph_create; host arrays); *gid names it. */
+kad_status kad_server_add_graph(kad_server *s, int32_t n, const int32_t *row_ptr, const int32_t *col, uint32_t flags,
+                                int32_t *gid);
+
+/* Queues a query.  bc_out (host, n doubles, or NULL) receives b~ when the query
+   completes and must stay valid until kad_wait returns for the ticket. */
+kad_status kad_submit(kad_server *s, int32_t gid, double eps, double delta, uint64_t seed, double *bc_out,
+                      uint64_t *ticket);
+
+/* *done = 1 once the query has finished (successfully or not). */
+kad_status kad_poll(kad_server *s, uint64_t ticket, int *done);
+
+/* Waits up to timeout_ns (< 0 = no limit) for the query; on completion fills *out
+   (its bc pointer is ignored; see kad_submit), the time it waited for a worker and
+   its submit-to-finish latency in milliseconds (either may be NULL), releases the
+   ticket and returns the query's status.  KAD_ERR_TIMEOUT if it has not finished. */
+kad_status kad_wait(kad_server *s, uint64_t ticket, int64_t timeout_ns, kad_result *out, double *queue_ms,
+                    double *latency_ms);
+
+/* Stops the workers after their current queries (queued ones end KAD_ERR_CANCELLED)
+   and releases every graph and buffer.  NULL is a no-op. */
+void kad_server_free(kad_server *s);
 
 /* Human-readable text of a status. Never NULL. */
 const char *kad_status_string(kad_status s);

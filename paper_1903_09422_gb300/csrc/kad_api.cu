@@ -18,7 +18,14 @@
 #include <string.h>
 #include <time.h>
 
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
 #include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
 
 #include "kad_internal.cuh"
 
@@ -27,9 +34,16 @@ namespace {
 const int kDefaultEpoch = 1000;   // N = 1000 (Appendix C.2)
 const int kDefaultCalibDiv = 100; // tau0 ~ omega / 100
 const int kDefaultMcap = 256;
+const int32_t kTuneMinVertices = 16384;   // smaller graphs keep the default variant
+const uint32_t kTuneEpochs = 4;           // epochs of the truncated query timed per candidate
+const uint64_t kTuneSeed = 0x6b61646162726174ull;
 
 struct Workspace {
-    int slots = 0; // sampling slots allocated
+    int slots = 0;            // sampling slots the scratch was last zeroed for
+    size_t scratch_elems = 0; // allocated entries of label / sigma / sigma2 / list (slots x n)
+    size_t bits_words = 0;    // allocated words of the bitmap
+    size_t n_cap = 0;         // allocated entries of cnt / c0
+    size_t path_elems = 0;    // allocated entries of the epoch ring's path rows
     uint32_t *label = nullptr;
     unsigned long long *sigma = nullptr, *sigma2 = nullptr;
     int32_t *list = nullptr;
@@ -42,6 +56,7 @@ struct Workspace {
     uint8_t *pflag = nullptr;
     // per-vertex state
     uint32_t *cnt = nullptr, *c0 = nullptr;
+    double *bc = nullptr;         // bc output staged here before a copy to host memory
     // per-class state
     size_t nclass_cap = 0;
     int32_t *classmax = nullptr;
@@ -62,6 +77,8 @@ struct Workspace {
     int32_t *h_cmax = nullptr;
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_launch = nullptr, ev_aux = nullptr;
+    cudaEvent_t tev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr}; // timing events
+    bool tev_ok = false;
 };
 
 } // namespace
@@ -72,6 +89,7 @@ struct kad_graph {
     int32_t vd = 0, ncomp = 0;
     bool poisoned = false;
     Workspace ws;
+    int tuned_threads = 0, tuned_per_sm = 0; // sampling-kernel variant chosen for this graph (0 = not yet)
 };
 
 namespace {
@@ -87,6 +105,8 @@ void ws_free_slots(Workspace &w) {
     w.list = nullptr;
     w.bits = nullptr;
     w.slots = 0;
+    w.scratch_elems = 0;
+    w.bits_words = 0;
 }
 
 void ws_free_all(Workspace &w) {
@@ -96,6 +116,7 @@ void ws_free_all(Workspace &w) {
     cudaFree(w.pflag);
     cudaFree(w.cnt);
     cudaFree(w.c0);
+    cudaFree(w.bc);
     cudaFree(w.classmax);
     cudaFree(w.ltab);
     cudaFree(w.hist);
@@ -108,6 +129,8 @@ void ws_free_all(Workspace &w) {
     if (w.aux) cudaStreamDestroy(w.aux);
     if (w.ev_launch) cudaEventDestroy(w.ev_launch);
     if (w.ev_aux) cudaEventDestroy(w.ev_aux);
+    for (auto &x : w.tev)
+        if (x) cudaEventDestroy(x);
     w = Workspace();
 }
 
@@ -116,6 +139,23 @@ template <typename T> cudaError_t dalloc(T **p, size_t count) {
     if (count == 0) count = 1;
     return cudaMalloc((void **)p, count * sizeof(T));
 }
+
+// Workspace buffers grow in stream order (cudaMallocAsync / cudaFreeAsync on the
+// run's stream): unlike cudaMalloc / cudaFree these never synchronise the whole
+// device, so one run growing its workspace does not stall runs on other streams.
+template <typename T> cudaError_t dalloc_s(T **p, size_t count, cudaStream_t st) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMallocAsync((void **)p, count * sizeof(T), st);
+}
+
+template <typename T> void dfree_s(T *&p, cudaStream_t st) {
+    if (p) cudaFreeAsync((void *)p, st);
+    p = nullptr;
+}
+
+// geometric growth, so that a workspace meeting ever larger queries reallocates rarely
+size_t grow(size_t need, size_t have) { return (need > have + have / 2) ? need : have + have / 2; }
 
 // bytes of sampling scratch per slot and vertex: label 4, sigma 8, sigma2 8, list 4
 // (plus one bit of the labelled-vertex bitmap)
@@ -139,82 +179,104 @@ kad_status fail(kad_graph *g, cudaError_t e) {
     return s;
 }
 
-kad_status ensure_slots(kad_graph *g, int slots, cudaStream_t st) {
-    Workspace &w = g->ws;
+// Slot scratch for `slots` samples of a graph with n vertices.  The scratch is
+// all zero between samples (each sample clears what it labelled), so a
+// workspace moves between graphs without re-zeroing; only new or dirty
+// (error-interrupted) scratch is cleared.
+kad_status ensure_slots(kad_graph *g, Workspace &w, int slots, cudaStream_t st) {
     const size_t n = (size_t)g->gd.n;
-    if (w.slots >= slots && !w.dirty) return KAD_OK;
-    if (w.slots < slots) {
-        ws_free_slots(w);
-        const size_t cnt = (size_t)slots * n;
-        if (dalloc(&w.label, cnt) != cudaSuccess || dalloc(&w.sigma, cnt) != cudaSuccess ||
-            dalloc(&w.sigma2, cnt) != cudaSuccess || dalloc(&w.list, cnt) != cudaSuccess ||
-            dalloc(&w.bits, (size_t)slots * nwords(g->gd.n)) != cudaSuccess) {
+    const size_t need = (size_t)slots * n, need_bits = (size_t)slots * nwords(g->gd.n);
+    bool clear = w.dirty;
+    if (need > w.scratch_elems || need_bits > w.bits_words) {
+        const size_t ne = grow(need, w.scratch_elems), nb = grow(need_bits, w.bits_words);
+        dfree_s(w.label, st);
+        dfree_s(w.sigma, st);
+        dfree_s(w.sigma2, st);
+        dfree_s(w.list, st);
+        dfree_s(w.bits, st);
+        w.scratch_elems = w.bits_words = 0;
+        if (dalloc_s(&w.label, ne, st) != cudaSuccess || dalloc_s(&w.sigma, ne, st) != cudaSuccess ||
+            dalloc_s(&w.sigma2, ne, st) != cudaSuccess || dalloc_s(&w.list, ne, st) != cudaSuccess ||
+            dalloc_s(&w.bits, nb, st) != cudaSuccess) {
             cudaGetLastError();
-            ws_free_slots(w);
+            dfree_s(w.label, st);
+            dfree_s(w.sigma, st);
+            dfree_s(w.sigma2, st);
+            dfree_s(w.list, st);
+            dfree_s(w.bits, st);
             return KAD_ERR_OOM;
         }
-        w.slots = slots;
+        w.scratch_elems = ne;
+        w.bits_words = nb;
+        clear = true;
     }
-    const size_t cnt = (size_t)w.slots * n;
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(w.label, 0, cnt * 4, st)) != cudaSuccess) return fail(g, e);
-    if ((e = cudaMemsetAsync(w.sigma, 0, cnt * 8, st)) != cudaSuccess) return fail(g, e);
-    if ((e = cudaMemsetAsync(w.sigma2, 0, cnt * 8, st)) != cudaSuccess) return fail(g, e);
-    if ((e = cudaMemsetAsync(w.bits, 0, (size_t)w.slots * nwords(g->gd.n) * 4, st)) != cudaSuccess) return fail(g, e);
-    w.dirty = false;
+    w.slots = slots;
+    if (clear) {
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(w.label, 0, w.scratch_elems * 4, st)) != cudaSuccess) return fail(g, e);
+        if ((e = cudaMemsetAsync(w.sigma, 0, w.scratch_elems * 8, st)) != cudaSuccess) return fail(g, e);
+        if ((e = cudaMemsetAsync(w.sigma2, 0, w.scratch_elems * 8, st)) != cudaSuccess) return fail(g, e);
+        if ((e = cudaMemsetAsync(w.bits, 0, w.bits_words * 4, st)) != cudaSuccess) return fail(g, e);
+        w.dirty = false;
+    }
     return KAD_OK;
 }
 
-kad_status ensure_rows(kad_graph *g, size_t rows, int32_t cap) {
-    Workspace &w = g->ws;
-    if (w.rows >= rows && w.cap == cap) return KAD_OK;
-    cudaFree(w.paths);
-    cudaFree(w.plen);
-    cudaFree(w.pflag);
-    w.paths = nullptr;
-    w.plen = nullptr;
-    w.pflag = nullptr;
+kad_status ensure_rows(Workspace &w, size_t rows, int32_t cap, cudaStream_t st) {
+    if (w.rows >= rows && w.path_elems >= rows * (size_t)cap) return KAD_OK;
+    const size_t nr = grow(rows, w.rows), ne = grow(rows * (size_t)cap, w.path_elems);
+    dfree_s(w.paths, st);
+    dfree_s(w.plen, st);
+    dfree_s(w.pflag, st);
     w.rows = 0;
-    if (dalloc(&w.paths, rows * (size_t)cap) != cudaSuccess || dalloc(&w.plen, rows) != cudaSuccess ||
-        dalloc(&w.pflag, rows) != cudaSuccess) {
+    w.path_elems = 0;
+    if (dalloc_s(&w.paths, ne, st) != cudaSuccess || dalloc_s(&w.plen, nr, st) != cudaSuccess ||
+        dalloc_s(&w.pflag, nr, st) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(w.paths);
-        cudaFree(w.plen);
-        cudaFree(w.pflag);
-        w.paths = nullptr;
-        w.plen = nullptr;
-        w.pflag = nullptr;
+        dfree_s(w.paths, st);
+        dfree_s(w.plen, st);
+        dfree_s(w.pflag, st);
         return KAD_ERR_OOM;
     }
-    w.rows = rows;
+    w.rows = nr;
     w.cap = cap;
+    w.path_elems = ne;
     return KAD_OK;
 }
 
-kad_status ensure_fixed(kad_graph *g, size_t nclass, size_t ring) {
-    Workspace &w = g->ws;
+kad_status ensure_fixed(kad_graph *g, Workspace &w, size_t nclass, size_t ring, cudaStream_t st) {
     const size_t n = (size_t)g->gd.n;
-    if (!w.cnt) {
-        if (dalloc(&w.cnt, n) != cudaSuccess || dalloc(&w.c0, n) != cudaSuccess || dalloc(&w.ctl, 1) != cudaSuccess ||
-            dalloc(&w.work, KAD_WORK_WORDS) != cudaSuccess) {
+    if (!w.ctl) {
+        if (dalloc(&w.ctl, 1) != cudaSuccess || dalloc(&w.work, KAD_WORK_WORDS) != cudaSuccess) {
             cudaGetLastError();
             return KAD_ERR_OOM;
         }
     }
-    if (w.nclass_cap < nclass) {
-        cudaFree(w.classmax);
-        cudaFree(w.ltab);
-        cudaFree(w.hist);
-        w.classmax = nullptr;
-        w.ltab = nullptr;
-        w.hist = nullptr;
-        w.nclass_cap = 0;
-        if (dalloc(&w.classmax, nclass) != cudaSuccess || dalloc(&w.ltab, nclass) != cudaSuccess ||
-            dalloc(&w.hist, nclass) != cudaSuccess) {
+    if (w.n_cap < n) {
+        const size_t nn = grow(n, w.n_cap);
+        dfree_s(w.cnt, st);
+        dfree_s(w.c0, st);
+        dfree_s(w.bc, st);
+        w.n_cap = 0;
+        if (dalloc_s(&w.cnt, nn, st) != cudaSuccess || dalloc_s(&w.c0, nn, st) != cudaSuccess ||
+            dalloc_s(&w.bc, nn, st) != cudaSuccess) {
             cudaGetLastError();
             return KAD_ERR_OOM;
         }
-        w.nclass_cap = nclass;
+        w.n_cap = nn;
+    }
+    if (w.nclass_cap < nclass) {
+        const size_t nc = grow(nclass < 4096 ? 4096 : nclass, w.nclass_cap);
+        dfree_s(w.classmax, st);
+        dfree_s(w.ltab, st);
+        dfree_s(w.hist, st);
+        w.nclass_cap = 0;
+        if (dalloc_s(&w.classmax, nc, st) != cudaSuccess || dalloc_s(&w.ltab, nc, st) != cudaSuccess ||
+            dalloc_s(&w.hist, nc, st) != cudaSuccess) {
+            cudaGetLastError();
+            return KAD_ERR_OOM;
+        }
+        w.nclass_cap = nc;
     }
     if (!w.aux) {
         if (cudaStreamCreateWithFlags(&w.aux, cudaStreamNonBlocking) != cudaSuccess ||
@@ -225,6 +287,7 @@ kad_status ensure_fixed(kad_graph *g, size_t nclass, size_t ring) {
         }
     }
     if (w.hpage_cap < nclass) {
+        nclass = w.nclass_cap; // size the pinned pages like the device arrays (grown geometrically)
         if (w.hpage) cudaFreeHost(w.hpage);
         if (w.h_ltab) cudaFreeHost(w.h_ltab);
         if (w.h_cmax) cudaFreeHost(w.h_cmax);
@@ -244,10 +307,10 @@ kad_status ensure_fixed(kad_graph *g, size_t nclass, size_t ring) {
         w.hpage_cap = nclass;
     }
     if (w.ring_cap < ring) {
-        cudaFree(w.epoch_done);
-        w.epoch_done = nullptr;
+        ring = grow(ring, w.ring_cap);
+        dfree_s(w.epoch_done, st);
         w.ring_cap = 0;
-        if (dalloc(&w.epoch_done, ring) != cudaSuccess) {
+        if (dalloc_s(&w.epoch_done, ring, st) != cudaSuccess) {
             cudaGetLastError();
             return KAD_ERR_OOM;
         }
@@ -315,14 +378,24 @@ double run_tau_star(const uint32_t *hist, uint64_t tau0, double eps, double delt
     return hi;
 }
 
+// Timing events of a run: five events owned by the workspace, created on the
+// first timed run and kept (creating and destroying events on every query of a
+// serving process takes driver locks that the other workers' calls wait on).
 struct Events {
-    cudaEvent_t e[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t *e = nullptr;
     bool on = false;
-    void create(bool want) {
-        on = want;
-        if (on)
-            for (auto &x : e)
-                if (cudaEventCreate(&x) != cudaSuccess) on = false;
+    Events(Workspace &w, bool want) {
+        if (!want) return;
+        if (!w.tev_ok) {
+            for (auto &x : w.tev)
+                if (!x && cudaEventCreate(&x) != cudaSuccess) {
+                    cudaGetLastError();
+                    return;
+                }
+            w.tev_ok = true;
+        }
+        e = w.tev;
+        on = true;
     }
     void record(int i, cudaStream_t st) {
         if (on) cudaEventRecord(e[i], st);
@@ -332,16 +405,34 @@ struct Events {
         if (!on || cudaEventElapsedTime(&t, e[a], e[b]) != cudaSuccess) return 0.0;
         return (double)t;
     }
-    ~Events() {
-        for (auto &x : e)
-            if (x) cudaEventDestroy(x);
-    }
 };
 
+// Device facts that do not change while the process runs, cached (a serving
+// process asks for them on every query).
 int device_sms(int dev) {
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms > 0 ? sms : 1;
+    static std::mutex mu;
+    static int cache[64] = {0};
+    if (dev < 0 || dev >= 64) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cache[dev]) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = sms > 0 ? sms : 1;
+    }
+    return cache[dev];
+}
+
+int blocks_per_sm_cached(int dev, int threads, int per_sm, size_t dyn_smem) {
+    static std::mutex mu;
+    static std::unordered_map<unsigned long long, int> cache;
+    const unsigned long long key = ((unsigned long long)(dev & 0xff) << 56) | ((unsigned long long)threads << 40) |
+                                   ((unsigned long long)per_sm << 32) | (unsigned long long)(dyn_smem & 0xffffffffu);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const int b = kad_sample_max_blocks_per_sm(threads, per_sm, dyn_smem);
+    cache[key] = b;
+    return b;
 }
 
 struct LaunchCfg {
@@ -375,16 +466,19 @@ void choose_bitmap_home(LaunchCfg &c, int32_t n, int dev) {
 }
 
 // Number of sampling slots: all resident blocks, capped by a share of free memory.
-int resolve_slots(kad_graph *g, const kad_options &o, const LaunchCfg &cfg) {
+int resolve_slots(kad_graph *g, const Workspace &w, const kad_options &o, const LaunchCfg &cfg) {
     int slots = o.slots;
     if (slots <= 0) {
-        const int per_sm = kad_sample_max_blocks_per_sm(cfg.threads, cfg.per_sm, cfg.dyn_smem);
+        const int per_sm = blocks_per_sm_cached(g->device, cfg.threads, cfg.per_sm, cfg.dyn_smem);
         slots = device_sms(g->device) * (per_sm > 0 ? per_sm : 1);
     }
+    // the free-memory cap matters only when the scratch would have to grow
+    const bool fits = (size_t)slots * (size_t)g->gd.n <= w.scratch_elems &&
+                      (size_t)slots * nwords(g->gd.n) <= w.bits_words;
     size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+    if (!fits && cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
         const size_t per = kSlotBytesPerVertex * (size_t)g->gd.n;
-        size_t budget = fr / 3 + (size_t)g->ws.slots * per; // what we already hold counts too
+        size_t budget = fr / 3 + w.scratch_elems * (kSlotBytesPerVertex - 1) + w.bits_words * 4; // held counts too
         const size_t maxb = (size_t)64 << 30;
         if (budget > maxb) budget = maxb;
         const size_t cap = per ? budget / per : (size_t)slots;
@@ -419,7 +513,7 @@ double now_ms() {
     return (double)t.tv_sec * 1e3 + (double)t.tv_nsec * 1e-6;
 }
 
-kad_status launch_phase(kad_graph *g, const SampleArgs &a, int blocks, const LaunchCfg &cfg,
+kad_status launch_phase(kad_graph *g, Workspace &w, const SampleArgs &a, int blocks, const LaunchCfg &cfg,
                         unsigned long long next0, cudaStream_t st) {
     k_set_ctl<<<1, 1, 0, st>>>(a.ctl, next0);
     cudaError_t e = cudaGetLastError();
@@ -427,48 +521,89 @@ kad_status launch_phase(kad_graph *g, const SampleArgs &a, int blocks, const Lau
     SampleArgs b = a;
     b.bits_smem = cfg.dyn_smem ? 1 : 0;
     e = kad_launch_sample(b, blocks, cfg.threads, cfg.per_sm, cfg.dyn_smem, st);
-    if (e == cudaSuccess) e = cudaEventRecord(g->ws.ev_launch, st);
+    if (e == cudaSuccess && w.ev_launch) e = cudaEventRecord(w.ev_launch, st);
     if (e != cudaSuccess) return fail(g, e);
     return KAD_OK;
 }
 
-SampleArgs base_args(kad_graph *g, uint64_t seed) {
+SampleArgs base_args(kad_graph *g, const Workspace &w, uint64_t seed) {
     SampleArgs a;
     memset(&a, 0, sizeof(a));
     a.rp = g->gd.rp;
     a.col = g->gd.col;
     a.comp = g->gd.comp;
     a.n = g->gd.n;
-    a.label = g->ws.label;
-    a.sigma = g->ws.sigma;
-    a.sigma2 = g->ws.sigma2;
-    a.list = g->ws.list;
-    a.bits = g->ws.bits;
+    a.label = w.label;
+    a.sigma = w.sigma;
+    a.sigma2 = w.sigma2;
+    a.list = w.list;
+    a.bits = w.bits;
     a.nw = (int32_t)nwords(g->gd.n);
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
-    a.ctl = g->ws.ctl;
-    a.work = g->ws.work;
+    a.ctl = w.ctl;
+    a.work = w.work;
     a.mcap = kDefaultMcap;
     return a;
 }
 
 int32_t path_cap(const kad_graph *g) { return (g->vd - 2 > 1) ? g->vd - 2 : 1; }
 
-kad_status read_ctl(kad_graph *g, KadCtl *h, cudaStream_t st) {
-    cudaError_t e = cudaMemcpyAsync(h, g->ws.ctl, sizeof(KadCtl), cudaMemcpyDeviceToHost, st);
+kad_status read_ctl(kad_graph *g, Workspace &w, KadCtl *h, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(h, w.ctl, sizeof(KadCtl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(g, e);
     if (h->err) {
-        g->ws.dirty = true;
+        w.dirty = true;
         return KAD_ERR_INTERNAL;
     }
     return KAD_OK;
 }
 
-kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaStream_t st, const kad_options *opt_in,
-                    double *d_bc, uint32_t *d_counts, kad_result *out, bool host_out) {
+kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64_t seed, cudaStream_t st,
+                    const kad_options *opt_in, double *d_bc, uint32_t *d_counts, kad_result *out, bool host_out);
+
+// The autotuner: the first run on a graph that leaves the kernel variant to the
+// library runs the same query, truncated after kTuneEpochs epochs, once under
+// each candidate variant and keeps the fastest for the graph.  Every variant
+// computes the same samples, so the choice changes speed only.
+kad_status autotune(kad_graph *g, Workspace &w, double eps, double delta, const kad_options &o, cudaStream_t st,
+                    LaunchCfg &best) {
+    best = resolve_cfg(o);
+    if (!g->tuned_threads && g->gd.n < kTuneMinVertices) { // too small to matter
+        g->tuned_threads = best.threads;
+        g->tuned_per_sm = best.per_sm;
+    }
+    if (!g->tuned_threads) {
+        static const int cand[4][2] = {{512, 2}, {256, 4}, {256, 2}, {1024, 1}};
+        double best_ms = 0.0;
+        for (int c = 0; c < 4; c++) {
+            kad_options o2 = o;
+            o2.block_threads = cand[c][0];
+            o2.blocks_per_sm = cand[c][1];
+            o2.max_epochs = kTuneEpochs;
+            o2.flags |= KAD_RUN_TIMING | KAD_RUN_NO_AUTOTUNE;
+            kad_result r;
+            memset(&r, 0, sizeof(r));
+            const kad_status s = run_impl(g, w, eps, delta, kTuneSeed, st, &o2, nullptr, nullptr, &r, false);
+            if (s != KAD_OK) return s;
+            if (c == 0 || r.t_total_ms < best_ms) {
+                best_ms = r.t_total_ms;
+                g->tuned_threads = cand[c][0];
+                g->tuned_per_sm = cand[c][1];
+            }
+        }
+    }
+    best.threads = g->tuned_threads;
+    best.per_sm = g->tuned_per_sm;
+    best.dyn_smem = 0;
+    return KAD_OK;
+}
+
+kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64_t seed, cudaStream_t st,
+                    const kad_options *opt_in, double *d_bc, uint32_t *d_counts, kad_result *out, bool host_out) {
     if (!g || !out) return KAD_ERR_INVALID_ARG;
+    const double t_entry = now_ms();
     if (g->poisoned) return KAD_ERR_CUDA;
     if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0)) return KAD_ERR_INVALID_ARG;
     kad_options o;
@@ -487,9 +622,12 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     if (o.max_epochs && o.max_epochs < max_epochs) max_epochs = o.max_epochs;
     const size_t nclass = (size_t)tau0 + 1;
     if (nclass > (size_t)0x7fffffff || omega > ((uint64_t)1 << 40)) return KAD_ERR_INVALID_ARG;
+    kad_status s;
     LaunchCfg cfg = resolve_cfg(o);
+    if (o.block_threads == 0 && o.blocks_per_sm == 0 && !(o.flags & KAD_RUN_NO_AUTOTUNE))
+        if ((s = autotune(g, w, eps, delta, o, st, cfg)) != KAD_OK) return s;
     if (o.debug & KAD_DEBUG_SMEM_BITMAP) choose_bitmap_home(cfg, g->gd.n, g->device);
-    const int slots = resolve_slots(g, o, cfg);
+    const int slots = resolve_slots(g, w, o, cfg);
     const int32_t cap = path_cap(g);
     // Epoch ring: enough to hold the whole run when it fits in about 1 GiB of
     // path rows, else as many epochs as fit (at least 2).
@@ -500,16 +638,14 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     if (ring < 2) ring = 2;
     if (ring > max_epochs && max_epochs >= 2 && !o.ring_epochs) ring = max_epochs;
 
-    kad_status s;
-    if ((s = ensure_fixed(g, nclass, ring)) != KAD_OK) return s;
-    if ((s = ensure_slots(g, slots, st)) != KAD_OK) return s;
-    if ((s = ensure_rows(g, ring * N, cap)) != KAD_OK) return s;
-    Workspace &w = g->ws;
+    if ((s = ensure_fixed(g, w, nclass, ring, st)) != KAD_OK) return s;
+    if ((s = ensure_slots(g, w, slots, st)) != KAD_OK) return s;
+    if ((s = ensure_rows(w, ring * N, cap, st)) != KAD_OK) return s;
 
-    Events ev;
-    ev.create((o.flags & KAD_RUN_TIMING) != 0);
+    Events ev(w, (o.flags & KAD_RUN_TIMING) != 0);
     cudaError_t e;
     ev.record(0, st);
+    const double t_setup = now_ms() - t_entry;
 
     // ---- one launch: calibration samples (phase 1), then adaptive samples (phase 0)
     if ((e = cudaMemsetAsync(w.c0, 0, (size_t)n * 4, st)) != cudaSuccess) return fail(g, e);
@@ -524,7 +660,7 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     *(volatile int *)&w.hpage->calib_flag = 0;
     w.hpage->one = 1;
 
-    SampleArgs a = base_args(g, seed);
+    SampleArgs a = base_args(g, w, seed);
     a.mcap = (o.mcap < 0) ? kDefaultMcap : o.mcap;
     a.debug = o.debug;
     a.mode = KAD_MODE_RING;
@@ -551,7 +687,7 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     a.i1 = (uint64_t)((ring < max_epochs) ? ring : max_epochs) * N;
     a.k_end = a.i1 / N;
     ev.record(2, st);
-    if ((s = launch_phase(g, a, slots, cfg, 0, st)) != KAD_OK) return s;
+    if ((s = launch_phase(g, w, a, slots, cfg, 0, st)) != KAD_OK) return s;
     ev.record(3, st);
     uint32_t launches = 1;
     uint64_t issued = a.i1; // adaptive samples handed to launches so far
@@ -559,21 +695,30 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     // ---- host: wait for the calibration histogram (the kernel keeps sampling),
     // then tau* by bisection, the L table and class presence, uploaded on a side
     // stream; the kernel's closer starts once ltab_ready is set.
+    // The flag lives in mapped host memory: poll it with plain reads, look at the
+    // launch's event only every 64th time (or after 2 ms), and back off with short
+    // sleeps, so that waiting threads do not crowd the driver.
     const double t_wait0 = now_ms();
-    for (;;) {
+    for (unsigned it = 0;; it++) {
         if (*(volatile int *)&w.hpage->calib_flag) break;
+        const double waited = now_ms() - t_wait0;
+        if (waited > 0.05) {
+            struct timespec ts = {0, waited > 2.0 ? 50000 : 5000};
+            nanosleep(&ts, nullptr);
+        }
+        if ((it & 63) != 63 && waited < 2.0) continue;
         const cudaError_t q = cudaEventQuery(w.ev_launch);
         if (q == cudaSuccess) { // the launch ended; the flag must be set by now
             if (*(volatile int *)&w.hpage->calib_flag) break;
             KadCtl hc0;
-            kad_status s0 = read_ctl(g, &hc0, st);
-            g->ws.dirty = true;
+            kad_status s0 = read_ctl(g, w, &hc0, st);
+            w.dirty = true;
             return (s0 != KAD_OK) ? s0 : KAD_ERR_INTERNAL;
         }
         if (q != cudaErrorNotReady) return fail(g, q);
         if (now_ms() - t_wait0 > kCalibWaitMs) {
             cudaStreamSynchronize(st);
-            g->ws.dirty = true;
+            w.dirty = true;
             return KAD_ERR_TIMEOUT;
         }
     }
@@ -596,7 +741,7 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     // what is pending
     KadCtl hc;
     for (;;) {
-        if ((s = read_ctl(g, &hc, st)) != KAD_OK) return s;
+        if ((s = read_ctl(g, w, &hc, st)) != KAD_OK) return s;
         if (hc.stop) break;
         if (launches > 4 * max_epochs + 8) return KAD_ERR_INTERNAL; // cannot happen: tau >= omega stops
         const uint64_t closed = hc.closed;
@@ -606,7 +751,7 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
         a.i0 = issued;
         a.i1 = i1;
         a.k_end = i1 / N;
-        if ((s = launch_phase(g, a, slots, cfg, 0, st)) != KAD_OK) return s;
+        if ((s = launch_phase(g, w, a, slots, cfg, 0, st)) != KAD_OK) return s;
         launches++;
         issued = i1;
     }
@@ -615,16 +760,9 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     if ((e = cudaMemcpyAsync(work, w.work, sizeof(work), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(g, e);
 
     // ---- outputs
-    double *bc_dst = d_bc;
-    if (host_out && out->bc) {
-        if ((e = cudaMalloc(&bc_dst, (size_t)n * 8)) != cudaSuccess) return fail(g, e);
-    }
-    if (bc_dst) {
-        if ((e = kad_launch_finalize(w.cnt, n, tau, bc_dst, st)) != cudaSuccess) {
-            if (host_out) cudaFree(bc_dst);
-            return fail(g, e);
-        }
-    }
+    double *bc_dst = (host_out && out->bc) ? w.bc : d_bc;
+    if (bc_dst)
+        if ((e = kad_launch_finalize(w.cnt, n, tau, bc_dst, st)) != cudaSuccess) return fail(g, e);
     if (!host_out && d_counts)
         if ((e = cudaMemcpyAsync(d_counts, w.cnt, (size_t)n * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
             return fail(g, e);
@@ -638,7 +776,6 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     }
     ev.record(4, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (host_out && out->bc) cudaFree(bc_dst);
     if (e != cudaSuccess) return fail(g, e);
 
     out->tau = tau;
@@ -655,6 +792,8 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
     for (int i = 0; i < 6; i++) out->phase_cycles[i] = work[8 + i];
     out->ads_launches = launches;
     out->slots_used = slots;
+    out->block_threads_used = cfg.threads;
+    out->blocks_per_sm_used = cfg.per_sm;
     // k_hist_init, then k_set_ctl + k_sample per launch, and k_finalize if b~ was wanted
     out->kernel_launches = 1u + 2u * launches + (bc_dst ? 1u : 0u);
     if (ev.on) {
@@ -662,6 +801,8 @@ kad_status run_impl(kad_graph *g, double eps, double delta, uint64_t seed, cudaS
         out->t_calib_ms = t_calib; // host wall time from launch to the histogram (sampling continues meanwhile)
         out->t_ads_ms = ev.ms(2, 4);
         out->t_ads_kernel_ms = ev.ms(2, 3);
+        out->t_setup_ms = t_setup;
+        out->t_host_ms = now_ms() - t_entry;
     }
     return KAD_OK;
 }
@@ -705,6 +846,129 @@ kad_status create_common(int32_t n, int64_t m, const int32_t *rp, const int32_t 
     g->ncomp = nc;
     *out = g;
     return KAD_OK;
+}
+
+} // namespace
+
+// ================================================================ serving
+namespace {
+
+struct ServerQuery {
+    uint64_t ticket = 0;
+    int32_t gid = 0;
+    double eps = 0, delta = 0;
+    uint64_t seed = 0;
+    double *bc_out = nullptr;
+    size_t footprint = 0;
+    kad_result result;
+    kad_status status = KAD_OK;
+    bool done = false;
+    double t_submit = 0, t_start = 0, t_end = 0;
+};
+
+} // namespace
+
+struct kad_server {
+    int device = 0;
+    int workers = 4, slots_per_query = 0, threads = 512, per_sm = 2;
+    int resident = 1; // sampling blocks the device holds at once
+    size_t budget = 0, inflight = 0;
+    std::vector<kad_graph *> graphs;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ServerQuery *> pending;
+    std::unordered_map<uint64_t, ServerQuery *> queries;
+    uint64_t next_ticket = 1;
+    int running = 0; // queries on workers
+    bool stopping = false;
+    std::vector<std::thread> pool;
+};
+
+namespace {
+
+// Device memory a query needs on top of its graph: slot scratch, the epoch ring
+// and the per-vertex and per-class arrays (the same sizes run_impl allocates).
+size_t query_footprint(const kad_graph *g, double eps, double delta, int slots) {
+    const size_t n = (size_t)g->gd.n;
+    const uint64_t omega = run_omega(g->vd, eps, delta);
+    const uint64_t tau0 = run_calib(omega, kDefaultEpoch, kDefaultCalibDiv);
+    const uint64_t epochs = (omega + kDefaultEpoch - 1) / kDefaultEpoch;
+    const size_t cap = (size_t)path_cap(g);
+    const size_t row_bytes = cap * 4 + 5;
+    size_t ring = (size_t)epochs;
+    const size_t max_ring = ((size_t)1 << 30) / ((size_t)kDefaultEpoch * row_bytes);
+    if (ring > max_ring) ring = max_ring;
+    if (ring < 2) ring = 2;
+    return (size_t)slots * n * kSlotBytesPerVertex + ring * kDefaultEpoch * row_bytes + 8 * n +
+           ((size_t)tau0 + 1) * 16;
+}
+
+void server_worker(kad_server *S) {
+    cudaSetDevice(S->device);
+    cudaStream_t st = nullptr;
+    const bool have_stream = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    Workspace ws;
+    for (;;) {
+        ServerQuery *q = nullptr;
+        int slots = 1;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            for (;;) {
+                if (S->stopping) break;
+                // Slots: a fixed number per query, or (adaptive) the resident blocks
+                // shared among the queries that will be in flight, so that a query
+                // arriving at an idle server gets the whole device.
+                int share = S->running + (int)S->pending.size();
+                if (share > S->workers) share = S->workers;
+                if (share < 1) share = 1;
+                slots = S->slots_per_query > 0 ? S->slots_per_query : S->resident / share;
+                if (slots < 1) slots = 1;
+                // the first queued query whose footprint fits next to those in flight;
+                // a query larger than the whole budget runs when nothing else does
+                for (auto it = S->pending.begin(); it != S->pending.end(); ++it) {
+                    const size_t fp = query_footprint(S->graphs[(*it)->gid], (*it)->eps, (*it)->delta, slots);
+                    if (S->inflight + fp <= S->budget || S->running == 0) {
+                        q = *it;
+                        q->footprint = fp;
+                        S->pending.erase(it);
+                        break;
+                    }
+                }
+                if (q) break;
+                S->cv_work.wait(lk);
+            }
+            if (!q) break;
+            S->inflight += q->footprint;
+            S->running++;
+        }
+        q->t_start = now_ms();
+        kad_graph *g = S->graphs[q->gid];
+        kad_options o;
+        fill_defaults(&o);
+        o.block_threads = S->threads;
+        o.blocks_per_sm = S->per_sm;
+        o.slots = slots;
+        o.flags |= KAD_RUN_NO_AUTOTUNE | KAD_RUN_TIMING;
+        kad_result r;
+        memset(&r, 0, sizeof(r));
+        r.bc = q->bc_out;
+        const kad_status status =
+            have_stream ? run_impl(g, ws, q->eps, q->delta, q->seed, st, &o, nullptr, nullptr, &r, true) : KAD_ERR_CUDA;
+        const double t_end = now_ms();
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            q->t_end = t_end;
+            q->result = r;
+            q->status = status;
+            q->done = true;
+            S->inflight -= q->footprint;
+            S->running--;
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+    ws_free_all(ws);
+    if (have_stream) cudaStreamDestroy(st);
 }
 
 } // namespace
@@ -755,12 +1019,14 @@ kad_status kad_graph_info(const kad_graph *g, int32_t *n, int64_t *m, int32_t *v
 
 kad_status kad_run(kad_graph *g, double eps, double delta, uint64_t seed, kad_stream_t stream, const kad_options *opt,
                    kad_result *out) {
-    return run_impl(g, eps, delta, seed, (cudaStream_t)stream, opt, nullptr, nullptr, out, true);
+    if (!g) return KAD_ERR_INVALID_ARG;
+    return run_impl(g, g->ws, eps, delta, seed, (cudaStream_t)stream, opt, nullptr, nullptr, out, true);
 }
 
 kad_status kad_run_device(kad_graph *g, double eps, double delta, uint64_t seed, kad_stream_t stream,
                           const kad_options *opt, double *d_bc, uint32_t *d_counts, kad_result *out) {
-    return run_impl(g, eps, delta, seed, (cudaStream_t)stream, opt, d_bc, d_counts, out, false);
+    if (!g) return KAD_ERR_INVALID_ARG;
+    return run_impl(g, g->ws, eps, delta, seed, (cudaStream_t)stream, opt, d_bc, d_counts, out, false);
 }
 
 kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint64_t i0, int64_t count,
@@ -781,12 +1047,12 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
         fill_defaults(&o);
     LaunchCfg cfg = resolve_cfg(o);
     if (o.debug & KAD_DEBUG_SMEM_BITMAP) choose_bitmap_home(cfg, g->gd.n, g->device);
-    int slots = resolve_slots(g, o, cfg);
+    Workspace &w = g->ws;
+    int slots = resolve_slots(g, w, o, cfg);
     if ((int64_t)slots > count) slots = (int)count;
     kad_status s;
-    if ((s = ensure_fixed(g, 1, 2)) != KAD_OK) return s;
-    if ((s = ensure_slots(g, slots, st)) != KAD_OK) return s;
-    Workspace &w = g->ws;
+    if ((s = ensure_fixed(g, w, 1, 2, st)) != KAD_OK) return s;
+    if ((s = ensure_slots(g, w, slots, st)) != KAD_OK) return s;
     int32_t *d_paths = nullptr, *d_plen = nullptr, *d_s = nullptr, *d_t = nullptr, *d_D = nullptr;
     uint8_t *d_flag = nullptr;
     unsigned long long *d_sst = nullptr;
@@ -800,7 +1066,7 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
         goto out;
     }
     {
-        SampleArgs a = base_args(g, seed);
+        SampleArgs a = base_args(g, w, seed);
         a.mcap = (o.mcap < 0) ? kDefaultMcap : o.mcap;
         a.debug = o.debug;
         a.domain = domain;
@@ -823,7 +1089,7 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
             s = fail(g, e);
             goto out;
         }
-        if ((s = launch_phase(g, a, slots, cfg, i0, st)) != KAD_OK) goto out;
+        if ((s = launch_phase(g, w, a, slots, cfg, i0, st)) != KAD_OK) goto out;
         uint8_t *hflag = (uint8_t *)malloc(c);
         unsigned long long hw[KAD_WORK_WORDS];
         if (!hflag) {
@@ -848,7 +1114,7 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
         if (work_out)
             for (int i = 0; i < 6; i++) work_out[i] = hw[i];
         KadCtl hc;
-        s = read_ctl(g, &hc, st);
+        s = read_ctl(g, w, &hc, st);
     }
 out:
     cudaFree(d_paths);
@@ -889,6 +1155,133 @@ kad_status kad_eval_fg(int32_t n, const uint32_t *counts, const uint32_t *c0, co
     cudaFree(df);
     cudaFree(dg);
     return s;
+}
+
+kad_status kad_server_create(const kad_server_options *opt, kad_server **out) {
+    if (!out) return KAD_ERR_INVALID_ARG;
+    *out = nullptr;
+    kad_server *S = new (std::nothrow) kad_server();
+    if (!S) return KAD_ERR_OOM;
+    cudaGetDevice(&S->device);
+    if (opt && opt->workers > 0) S->workers = opt->workers;
+    if (S->workers > 64) S->workers = 64;
+    if (opt && opt->block_threads > 0) S->threads = opt->block_threads;
+    if (opt && opt->blocks_per_sm > 0) S->per_sm = opt->blocks_per_sm;
+    kad_options o;
+    fill_defaults(&o);
+    o.block_threads = S->threads;
+    o.blocks_per_sm = S->per_sm;
+    const LaunchCfg cfg = resolve_cfg(o);
+    S->threads = cfg.threads;
+    S->per_sm = cfg.per_sm;
+    const int resident = device_sms(S->device) * (kad_sample_max_blocks_per_sm(cfg.threads, cfg.per_sm, 0) > 0
+                                                      ? kad_sample_max_blocks_per_sm(cfg.threads, cfg.per_sm, 0)
+                                                      : 1);
+    S->resident = resident > 0 ? resident : 1;
+    S->slots_per_query = (opt && opt->slots_per_query > 0) ? opt->slots_per_query : 0; // 0 = adaptive
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    S->budget = (opt && opt->hbm_budget > 0) ? (size_t)opt->hbm_budget : fr / 2;
+    for (int i = 0; i < S->workers; i++) S->pool.emplace_back(server_worker, S);
+    *out = S;
+    return KAD_OK;
+}
+
+kad_status kad_server_add_graph(kad_server *S, int32_t n, const int32_t *row_ptr, const int32_t *col, uint32_t flags,
+                                int32_t *gid) {
+    if (!S || !gid) return KAD_ERR_INVALID_ARG;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(S->device);
+    kad_graph *g = nullptr;
+    const kad_status st = kad_graph_create(n, row_ptr, col, flags, nullptr, &g);
+    cudaSetDevice(cur);
+    if (st != KAD_OK) return st;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->graphs.push_back(g);
+    *gid = (int32_t)S->graphs.size() - 1;
+    return KAD_OK;
+}
+
+kad_status kad_submit(kad_server *S, int32_t gid, double eps, double delta, uint64_t seed, double *bc_out,
+                      uint64_t *ticket) {
+    if (!S || !ticket) return KAD_ERR_INVALID_ARG;
+    if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0)) return KAD_ERR_INVALID_ARG;
+    ServerQuery *q = new (std::nothrow) ServerQuery();
+    if (!q) return KAD_ERR_OOM;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (gid < 0 || gid >= (int32_t)S->graphs.size() || S->stopping) {
+            delete q;
+            return KAD_ERR_INVALID_ARG;
+        }
+        q->ticket = S->next_ticket++;
+        q->gid = gid;
+        q->eps = eps;
+        q->delta = delta;
+        q->seed = seed;
+        q->bc_out = bc_out;
+        memset(&q->result, 0, sizeof(q->result));
+        q->t_submit = now_ms();
+        S->queries[q->ticket] = q;
+        S->pending.push_back(q);
+        *ticket = q->ticket;
+    }
+    S->cv_work.notify_one();
+    return KAD_OK;
+}
+
+kad_status kad_poll(kad_server *S, uint64_t ticket, int *done) {
+    if (!S || !done) return KAD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->queries.find(ticket);
+    if (it == S->queries.end()) return KAD_ERR_INVALID_ARG;
+    *done = it->second->done ? 1 : 0;
+    return KAD_OK;
+}
+
+kad_status kad_wait(kad_server *S, uint64_t ticket, int64_t timeout_ns, kad_result *out, double *queue_ms,
+                    double *latency_ms) {
+    if (!S) return KAD_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->queries.find(ticket);
+    if (it == S->queries.end()) return KAD_ERR_INVALID_ARG;
+    ServerQuery *q = it->second;
+    if (timeout_ns < 0) {
+        S->cv_done.wait(lk, [q] { return q->done; });
+    } else if (!S->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), [q] { return q->done; })) {
+        return KAD_ERR_TIMEOUT;
+    }
+    if (out) {
+        double *keep_bc = out->bc;
+        *out = q->result;
+        out->bc = keep_bc;
+    }
+    if (queue_ms) *queue_ms = q->t_start - q->t_submit;
+    if (latency_ms) *latency_ms = q->t_end - q->t_submit;
+    const kad_status st = q->status;
+    S->queries.erase(it);
+    delete q;
+    return st;
+}
+
+void kad_server_free(kad_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stopping = true;
+        for (ServerQuery *q : S->pending) {
+            q->status = KAD_ERR_CANCELLED;
+            q->done = true;
+        }
+        S->pending.clear();
+    }
+    S->cv_work.notify_all();
+    S->cv_done.notify_all();
+    for (auto &t : S->pool) t.join();
+    for (auto &kv : S->queries) delete kv.second;
+    for (kad_graph *g : S->graphs) kad_graph_free(g);
+    delete S;
 }
 
 const char *kad_status_string(kad_status s) {

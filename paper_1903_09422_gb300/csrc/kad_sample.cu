@@ -778,6 +778,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     // Claims first (all CAS of the pass in flight together), then
                     // the path-count pushes, then the new vertices' degrees: each
                     // kind of access overlaps across the items instead of chaining.
+                    // Does any arc of this pass reach the other side's frontier?  Then
+                    // the round meets, and no new vertex needs claiming.
+                    int reaches_y = 0;
+#pragma unroll
+                    for (int k = 0; k < KAD_ITEMS; k++)
+                        if (vv[k] >= 0 && ll[k] != 0u && (ll[k] & KAD_SIDE) != sideX) reaches_y = 1;
+                    if (__syncthreads_or(reaches_y)) sm.met = 1;
                     bool claimed[KAD_ITEMS];
                     const bool meeting_seen = sm.met != 0;
 #pragma unroll

@@ -331,9 +331,9 @@ static double hyp_expected_degree(int64_t n, double alpha, double R, int Q) {
 double gg_hyperbolic_radius(int64_t n, double avg_deg, double gamma) {
     double alpha = 0.5 * (gamma - 1.0);
     double lo = 0.5, hi = 200.0;
-    for (int it = 0; it < 40; it++) {
+    for (int it = 0; it < 36; it++) {
         double mid = 0.5 * (lo + hi);
-        double k = hyp_expected_degree(n, alpha, mid, 1200);
+        double k = hyp_expected_degree(n, alpha, mid, 500);
         if (k > avg_deg)
             lo = mid;
         else

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libkad.so")
 
 KAD_GRAPH_TRUSTED = 1
 KAD_RUN_TIMING = 1
+KAD_RUN_NO_AUTOTUNE = 2
 WORK_NAMES = ("expanded", "scanned", "labelled", "pred_arcs", "trace_arcs", "increments")
 
 
@@ -42,13 +43,20 @@ class Result(ctypes.Structure):
                 ("t_total_ms", ctypes.c_double), ("t_calib_ms", ctypes.c_double), ("t_ads_ms", ctypes.c_double),
                 ("t_ads_kernel_ms", ctypes.c_double), ("ads_launches", ctypes.c_uint32),
                 ("slots_used", ctypes.c_int32), ("kernel_launches", ctypes.c_uint32),
-                ("reserved_", ctypes.c_uint32), ("phase_cycles", ctypes.c_uint64 * 6)]
+                ("block_threads_used", ctypes.c_int32), ("blocks_per_sm_used", ctypes.c_int32),
+                ("phase_cycles", ctypes.c_uint64 * 6), ("t_host_ms", ctypes.c_double), ("t_setup_ms", ctypes.c_double)]
 
 PHASE_NAMES = ("draw", "bfs", "meet", "trace", "reset", "close")
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("slots_per_query", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
 EXPORTS = ("kad_graph_create", "kad_graph_create_device", "kad_graph_free", "kad_graph_info", "kad_options_default",
            "kad_run", "kad_run_device", "kad_sample_records", "kad_sample_records_noalloc", "kad_eval_fg",
+           "kad_server_create", "kad_server_add_graph", "kad_submit", "kad_poll", "kad_wait", "kad_server_free",
            "kad_status_string", "kad_version")
 
 _lib = None
@@ -87,6 +95,18 @@ def load():
     lib.kad_sample_records_noalloc.restype = st
     lib.kad_eval_fg.argtypes = [i32, vp, vp, vp, i32, u64, u64, vp, vp]
     lib.kad_eval_fg.restype = st
+    lib.kad_server_create.argtypes = [ctypes.POINTER(ServerOptions), ctypes.POINTER(vp)]
+    lib.kad_server_create.restype = st
+    lib.kad_server_add_graph.argtypes = [vp, i32, vp, vp, u32, ctypes.POINTER(ctypes.c_int32)]
+    lib.kad_server_add_graph.restype = st
+    lib.kad_submit.argtypes = [vp, i32, dbl, dbl, u64, vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.kad_submit.restype = st
+    lib.kad_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int)]
+    lib.kad_poll.restype = st
+    lib.kad_wait.argtypes = [vp, u64, i64, ctypes.POINTER(Result), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    lib.kad_wait.restype = st
+    lib.kad_server_free.argtypes = [vp]
+    lib.kad_server_free.restype = None
     lib.kad_status_string.argtypes = [st]
     lib.kad_status_string.restype = ctypes.c_char_p
     lib.kad_version.argtypes = []
@@ -252,7 +272,8 @@ def _result_scalars(r):
     d = {k: getattr(r, k) for k in ("tau", "omega", "calib_samples", "samples_computed", "overflow_samples", "epochs",
                                     "vd_bound", "sigma_overflow", "stopped_by_omega", "tau_star", "t_total_ms",
                                     "t_calib_ms", "t_ads_ms", "t_ads_kernel_ms", "ads_launches", "slots_used",
-                                    "kernel_launches")}
+                                    "kernel_launches", "block_threads_used", "blocks_per_sm_used", "t_host_ms",
+                                    "t_setup_ms")}
     d["counters"] = dict(zip(WORK_NAMES, (int(x) for x in r.work)))
     d["phase_cycles"] = dict(zip(PHASE_NAMES, (int(x) for x in r.phase_cycles)))
     return d
@@ -273,6 +294,80 @@ def sample_records_noalloc(d_row_ptr, d_col, seed, i0, count, out, cap, domain=0
                                           out["D"].data_ptr(), out["sigma_st"].data_ptr(),
                                           out["overflow"].data_ptr(), out["paths"].data_ptr(), cap),
            "kad_sample_records_noalloc")
+
+
+class Server:
+    """Query server (kad_server): resident graphs, concurrent queries.
+
+    ctypes releases the GIL during every call, so a Python thread can submit
+    while another waits."""
+
+    def __init__(self, workers=0, slots_per_query=0, hbm_budget=0, block_threads=0, blocks_per_sm=0):
+        lib = load()
+        o = ServerOptions(workers, slots_per_query, hbm_budget, block_threads, blocks_per_sm)
+        h = ctypes.c_void_p()
+        _check(lib.kad_server_create(ctypes.byref(o), ctypes.byref(h)), "kad_server_create")
+        self._h = h
+        self._n = []
+        self._bufs = {}
+
+    def add_graph(self, csr, trusted=False):
+        rp = np.ascontiguousarray(csr.row_ptr, dtype=np.int32)
+        cl = np.ascontiguousarray(csr.col, dtype=np.int32)
+        if cl.size == 0:
+            cl = np.zeros(1, np.int32)
+        gid = ctypes.c_int32()
+        _check(load().kad_server_add_graph(self._h, rp.size - 1, rp.ctypes.data, cl.ctypes.data,
+                                           KAD_GRAPH_TRUSTED if trusted else 0, ctypes.byref(gid)),
+               "kad_server_add_graph")
+        self._n.append(rp.size - 1)
+        return gid.value
+
+    def submit(self, gid, eps, delta, seed, want_bc=True):
+        n = self._n[gid] if 0 <= gid < len(self._n) else 0  # an unknown gid is rejected by kad_submit
+        bc = np.zeros(max(n, 1), np.float64) if want_bc else None
+        t = ctypes.c_uint64()
+        _check(load().kad_submit(self._h, gid, eps, delta, seed, bc.ctypes.data if bc is not None else None,
+                                 ctypes.byref(t)), "kad_submit")
+        self._bufs[t.value] = bc
+        return t.value
+
+    def poll(self, ticket):
+        d = ctypes.c_int()
+        _check(load().kad_poll(self._h, ticket, ctypes.byref(d)), "kad_poll")
+        return bool(d.value)
+
+    def wait(self, ticket, timeout_s=None):
+        r = Result()
+        qm, lm = ctypes.c_double(), ctypes.c_double()
+        tn = -1 if timeout_s is None else int(timeout_s * 1e9)
+        st = load().kad_wait(self._h, ticket, tn, ctypes.byref(r), ctypes.byref(qm), ctypes.byref(lm))
+        if st == 5 and timeout_s is not None:
+            raise TimeoutError(f"query {ticket} still running")
+        bc = self._bufs.pop(ticket, None)
+        _check(st, "kad_wait")
+        d = _result_scalars(r)
+        d["bc"] = bc
+        d["queue_ms"] = qm.value
+        d["latency_ms"] = lm.value
+        return d
+
+    def close(self):
+        if self._h:
+            load().kad_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def eval_fg(counts, c0, ltab, tau, omega):

@@ -156,6 +156,20 @@ def test_truncated_run_matches_oracle(kad, k):
     np.testing.assert_array_equal(r["counts"], ref["counts"])
 
 
+def test_autotuner_keeps_results_and_choice(kad):
+    g = gen.rmat(15, 8, seed=6)
+    assert g.n >= 16384
+    ref = O.kadabra(g, 0.05, 0.1, 8)
+    with kad.Graph.from_csr(g) as G:
+        r1 = G.run(0.05, 0.1, 8)
+        r2 = G.run(0.05, 0.1, 8)
+    assert (r1["block_threads_used"], r1["blocks_per_sm_used"]) in {(512, 2), (256, 4), (256, 2), (1024, 1)}
+    assert (r1["block_threads_used"], r1["blocks_per_sm_used"]) == (r2["block_threads_used"], r2["blocks_per_sm_used"])
+    for r in (r1, r2):
+        assert r["tau"] == ref["tau"]
+        np.testing.assert_array_equal(r["counts"], ref["counts"])
+
+
 def test_fg_kernel_matches_oracle(kad):
     g = gen.rmat(12, 8, seed=1)
     ref = O.kadabra(g, 0.05, 0.1, 1)
