@@ -96,6 +96,10 @@ typedef struct {
     uint32_t max_epochs; /* > 0: stop after this many epochs even if the stop rule does not hold
                             (a truncated run, for comparisons on large graphs); 0 = no limit */
     uint32_t reserved;
+    int32_t share_min_arcs;    /* > 0: a BFS chunk with at least this many arcs is shared -- blocks
+                                  between two samples help expand it (0 = never share: on R-MAT
+                                  graphs sharing has measured slower than each block alone) */
+    int32_t share_max_helpers; /* helper blocks per shared chunk (0 = 16) */
 } kad_options;
 
 #define KAD_RUN_TIMING 1u      /* fill kad_result.t_* with CUDA-event times of each phase */
@@ -104,6 +108,8 @@ typedef struct {
 #define KAD_DEBUG_TRACE_SCAN 1u    /* trace-back always scans the current vertex's adjacency */
 #define KAD_DEBUG_SMEM_BITMAP 2u /* keep the labelled-vertex bitmap in shared memory when it fits */
 #define KAD_DEBUG_FULL_SCAN 4u   /* the meeting round always scans the expanding side's rows */
+#define KAD_DEBUG_NO_SHARE 8u    /* every block expands its own levels alone (no shared expansions) */
+#define KAD_DEBUG_SHARE_ALL 16u  /* share every level with at least 256 arcs (tests the shared path) */
 
 /* Initialises *opt to the defaults above. */
 void kad_options_default(kad_options *opt);
@@ -145,8 +151,18 @@ typedef struct {
        and output, slot reset, epoch bookkeeping and close */
     uint64_t phase_cycles[6];
     /* KAD_RUN_TIMING, host milliseconds: t_host (the whole call), t_setup (from
-       the call's entry until its first device work is enqueued) */
-    double t_host_ms, t_setup_ms;
+       the call's entry until its first device work is enqueued), t_table (from the
+       histogram's arrival until the L table is enqueued for upload: tau* and L) */
+    double t_host_ms, t_setup_ms, t_table_ms;
+    /* KAD_RUN_TIMING, the device's timeline of the sampling, milliseconds after
+       its first sample started: calibration histogram published, first epoch
+       closed, stop decided, last sampling block finished; and the sample indices
+       (calibration + adaptive) handed out when the stop was decided */
+    double t_dev_calib_ms, t_dev_first_close_ms, t_dev_stop_ms, t_dev_end_ms;
+    uint64_t issued_at_stop;
+    /* shared expansions: levels published for helpers, helper visits that joined
+       one, and SM cycles blocks spent looking for or giving help */
+    uint64_t shared_levels, helper_joins, help_cycles;
 } kad_result;
 
 /*

@@ -53,6 +53,12 @@ __device__ __forceinline__ unsigned int atom_add_release(unsigned int *p, unsign
     return old;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -141,6 +147,12 @@ struct Smem {
     unsigned long long dsum[2];
     unsigned long long next_dsum;
     volatile int met;
+    int abort; // the run stopped while this (adaptive) sample was in its BFS
+    int help_j;    // shared expansion this block owns or helps (-1 none)
+    int help_open; // shared expansions open when this block took its sample
+    int h_owner, h_X, h_tailY, h_cnt, h_total, h_watch;
+    uint32_t h_keyNext, h_sideX;
+    unsigned long long help_pn, help_pm;
     int mcount;
     int mid;
     int D;
@@ -402,6 +414,369 @@ __device__ __forceinline__ void trace_from_level(const SampleArgs &a, const uint
 }
 
 // ---------------------------------------------------------------- closer
+// ---------------------------------------------------------------- expansion
+// What one warp needs to expand arcs of a frontier chunk: the slot's scratch,
+// the chunk (row starts, exclusive degree offsets and path counts of its cnt
+// frontier vertices, in shared memory), the round, and where new vertices,
+// their degree sum and a meeting are recorded (shared memory for a block alone,
+// a KadHelp record for a shared expansion).
+struct ExpandCtx {
+    uint32_t *label;
+    unsigned long long *sigma, *sigma2;
+    int32_t *list;
+    uint32_t *bits;
+    const int32_t *s_rs, *s_off;
+    const unsigned long long *s_sig;
+    int cnt, X, tailY, n;
+    uint32_t sideX, keyNext;
+    int *tail;
+    unsigned long long *next_dsum;
+    volatile int *met;
+    bool bsh, watch;
+};
+
+// Expand the arcs first + k*stride (k < KAD_ITEMS) below `total` of the chunk.
+// Called by whole warps.  All neighbour ids are loaded before any bitmap word,
+// and those before any label or atomic, so each thread keeps several
+// independent loads in flight.  No block barrier is needed: an unlabelled
+// vertex can only become keyNext during the round (only side X labels, and
+// every earlier label has its bit set), so claims and path-count pushes commute,
+// and a fresh vertex's push need not wait for its claim's answer.  Returns true
+// (for the whole warp) when the run has stopped and this sample may give up.
+__device__ __forceinline__ bool expand_items(const SampleArgs &a, const ExpandCtx &c, int first, int stride,
+                                             int total, unsigned long long &pred_next, unsigned long long &pred_m) {
+    const int lane = threadIdx.x & 31;
+    // lane 0 looks at the stop flag and every lane at the meeting flag (both
+    // issued here, used below)
+    int stop_now = 0;
+    if (lane == 0 && c.watch) stop_now = *(volatile int *)&a.ctl->stop;
+    const int met_before = *c.met;
+    int vv[KAD_ITEMS];
+    int ix[KAD_ITEMS]; // frontier entry of the arc (its sigma is s_sig[ix])
+    uint32_t ll[KAD_ITEMS];
+#pragma unroll
+    for (int k = 0; k < KAD_ITEMS; k++) {
+        const int e = first + k * stride;
+        vv[k] = -1;
+        ix[k] = 0;
+        if (e < total) {
+            // frontier entry owning arc e: last j with off[j] <= e
+            int lo = 0, hi = c.cnt - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (c.s_off[mid] <= e)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            vv[k] = __ldg(a.col + c.s_rs[lo] + (e - c.s_off[lo]));
+            ix[k] = lo;
+        }
+    }
+    uint32_t bw[KAD_ITEMS];
+#pragma unroll
+    for (int k = 0; k < KAD_ITEMS; k++) bw[k] = (vv[k] >= 0) ? bits_ld(c.bsh, c.bits, vv[k] >> 5) : 0u;
+    // only vertices whose bit is set carry a label worth reading
+    bool fresh[KAD_ITEMS]; // unlabelled when the bitmap was read
+#pragma unroll
+    for (int k = 0; k < KAD_ITEMS; k++) {
+        const bool set = vv[k] >= 0 && ((bw[k] >> (vv[k] & 31)) & 1u);
+        fresh[k] = vv[k] >= 0 && !set;
+        ll[k] = set ? kad_ld_u32(c.label + vv[k]) : 0u;
+    }
+    // Does an arc of this warp reach the other side's frontier?  Then the round
+    // meets and no new vertex needs claiming (other warps learn it through met).
+    int reaches_y = 0;
+#pragma unroll
+    for (int k = 0; k < KAD_ITEMS; k++)
+        if (ll[k] != 0u && (ll[k] & KAD_SIDE) != c.sideX) reaches_y = 1;
+    const bool warp_meets = __any_sync(FULL_MASK, reaches_y) != 0;
+    if (__shfl_sync(FULL_MASK, stop_now, 0)) return true;
+    if (warp_meets && lane == 0) *c.met = 1;
+    const bool meeting_seen = warp_meets || met_before != 0;
+    uint32_t old[KAD_ITEMS];
+    unsigned long long prev[KAD_ITEMS];
+    int kind[KAD_ITEMS]; // 0 none, 1 next level of X, 2 other side's frontier
+#pragma unroll
+    for (int k = 0; k < KAD_ITEMS; k++) {
+        old[k] = 0u;
+        kind[k] = 0;
+        prev[k] = 0;
+        const int v = vv[k];
+        if (fresh[k]) {
+            if (meeting_seen) continue;
+            old[k] = atomicCAS(c.label + v, 0u, c.keyNext);
+            kind[k] = 1;
+            prev[k] = atomicAdd(c.sigma + v, c.s_sig[ix[k]]);
+        } else if (ll[k] != 0u) {
+            const uint32_t lv = ll[k];
+            if ((lv & KAD_KEY) == c.keyNext) {
+                kind[k] = 1;
+                prev[k] = atomicAdd(c.sigma + v, c.s_sig[ix[k]]);
+            } else if ((lv & KAD_SIDE) != c.sideX) {
+                // v is on the other side's frontier: the searches meet.
+                kind[k] = 2;
+                if (!(lv & KAD_INM)) atomicOr(c.label + v, KAD_INM);
+                prev[k] = atomicAdd(c.sigma2 + v, c.s_sig[ix[k]]);
+            }
+        }
+    }
+    int rs0[KAD_ITEMS], rs1[KAD_ITEMS];
+#pragma unroll
+    for (int k = 0; k < KAD_ITEMS; k++) {
+        rs0[k] = rs1[k] = 0;
+        if (fresh[k] && kind[k] == 1) {
+            rs0[k] = __ldg(a.rp + vv[k]);
+            rs1[k] = __ldg(a.rp + vv[k] + 1);
+        }
+    }
+    bool claimed[KAD_ITEMS];
+#pragma unroll
+    for (int k = 0; k < KAD_ITEMS; k++) {
+        claimed[k] = fresh[k] && kind[k] == 1 && old[k] == 0u;
+        if (fresh[k] && kind[k] == 1 && old[k] != 0u && old[k] != c.keyNext)
+            kad_set_err(a.ctl, KAD_DERR_LEVEL); // cannot happen (see above)
+        if (claimed[k]) bits_set(c.bsh, c.bits, vv[k]);
+        if (kind[k] == 1) {
+            pred_next++;
+            if (prev[k] + c.s_sig[ix[k]] < prev[k]) atomicOr(c.label + vv[k], KAD_OVF);
+        } else if (kind[k] == 2) {
+            pred_m++;
+            *c.met = 1;
+            if (prev[k] + c.s_sig[ix[k]] < prev[k]) atomicOr(c.label + vv[k], KAD_OVF2);
+        }
+    }
+    // new vertices: one list reservation and one degree-sum update per warp
+    unsigned mask[KAD_ITEMS];
+    int nclaim = 0;
+    unsigned long long mydeg = 0;
+#pragma unroll
+    for (int k = 0; k < KAD_ITEMS; k++) {
+        mask[k] = __ballot_sync(FULL_MASK, claimed[k]);
+        nclaim += __popc(mask[k]);
+        if (claimed[k]) mydeg += (unsigned long long)(rs1[k] - rs0[k]);
+    }
+    if (nclaim) {
+        int pos0 = 0;
+        if (lane == 0) pos0 = atomicAdd(c.tail, nclaim);
+        pos0 = __shfl_sync(FULL_MASK, pos0, 0);
+#pragma unroll
+        for (int k = 0; k < KAD_ITEMS; k++) {
+            if (claimed[k]) {
+                const int pos = pos0 + __popc(mask[k] & lanemask_lt());
+                if (pos + c.tailY < c.n)
+                    c.list[phys(c.X, pos, c.n)] = vv[k];
+                else
+                    kad_set_err(a.ctl, KAD_DERR_FRONTIER);
+            }
+            pos0 += __popc(mask[k]);
+        }
+        const unsigned long long ds = warp_sum_u64(mydeg);
+        if (lane == 0) atomicAdd(c.next_dsum, ds);
+    }
+    return false;
+}
+
+#define KAD_WARP_CHUNK (32 * KAD_ITEMS) // arcs a warp expands per call in a shared expansion
+#define KAD_WARP_GRAB (4 * KAD_WARP_CHUNK) // arcs a warp takes at a time
+#define KAD_HELP_WAIT 20000000          // bound of the owner's wait for stragglers (x ~100 ns)
+
+// One warp works through a shared expansion: take a chunk of arcs (the next one
+// is taken before the current one is expanded, hiding the atomic's latency) and
+// expand it, until no arcs are left.  After the run has stopped the warp still
+// takes chunks, without expanding them.  The warp's arc counts go to the record.
+// Every chunk handed out is finished by the warp that took it before that
+// warp's block leaves (helpers) or passes its barrier (owner), so once the
+// owner's warps are through and no helper is inside, the level is complete.
+// Returns whether this warp saw the stop.
+__device__ __forceinline__ bool help_warp_loop(const SampleArgs &a, KadHelp *h, const ExpandCtx &c, int total) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long pn = 0, pm = 0;
+    bool stopped = false;
+    int ci = 0;
+    if (lane == 0) ci = atomicAdd(&h->next, KAD_WARP_GRAB);
+    ci = __shfl_sync(FULL_MASK, ci, 0);
+    while (ci < total) {
+        int cn = 0;
+        if (lane == 0) cn = atomicAdd(&h->next, KAD_WARP_GRAB);
+        const int end = min(total, ci + KAD_WARP_GRAB);
+        for (int q = ci; q < end && !stopped; q += KAD_WARP_CHUNK)
+            stopped = expand_items(a, c, q + lane, 32, end, pn, pm);
+        ci = __shfl_sync(FULL_MASK, cn, 0);
+    }
+    pn = warp_sum_u64(pn);
+    pm = warp_sum_u64(pm);
+    if (lane == 0) {
+        if (pn) atomicAdd(&h->pred_next, pn);
+        if (pm) atomicAdd(&h->pred_m, pm);
+        if (stopped) atomicExch(&h->stopped, 1);
+    }
+    return stopped;
+}
+
+// Owner side: publish the chunk as a shared expansion if a record is free;
+// returns the record index (the same in every thread) or -1.
+template <int BLOCK>
+__device__ int help_open(const SampleArgs &a, Smem<BLOCK> &sm, const ExpandCtx &c, int total) {
+    if (threadIdx.x == 0) {
+        int j = -1;
+        const int start = (int)(blockIdx.x % KAD_HELP_SLOTS);
+        for (int q = 0; q < KAD_HELP_SLOTS; q++) {
+            const int cand = (start + q) % KAD_HELP_SLOTS;
+            if (*(volatile int *)&a.help[cand].state == 0 && atomicCAS(&a.help[cand].state, 0, 3) == 0) {
+                j = cand;
+                break;
+            }
+        }
+        sm.help_j = j;
+    }
+    __syncthreads();
+    const int j = sm.help_j;
+    if (j < 0) return -1;
+    KadHelp *h = a.help + j;
+    for (int i = threadIdx.x; i < c.cnt; i += BLOCK) {
+        h->rs[i] = c.s_rs[i];
+        h->off[i] = c.s_off[i];
+        h->sig[i] = c.s_sig[i];
+    }
+    if (threadIdx.x == 0) {
+        h->owner = blockIdx.x;
+        h->X = c.X;
+        h->tailY = c.tailY;
+        h->cnt = c.cnt;
+        h->total = total;
+        h->watch = c.watch ? 1 : 0;
+        h->keyNext = c.keyNext;
+        h->sideX = c.sideX;
+        h->next = 0;
+        h->tail = *c.tail;
+        h->met = *c.met;
+        h->stopped = 0;
+        h->next_dsum = 0;
+        h->pred_next = 0;
+        h->pred_m = 0;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicExch(&h->state, 1); // open: the fields above are published
+        atomicAdd(&a.ctl->help_open, 1);
+    }
+    return j;
+}
+
+// Owner side: expand with every warp, then close the record to newcomers and
+// wait (bounded) until no helper is inside; take the results, free the record.
+template <int BLOCK>
+__device__ void help_own(const SampleArgs &a, Smem<BLOCK> &sm, int j, const ExpandCtx &c0, int total, int X) {
+    KadHelp *h = a.help + j;
+    ExpandCtx c = c0;
+    c.tail = &h->tail;
+    c.next_dsum = &h->next_dsum;
+    c.met = &h->met;
+    help_warp_loop(a, h, c, total);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicExch(&h->state, 2); // closing: no new helper enters
+        kad_fence_sc();
+        int it = 0;
+        while (*(volatile int *)&h->helpers != 0 && it < KAD_HELP_WAIT) {
+            __nanosleep(100);
+            it++;
+        }
+        if (it >= KAD_HELP_WAIT) kad_set_err(a.ctl, KAD_DERR_HELP);
+        __threadfence();
+        sm.tail[X] = *(volatile int *)&h->tail;
+        sm.next_dsum += *(volatile unsigned long long *)&h->next_dsum;
+        if (*(volatile int *)&h->met) sm.met = 1;
+        // arcs skipped after the stop (by any warp) leave the level incomplete:
+        // the sample gives up
+        if (*(volatile int *)&h->stopped) sm.abort = 1;
+        sm.help_pn = *(volatile unsigned long long *)&h->pred_next;
+        sm.help_pm = *(volatile unsigned long long *)&h->pred_m;
+        atomicSub(&a.ctl->help_open, 1);
+        atomicExch(&h->state, 0);
+    }
+    __syncthreads();
+}
+
+// Helper side, between two samples of this block: join an open shared
+// expansion if there is one, work through it, leave.
+template <int BLOCK>
+__device__ void help_others(const SampleArgs &a, Smem<BLOCK> &sm, int32_t n) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        const int st = (lane < KAD_HELP_SLOTS) ? *(volatile int *)&a.help[lane].state : 0;
+        unsigned m = __ballot_sync(FULL_MASK, st == 1);
+        if (lane == 0) {
+            int j = -1;
+            const int rot = (int)(blockIdx.x % 32);
+            m = (m >> rot) | (rot ? (m << (32 - rot)) : 0u); // start looking at this block's own offset
+            while (m) {
+                const int cand = (__ffs(m) - 1 + rot) % 32;
+                m &= m - 1;
+                KadHelp *h = a.help + cand;
+                const int inside = atomicAdd(&h->helpers, 1);
+                kad_fence_sc();
+                if (inside < a.help_max && *(volatile int *)&h->state == 1 &&
+                    *(volatile int *)&h->next < *(volatile int *)&h->total) {
+                    j = cand;
+                    break;
+                }
+                atomicSub(&h->helpers, 1);
+            }
+            sm.help_j = j;
+            if (j >= 0) {
+                KadHelp *h = a.help + j;
+                sm.h_owner = *(volatile int *)&h->owner;
+                sm.h_X = *(volatile int *)&h->X;
+                sm.h_tailY = *(volatile int *)&h->tailY;
+                sm.h_cnt = *(volatile int *)&h->cnt;
+                sm.h_total = *(volatile int *)&h->total;
+                sm.h_watch = *(volatile int *)&h->watch;
+                sm.h_keyNext = *(volatile uint32_t *)&h->keyNext;
+                sm.h_sideX = *(volatile uint32_t *)&h->sideX;
+            }
+        }
+    }
+    __syncthreads();
+    const int j = sm.help_j;
+    if (j < 0) return;
+    KadHelp *h = a.help + j;
+    const int cnt = min(sm.h_cnt, BLOCK); // every block of a launch has BLOCK threads: cnt <= BLOCK
+    for (int i = tid; i < cnt; i += BLOCK) {
+        sm.rs[i] = __ldcg(h->rs + i);
+        sm.off[i] = __ldcg(h->off + i);
+        sm.sig[i] = __ldcg(h->sig + i);
+    }
+    __syncthreads();
+    const size_t soff = (size_t)sm.h_owner * (size_t)n;
+    ExpandCtx c;
+    c.label = a.label + soff;
+    c.sigma = a.sigma + soff;
+    c.sigma2 = a.sigma2 + soff;
+    c.list = a.list + soff;
+    c.bits = a.bits + (size_t)sm.h_owner * (size_t)a.nw;
+    c.s_rs = sm.rs;
+    c.s_off = sm.off;
+    c.s_sig = sm.sig;
+    c.cnt = cnt;
+    c.X = sm.h_X;
+    c.tailY = sm.h_tailY;
+    c.n = n;
+    c.sideX = sm.h_sideX;
+    c.keyNext = sm.h_keyNext;
+    c.tail = &h->tail;
+    c.next_dsum = &h->next_dsum;
+    c.met = &h->met;
+    c.bsh = false;
+    c.watch = sm.h_watch != 0;
+    help_warp_loop(a, h, c, sm.h_total);
+    __threadfence(); // this thread's writes to the owner's scratch, before leaving
+    __syncthreads();
+    if (tid == 0) atomicSub(&h->helpers, 1);
+}
+
 // Fold epoch k (sample rows of ring slot k mod R) into the counts, then
 // evaluate the stop rule on the consistent state after k+1 epochs.
 template <int BLOCK>
@@ -444,12 +819,15 @@ __device__ void close_epoch(const SampleArgs &a, Smem<BLOCK> &sm, unsigned long 
     }
     const int all = __syncthreads_and(pass);
     if (tid == 0) {
+        if (a.ctl->t_first_close == 0) a.ctl->t_first_close = global_ns();
         a.ctl->overflow += sm.ovf_acc;
         a.epoch_done[k % a.ring] = 0;
         const bool cut = a.max_epochs && k + 1 >= a.max_epochs;
         if (tau >= a.omega || all || cut) {
             a.ctl->tau = tau;
             a.ctl->stopped_by_omega = (tau >= a.omega) ? 1 : (all ? 0 : 2);
+            a.ctl->t_stop = global_ns();
+            a.ctl->issued_at_stop = *(volatile unsigned long long *)&a.ctl->next;
             __threadfence();
             *(volatile int *)&a.ctl->stop = 1;
         }
@@ -531,6 +909,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     // into the next level or meeting set.
     unsigned long long w_pred = 0;
     if (tid < KAD_WORK_WORDS) sm.acc[tid] = 0;
+    if (tid == 0 && a.mode == KAD_MODE_RING) atomicCAS(&a.ctl->t_start, 0ull, global_ns());
     Stream st;
 
     // A launch that continues a run first closes the epochs an earlier launch
@@ -538,7 +917,22 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     if (a.mode == KAD_MODE_RING && blockIdx.x == 0) run_closer<BLOCK>(a, sm);
 
     for (;;) {
-        // ---------------------------------------------------- next sample index
+        // ---------------------------------------------------- help, then next sample index
+        // A block between two samples first helps with another block's long level
+        // if one is open (before taking an index, so that no sample of its own
+        // waits meanwhile).
+        if (a.help) {
+            if (tid == 0) sm.help_open = *(volatile int *)&a.ctl->help_open;
+            __syncthreads();
+            if (sm.help_open > 0) {
+                const long long h0 = clock64();
+                help_others<BLOCK>(a, sm, n);
+                if (tid == 0) {
+                    sm.acc[7] += (unsigned long long)(clock64() - h0);
+                    if (sm.help_j >= 0) sm.acc[15]++;
+                }
+            }
+        }
         if (tid == 0) {
             unsigned long long idx = ~0ull;
             int calib = 0;
@@ -565,6 +959,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
         const unsigned long long idx = sm.idx;
         if (idx == ~0ull) break;
         const bool calib = sm.calib != 0;
+        // adaptive samples of a run may be abandoned once the run has stopped
+        const bool watch_stop = !calib && a.mode == KAD_MODE_RING;
         if (tid == 0) sm.tmark = clock64();
 
         // ---------------------------------------------------- pair draw
@@ -577,6 +973,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             sm.t = t;
             sm.tail[0] = sm.tail[1] = 0;
             sm.D = 0;
+            sm.abort = 0;
             if (__ldg(a.comp + s) == __ldg(a.comp + t)) {
                 label[s] = 1u;            // s side, level 0
                 label[t] = KAD_SIDE | 1u; // t side, level 0
@@ -743,121 +1140,57 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 const int excl = block_excl_scan<BLOCK>(d, sm.wtmp, total);
                 if (tid < cnt) sm.off[tid] = excl;
                 __syncthreads();
-                // KAD_ITEMS arcs per thread and pass: all neighbour ids are loaded
-                // before any label, and all labels before any atomic, so each
-                // thread keeps several independent loads in flight.
-                for (int base = 0; base < total; base += BLOCK * KAD_ITEMS) {
-                    int vv[KAD_ITEMS];
-                    unsigned long long ss[KAD_ITEMS];
-                    uint32_t ll[KAD_ITEMS];
-#pragma unroll
-                    for (int k = 0; k < KAD_ITEMS; k++) {
-                        const int e = base + k * BLOCK + tid;
-                        vv[k] = -1;
-                        ss[k] = 0;
-                        if (e < total) {
-                            // frontier entry owning arc e: last j with off[j] <= e
-                            int lo = 0, hi = cnt - 1;
-                            while (lo < hi) {
-                                const int mid = (lo + hi + 1) >> 1;
-                                if (sm.off[mid] <= e)
-                                    lo = mid;
-                                else
-                                    hi = mid - 1;
-                            }
-                            vv[k] = __ldg(a.col + sm.rs[lo] + (e - sm.off[lo]));
-                            ss[k] = sm.sig[lo];
-                        }
+                ExpandCtx ec;
+                ec.label = label;
+                ec.sigma = sigma;
+                ec.sigma2 = sigma2;
+                ec.list = list;
+                ec.bits = bits;
+                ec.s_rs = sm.rs;
+                ec.s_off = sm.off;
+                ec.s_sig = sm.sig;
+                ec.cnt = (levX == 0) ? 1 : cnt;
+                ec.X = X;
+                ec.tailY = tailY;
+                ec.n = n;
+                ec.sideX = sideX;
+                ec.keyNext = keyNext;
+                ec.tail = &sm.tail[X];
+                ec.next_dsum = &sm.next_dsum;
+                ec.met = &sm.met;
+                ec.bsh = bsh;
+                ec.watch = watch_stop;
+                // a chunk with many arcs (hub rows) is shared with blocks between samples
+                const int hj = (a.help && !bsh && total >= a.help_min) ? help_open<BLOCK>(a, sm, ec, total) : -1;
+                if (hj >= 0) {
+                    help_own<BLOCK>(a, sm, hj, ec, total, X);
+                    if (tid == 0) {
+                        pred_next += sm.help_pn;
+                        pred_m += sm.help_pm;
+                        sm.acc[14]++;
                     }
-#pragma unroll
-                    for (int k = 0; k < KAD_ITEMS; k++) ll[k] = (vv[k] >= 0) ? bits_ld(bsh, bits, vv[k] >> 5) : 0u;
-                    // only vertices whose bit is set carry a label worth reading
-#pragma unroll
-                    for (int k = 0; k < KAD_ITEMS; k++)
-                        ll[k] = (vv[k] >= 0 && ((ll[k] >> (vv[k] & 31)) & 1u)) ? kad_ld_u32(label + vv[k]) : 0u;
-                    // Claims first (all CAS of the pass in flight together), then
-                    // the path-count pushes, then the new vertices' degrees: each
-                    // kind of access overlaps across the items instead of chaining.
-                    // Does any arc of this pass reach the other side's frontier?  Then
-                    // the round meets, and no new vertex needs claiming.
-                    int reaches_y = 0;
-#pragma unroll
-                    for (int k = 0; k < KAD_ITEMS; k++)
-                        if (vv[k] >= 0 && ll[k] != 0u && (ll[k] & KAD_SIDE) != sideX) reaches_y = 1;
-                    if (__syncthreads_or(reaches_y)) sm.met = 1;
-                    bool claimed[KAD_ITEMS];
-                    const bool meeting_seen = sm.met != 0;
-#pragma unroll
-                    for (int k = 0; k < KAD_ITEMS; k++) {
-                        claimed[k] = false;
-                        if (vv[k] >= 0 && ll[k] == 0u && !meeting_seen) {
-                            const uint32_t old = atomicCAS(label + vv[k], 0u, keyNext);
-                            claimed[k] = (old == 0u);
-                            ll[k] = claimed[k] ? keyNext : old;
-                        }
-                    }
-                    unsigned long long prev[KAD_ITEMS];
-                    int kind[KAD_ITEMS]; // 0 none, 1 next level of X, 2 other side's frontier
-#pragma unroll
-                    for (int k = 0; k < KAD_ITEMS; k++) {
-                        kind[k] = 0;
-                        prev[k] = 0;
-                        const int v = vv[k];
-                        const uint32_t lv = ll[k];
-                        if (v < 0 || lv == 0u) continue;
-                        if (claimed[k]) bits_set(bsh, bits, v);
-                        if ((lv & KAD_KEY) == keyNext) {
-                            kind[k] = 1;
-                            prev[k] = atomicAdd(sigma + v, ss[k]);
-                        } else if ((lv & KAD_SIDE) != sideX) {
-                            // v is on the other side's frontier: the searches meet.
-                            kind[k] = 2;
-                            if (!(lv & KAD_INM)) atomicOr(label + v, KAD_INM);
-                            prev[k] = atomicAdd(sigma2 + v, ss[k]);
-                        }
-                    }
-                    int vdeg[KAD_ITEMS];
-#pragma unroll
-                    for (int k = 0; k < KAD_ITEMS; k++)
-                        vdeg[k] = claimed[k] ? __ldg(a.rp + vv[k] + 1) - __ldg(a.rp + vv[k]) : 0;
-#pragma unroll
-                    for (int k = 0; k < KAD_ITEMS; k++) {
-                        if (kind[k] == 1) {
-                            pred_next++;
-                            if (prev[k] + ss[k] < prev[k]) atomicOr(label + vv[k], KAD_OVF);
-                        } else if (kind[k] == 2) {
-                            pred_m++;
-                            sm.met = 1;
-                            if (prev[k] + ss[k] < prev[k]) atomicOr(label + vv[k], KAD_OVF2);
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < KAD_ITEMS; k++) {
-                        const unsigned mask = __ballot_sync(FULL_MASK, claimed[k]);
-                        if (mask) {
-                            const int leader = __ffs(mask) - 1;
-                            int pos0 = 0;
-                            if (lane == leader) pos0 = atomicAdd(&sm.tail[X], __popc(mask));
-                            pos0 = __shfl_sync(FULL_MASK, pos0, leader);
-                            if (claimed[k]) {
-                                const int pos = pos0 + __popc(mask & lanemask_lt());
-                                if (pos + tailY < n)
-                                    list[phys(X, pos, n)] = vv[k];
-                                else
-                                    kad_set_err(a.ctl, KAD_DERR_FRONTIER);
-                            }
-                            const unsigned long long ds = warp_sum_u64((unsigned long long)vdeg[k]);
-                            if (lane == 0) atomicAdd(&sm.next_dsum, ds);
+                } else {
+                    for (int base = 0; base < total; base += BLOCK * KAD_ITEMS) {
+                        if (expand_items(a, ec, base + tid, BLOCK, total, pred_next, pred_m)) {
+                            if (lane == 0) sm.abort = 1;
+                            break;
                         }
                     }
                 }
                 __syncthreads();
+                if (sm.abort) break;
             }
             const int met = sm.met;
             w_pred += met ? pred_m : pred_next;
             __syncthreads();
             if (tid == 0) {
-                if (met) {
+                if (sm.abort || (watch_stop && !met && *(volatile int *)&a.ctl->stop)) {
+                    // The run has stopped: this sample lies beyond the stop epoch and
+                    // is never counted.  Give up (the reset below also clears sigma2
+                    // on the other side's frontier, where a meeting may have begun).
+                    sm.abort = 1;
+                    sm.D = 0;
+                } else if (met) {
                     sm.D = sm.lev[X] + 1 + sm.lev[Y];
                 } else {
                     const int tl = min(sm.tail[X], n - tailY);
@@ -1089,7 +1422,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     bits_clear_word(bsh, bits, vr[k] >> 5); // every set bit of the word is a listed vertex
                 }
             }
-            if (D > 0) {
+            if (D > 0 || sm.abort) {
                 const int Y = 1 - X;
                 for (int j = sm.fb[Y] + tid; j < sm.fe[Y]; j += BLOCK) sigma2[__ldcg(list + phys(Y, j, n))] = 0ull;
             }
@@ -1119,6 +1452,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 __threadfence_system();
                 __syncthreads();
                 if (tid == 0) {
+                    a.ctl->t_calib = global_ns();
                     *(volatile int *)&a.hpage->calib_flag = 1;
                     __threadfence_system();
                 }
@@ -1154,6 +1488,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     if (tid == 0) {
         for (int i = 0; i < KAD_WORK_WORDS; i++)
             if (i != 3 && sm.acc[i]) atomicAdd(a.work + i, sm.acc[i]);
+        if (a.mode == KAD_MODE_RING) atomicMax(&a.ctl->t_end, global_ns());
     }
 }
 

@@ -29,7 +29,8 @@ class Options(ctypes.Structure):
     _fields_ = [("epoch_size", ctypes.c_uint32), ("calib_div", ctypes.c_uint32), ("ring_epochs", ctypes.c_uint32),
                 ("slots", ctypes.c_int32), ("mcap", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("flags", ctypes.c_uint32), ("debug", ctypes.c_uint32),
-                ("max_epochs", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("max_epochs", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("share_min_arcs", ctypes.c_int32), ("share_max_helpers", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -44,7 +45,11 @@ class Result(ctypes.Structure):
                 ("t_ads_kernel_ms", ctypes.c_double), ("ads_launches", ctypes.c_uint32),
                 ("slots_used", ctypes.c_int32), ("kernel_launches", ctypes.c_uint32),
                 ("block_threads_used", ctypes.c_int32), ("blocks_per_sm_used", ctypes.c_int32),
-                ("phase_cycles", ctypes.c_uint64 * 6), ("t_host_ms", ctypes.c_double), ("t_setup_ms", ctypes.c_double)]
+                ("phase_cycles", ctypes.c_uint64 * 6), ("t_host_ms", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
+                ("t_table_ms", ctypes.c_double), ("t_dev_calib_ms", ctypes.c_double),
+                ("t_dev_first_close_ms", ctypes.c_double), ("t_dev_stop_ms", ctypes.c_double),
+                ("t_dev_end_ms", ctypes.c_double), ("issued_at_stop", ctypes.c_uint64),
+                ("shared_levels", ctypes.c_uint64), ("helper_joins", ctypes.c_uint64), ("help_cycles", ctypes.c_uint64)]
 
 PHASE_NAMES = ("draw", "bfs", "meet", "trace", "reset", "close")
 
@@ -273,7 +278,9 @@ def _result_scalars(r):
                                     "vd_bound", "sigma_overflow", "stopped_by_omega", "tau_star", "t_total_ms",
                                     "t_calib_ms", "t_ads_ms", "t_ads_kernel_ms", "ads_launches", "slots_used",
                                     "kernel_launches", "block_threads_used", "blocks_per_sm_used", "t_host_ms",
-                                    "t_setup_ms")}
+                                    "t_setup_ms", "t_table_ms", "t_dev_calib_ms", "t_dev_first_close_ms",
+                                    "t_dev_stop_ms", "t_dev_end_ms", "issued_at_stop", "shared_levels",
+                                    "helper_joins", "help_cycles")}
     d["counters"] = dict(zip(WORK_NAMES, (int(x) for x in r.work)))
     d["phase_cycles"] = dict(zip(PHASE_NAMES, (int(x) for x in r.phase_cycles)))
     return d
