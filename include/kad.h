@@ -88,28 +88,25 @@ typedef struct {
     int32_t block_threads; /* threads per sampling block: 128, 256, 512 or 1024 (0 = 512) */
     int32_t blocks_per_sm; /* resident sampling blocks per SM the kernel is built for: 128 threads 4|8,
                               256: 2|4, 512: 1|2, 1024: 1 (0 = 4, 2, 2, 1 respectively).  When both
-                              are 0 the graph's first run picks the fastest of 512x2, 256x4, 256x2
-                              and 1024x1 by timing the same query, truncated after 4 epochs, under
-                              each (the autotuner; graphs under 16384 vertices keep 512x2) */
+                              are 0 the kernel is 512x2, or with KAD_RUN_AUTOTUNE the fastest of
+                              512x2, 256x4, 256x2, 1024x1 and 128x8 on this graph */
     uint32_t flags;      /* KAD_RUN_* */
     uint32_t debug;      /* KAD_DEBUG_* (tests only; results do not depend on it) */
     uint32_t max_epochs; /* > 0: stop after this many epochs even if the stop rule does not hold
                             (a truncated run, for comparisons on large graphs); 0 = no limit */
     uint32_t reserved;
-    int32_t share_min_arcs;    /* > 0: a BFS chunk with at least this many arcs is shared -- blocks
-                                  between two samples help expand it (0 = never share: on R-MAT
-                                  graphs sharing has measured slower than each block alone) */
-    int32_t share_max_helpers; /* helper blocks per shared chunk (0 = 16) */
 } kad_options;
 
 #define KAD_RUN_TIMING 1u      /* fill kad_result.t_* with CUDA-event times of each phase */
-#define KAD_RUN_NO_AUTOTUNE 2u /* keep the default kernel variant instead of timing the candidates on the
-                                  graph's first run (when block_threads and blocks_per_sm are both 0) */
+#define KAD_RUN_AUTOTUNE 2u    /* the graph's first run (block_threads and blocks_per_sm both 0) times the
+                                  same query, truncated after 4 epochs, twice under each candidate variant
+                                  and keeps the fastest for the graph's later runs (graphs under 16384
+                                  vertices keep 512x2).  Off by default: 512x2 has been the fastest on
+                                  every configured workload, and tuning costs ~10 truncated runs */
 #define KAD_DEBUG_TRACE_SCAN 1u    /* trace-back always scans the current vertex's adjacency */
 #define KAD_DEBUG_SMEM_BITMAP 2u /* keep the labelled-vertex bitmap in shared memory when it fits */
 #define KAD_DEBUG_FULL_SCAN 4u   /* the meeting round always scans the expanding side's rows */
-#define KAD_DEBUG_NO_SHARE 8u    /* every block expands its own levels alone (no shared expansions) */
-#define KAD_DEBUG_SHARE_ALL 16u  /* share every level with at least 256 arcs (tests the shared path) */
+#define KAD_DEBUG_SERIAL_TRACE 8u /* one warp traces both sides (no speculative t-side trace) */
 
 /* Initialises *opt to the defaults above. */
 void kad_options_default(kad_options *opt);
@@ -160,9 +157,6 @@ typedef struct {
        (calibration + adaptive) handed out when the stop was decided */
     double t_dev_calib_ms, t_dev_first_close_ms, t_dev_stop_ms, t_dev_end_ms;
     uint64_t issued_at_stop;
-    /* shared expansions: levels published for helpers, helper visits that joined
-       one, and SM cycles blocks spent looking for or giving help */
-    uint64_t shared_levels, helper_joins, help_cycles;
 } kad_result;
 
 /*

@@ -37,7 +37,6 @@ const int kDefaultMcap = 256;
 const int32_t kTuneMinVertices = 16384;   // smaller graphs keep the default variant
 const uint32_t kTuneEpochs = 4;           // epochs of the truncated query timed per candidate
 const uint64_t kTuneSeed = 0x6b61646162726174ull;
-const int kHelpMaxHelpers = 16; // helper blocks per shared chunk
 
 struct Workspace {
     int slots = 0;            // sampling slots the scratch was last zeroed for
@@ -58,7 +57,6 @@ struct Workspace {
     // per-vertex state
     uint32_t *cnt = nullptr, *c0 = nullptr;
     double *bc = nullptr;         // bc output staged here before a copy to host memory
-    KadHelp *help = nullptr;      // shared-expansion records (KAD_HELP_SLOTS)
     // per-class state
     size_t nclass_cap = 0;
     int32_t *classmax = nullptr;
@@ -119,7 +117,6 @@ void ws_free_all(Workspace &w) {
     cudaFree(w.cnt);
     cudaFree(w.c0);
     cudaFree(w.bc);
-    cudaFree(w.help);
     cudaFree(w.classmax);
     cudaFree(w.ltab);
     cudaFree(w.hist);
@@ -250,8 +247,7 @@ kad_status ensure_rows(Workspace &w, size_t rows, int32_t cap, cudaStream_t st) 
 kad_status ensure_fixed(kad_graph *g, Workspace &w, size_t nclass, size_t ring, cudaStream_t st) {
     const size_t n = (size_t)g->gd.n;
     if (!w.ctl) {
-        if (dalloc(&w.ctl, 1) != cudaSuccess || dalloc(&w.work, KAD_WORK_WORDS) != cudaSuccess ||
-            dalloc(&w.help, KAD_HELP_SLOTS) != cudaSuccess) {
+        if (dalloc(&w.ctl, 1) != cudaSuccess || dalloc(&w.work, KAD_WORK_WORDS) != cudaSuccess) {
             cudaGetLastError();
             return KAD_ERR_OOM;
         }
@@ -530,21 +526,6 @@ kad_status launch_phase(kad_graph *g, Workspace &w, const SampleArgs &a, int blo
     return KAD_OK;
 }
 
-// Shared expansions: off unless kad_options asks for them (share_min_arcs > 0)
-// or a test forces them (KAD_DEBUG_SHARE_ALL); KAD_DEBUG_NO_SHARE wins.
-void apply_share_options(SampleArgs &a, const Workspace &w, const kad_options &o) {
-    a.help = nullptr;
-    if (o.debug & KAD_DEBUG_NO_SHARE) return;
-    if (o.debug & KAD_DEBUG_SHARE_ALL) {
-        a.help = w.help;
-        a.help_min = 256;
-    } else if (o.share_min_arcs > 0) {
-        a.help = w.help;
-        a.help_min = o.share_min_arcs;
-    }
-    if (o.share_max_helpers > 0) a.help_max = o.share_max_helpers;
-}
-
 SampleArgs base_args(kad_graph *g, const Workspace &w, uint64_t seed) {
     SampleArgs a;
     memset(&a, 0, sizeof(a));
@@ -562,9 +543,6 @@ SampleArgs base_args(kad_graph *g, const Workspace &w, uint64_t seed) {
     a.key1 = (uint32_t)(seed >> 32);
     a.ctl = w.ctl;
     a.work = w.work;
-    a.help = nullptr; // shared expansions only on request (apply_share_options)
-    a.help_min = 0x7fffffff;
-    a.help_max = kHelpMaxHelpers;
     a.mcap = kDefaultMcap;
     return a;
 }
@@ -604,7 +582,7 @@ kad_status autotune(kad_graph *g, Workspace &w, double eps, double delta, const 
             o2.block_threads = cand[c][0];
             o2.blocks_per_sm = cand[c][1];
             o2.max_epochs = kTuneEpochs;
-            o2.flags |= KAD_RUN_TIMING | KAD_RUN_NO_AUTOTUNE;
+            o2.flags = (o2.flags | KAD_RUN_TIMING) & ~KAD_RUN_AUTOTUNE;
             // twice, keeping the faster: the first launch of a variant also pays
             // for loading its code and for growing the workspace
             double ms = 0.0;
@@ -652,7 +630,7 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
     if (nclass > (size_t)0x7fffffff || omega > ((uint64_t)1 << 40)) return KAD_ERR_INVALID_ARG;
     kad_status s;
     LaunchCfg cfg = resolve_cfg(o);
-    if (o.block_threads == 0 && o.blocks_per_sm == 0 && !(o.flags & KAD_RUN_NO_AUTOTUNE))
+    if (o.block_threads == 0 && o.blocks_per_sm == 0 && (o.flags & KAD_RUN_AUTOTUNE))
         if ((s = autotune(g, w, eps, delta, o, st, cfg)) != KAD_OK) return s;
     if (o.debug & KAD_DEBUG_SMEM_BITMAP) choose_bitmap_home(cfg, g->gd.n, g->device);
     const int slots = resolve_slots(g, w, o, cfg);
@@ -680,7 +658,6 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
     if ((e = cudaMemsetAsync(w.cnt, 0, (size_t)n * 4, st)) != cudaSuccess) return fail(g, e);
     if ((e = cudaMemsetAsync(w.hist, 0, nclass * 4, st)) != cudaSuccess) return fail(g, e);
     if ((e = cudaMemsetAsync(w.ctl, 0, sizeof(KadCtl), st)) != cudaSuccess) return fail(g, e);
-    if ((e = cudaMemsetAsync(w.help, 0, KAD_HELP_SLOTS * sizeof(KadHelp), st)) != cudaSuccess) return fail(g, e);
     if ((e = cudaMemsetAsync(w.epoch_done, 0, ring * 4, st)) != cudaSuccess) return fail(g, e);
     if ((e = cudaMemsetAsync(w.work, 0, KAD_WORK_WORDS * sizeof(unsigned long long), st)) != cudaSuccess)
         return fail(g, e);
@@ -692,7 +669,6 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
     SampleArgs a = base_args(g, w, seed);
     a.mcap = (o.mcap < 0) ? kDefaultMcap : o.mcap;
     a.debug = o.debug;
-    apply_share_options(a, w, o);
     a.mode = KAD_MODE_RING;
     a.calib_n = tau0;
     a.c0w = w.c0;
@@ -821,9 +797,6 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
     out->tau_star = ts;
     for (int i = 0; i < 6; i++) out->work[i] = work[i];
     for (int i = 0; i < 6; i++) out->phase_cycles[i] = work[8 + i];
-    out->help_cycles = work[7];
-    out->shared_levels = work[14];
-    out->helper_joins = work[15];
     out->ads_launches = launches;
     out->slots_used = slots;
     out->block_threads_used = cfg.threads;
@@ -989,7 +962,7 @@ void server_worker(kad_server *S) {
         o.block_threads = S->threads;
         o.blocks_per_sm = S->per_sm;
         o.slots = slots;
-        o.flags |= KAD_RUN_NO_AUTOTUNE | KAD_RUN_TIMING;
+        o.flags |= KAD_RUN_TIMING;
         kad_result r;
         memset(&r, 0, sizeof(r));
         r.bc = q->bc_out;
@@ -1110,7 +1083,6 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
         SampleArgs a = base_args(g, w, seed);
         a.mcap = (o.mcap < 0) ? kDefaultMcap : o.mcap;
         a.debug = o.debug;
-        apply_share_options(a, w, o);
         a.domain = domain;
         a.i0 = i0;
         a.i1 = i0 + c;
@@ -1127,7 +1099,6 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
         a.ring = 1;
         if ((e = cudaMemsetAsync(d_paths, 0xff, c * (size_t)cap * 4, st)) != cudaSuccess ||
             (e = cudaMemsetAsync(w.ctl, 0, sizeof(KadCtl), st)) != cudaSuccess ||
-            (e = cudaMemsetAsync(w.help, 0, KAD_HELP_SLOTS * sizeof(KadHelp), st)) != cudaSuccess ||
             (e = cudaMemsetAsync(w.work, 0, KAD_WORK_WORDS * 8, st)) != cudaSuccess) {
             s = fail(g, e);
             goto out;

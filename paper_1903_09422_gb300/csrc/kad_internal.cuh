@@ -38,7 +38,6 @@
 #define KAD_DERR_SELECT 4    // meeting draw found no vertex
 #define KAD_DERR_LEVEL 5     // level overflow
 #define KAD_DERR_FRONTIER 6  // list overflow
-#define KAD_DERR_HELP 7      // a shared expansion did not finish in time
 
 // Control block of one adaptive run (device memory).
 struct KadCtl {
@@ -58,32 +57,6 @@ struct KadCtl {
     // block finished; and the sample indices handed out when the stop was decided
     unsigned long long t_start, t_calib, t_first_close, t_stop, t_end;
     unsigned long long issued_at_stop;
-    int help_open; // shared expansions open for helpers (see KadHelp)
-};
-
-// A shared expansion.  A block whose sample reaches a level with many arcs
-// (hub rows) publishes the level's frontier here; blocks between two samples of
-// their own join and take 32 x KAD_ITEMS arcs at a time, exactly as the owner's
-// warps do.  Claims and path-count pushes commute (only side X labels during the
-// round), so the result does not depend on who processes which arcs.
-#define KAD_HELP_SLOTS 32
-#define KAD_HELP_MAX_FRONTIER 1024 // frontier entries of one chunk (the largest block size)
-struct KadHelp {
-    // the counters many warps update sit on cache lines of their own
-    alignas(128) int next;                // next arc handed out
-    alignas(128) int tail;                // side X's list tail during the shared expansion
-    alignas(128) unsigned long long next_dsum;
-    alignas(128) int met;                 // an arc reached the other side's frontier
-    alignas(128) int helpers;             // blocks inside as helpers
-    alignas(128) int state;               // 0 free, 3 being filled, 1 open, 2 closing
-    int owner;                            // slot (block) whose scratch the level belongs to
-    int X, tailY, cnt, total, watch;
-    uint32_t keyNext, sideX;
-    int stopped;                          // a warp saw the run's stop and skipped its arcs
-    unsigned long long pred_next, pred_m; // arcs into the next level / the meeting set
-    int32_t rs[KAD_HELP_MAX_FRONTIER];
-    int32_t off[KAD_HELP_MAX_FRONTIER];
-    unsigned long long sig[KAD_HELP_MAX_FRONTIER];
 };
 
 // Host-mapped page of a run (pinned host memory the kernel writes through).
@@ -148,11 +121,6 @@ struct SampleArgs {
     unsigned long long max_epochs; // forced stop after this many epochs (truncated runs); 0 = none
     // work counters [0..5], samples [6], SM cycles per phase [8..13] (KAD_WORK_WORDS)
     unsigned long long *work;
-    // shared expansions (KAD_HELP_SLOTS records, zeroed), or null: every block alone;
-    // chunks with at least help_min arcs are shared
-    KadHelp *help;
-    int help_min;
-    int help_max; // helper blocks per shared chunk
 };
 
 // ----------------------------------------------------------------- helpers

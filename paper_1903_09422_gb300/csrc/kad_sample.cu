@@ -42,6 +42,7 @@
 #define KAD_DEG_SCAN 64 // adjacency lists up to this length are always scanned
 #define KAD_PAIR_MIN_ARCS 1024 // rounds with fewer arcs always expand by scanning
 #define KAD_PAIR_COST 16       // one pairwise adjacency test counts as this many arc reads
+#define KAD_TBUF 64            // t-side trace steps warp 1 can buffer (longer: warp 0 traces both sides)
 
 namespace {
 
@@ -148,12 +149,7 @@ struct Smem {
     unsigned long long next_dsum;
     volatile int met;
     int abort; // the run stopped while this (adaptive) sample was in its BFS
-    int help_j;    // shared expansion this block owns or helps (-1 none)
-    int help_open; // shared expansions open when this block took its sample
-    int h_owner, h_X, h_tailY, h_cnt, h_total, h_watch;
-    uint32_t h_keyNext, h_sideX;
-    unsigned long long help_pn, help_pm;
-    int mcount;
+    int mcount;    // members of M recorded (the first m_cap ids are in m_id)
     int mid;
     int D;
     int s, t;
@@ -165,6 +161,16 @@ struct Smem {
     unsigned int prefix;
     unsigned long long P;
     unsigned long long r;
+    // the stream after the meeting draw (for the t-side trace in warp 1), the
+    // stream positions that must agree, and warp 1's buffered t-side vertices
+    unsigned long long st_w0, st_w1;
+    uint32_t st_blk;
+    int st_pos;
+    uint32_t st_end_blk, st_spec_blk;
+    int st_end_pos, st_spec_pos;
+    int tcount;
+    unsigned long long wt1;
+    int32_t tbuf_v[KAD_TBUF], tbuf_j[KAD_TBUF];
     unsigned long long sst;
     unsigned long long idx;
     unsigned long long k;
@@ -413,25 +419,76 @@ __device__ __forceinline__ void trace_from_level(const SampleArgs &a, const uint
     if (lane == 0) w_trace += pr;
 }
 
-// ---------------------------------------------------------------- closer
+// Trace one side z of the sample from the meeting vertex `cur` (distance d,
+// path count sc, row [rsC, reC)) back to its root, drawing one bounded number
+// per step from the stream (lane 0's copy; the warp follows).  Each chosen
+// vertex goes out directly (buf == nullptr) or into buf_v/buf_j for later.
+// Called by one warp.  Returns the number of buffered vertices, or -1 on error.
+template <int BLOCK>
+__device__ __noinline__ int trace_side(const SampleArgs &a, Smem<BLOCK> &sm, Stream &st, const uint32_t *label,
+                                          bool bsh, const uint32_t *bits, const unsigned long long *sigma,
+                                          const int32_t *list, int n, int z, int d, unsigned long long sc, int cur,
+                                          int rsC, int reC, int D, int32_t *out, int32_t *buf_v, int32_t *buf_j,
+                                          unsigned long long &w_trace) {
+    const int lane = threadIdx.x & 31;
+    int nb = 0;
+    while (d >= 1) {
+        unsigned long long r = 0;
+        if (lane == 0) r = st.uniform(sc, a.ctl);
+        r = __shfl_sync(FULL_MASK, r, 0);
+        int p_sel = -1, rs_sel = 0, re_sel = 0;
+        unsigned long long s_sel = 0;
+        const int ls = (d <= KAD_MAXLV) ? sm.lvs[z][d - 1] : 0;
+        const int lcnt = (d <= KAD_MAXLV) ? sm.lvs[z][d] - ls : KAD_LCAP + 1;
+        if (d == 1) {
+            // the only vertex at distance 0 is the root
+            p_sel = z ? sm.t : sm.s;
+            s_sel = 1ull;
+        } else if (!(a.debug & KAD_DEBUG_TRACE_SCAN) && reC - rsC > KAD_DEG_SCAN && lcnt <= KAD_LCAP) {
+            trace_from_level<BLOCK>(a, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel, s_sel, w_trace);
+            if (p_sel >= 0) {
+                rs_sel = __ldg(a.rp + p_sel);
+                re_sel = __ldg(a.rp + p_sel + 1);
+            }
+        } else {
+            trace_scan(a, label, bsh, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, rs_sel, re_sel, w_trace);
+        }
+        if (p_sel < 0) {
+            if (lane == 0) kad_set_err(a.ctl, KAD_DERR_TRACE);
+            return -1;
+        }
+        d--;
+        if (d >= 1) {
+            const int j = (z == 0) ? d : D - d;
+            if (!buf_v) {
+                if (lane == 0) emit(a, out, D, j, p_sel);
+            } else if (lane == 0) {
+                buf_v[nb] = p_sel;
+                buf_j[nb] = j;
+            }
+            nb++;
+        }
+        cur = p_sel;
+        sc = s_sel;
+        rsC = rs_sel;
+        reC = re_sel;
+    }
+    return nb;
+}
+
 // ---------------------------------------------------------------- expansion
-// What one warp needs to expand arcs of a frontier chunk: the slot's scratch,
-// the chunk (row starts, exclusive degree offsets and path counts of its cnt
-// frontier vertices, in shared memory), the round, and where new vertices,
-// their degree sum and a meeting are recorded (shared memory for a block alone,
-// a KadHelp record for a shared expansion).
+// What the warps of a block need to expand arcs of a frontier chunk: the slot's
+// scratch and the round.  The chunk itself -- row starts, exclusive degree
+// offsets and path counts of its cnt frontier vertices -- is in shared memory
+// (sm.rs, sm.off, sm.sig), and so are the list tail, the next frontier's degree
+// sum, the meeting flag and the recorded meeting set.
 struct ExpandCtx {
     uint32_t *label;
     unsigned long long *sigma, *sigma2;
     int32_t *list;
     uint32_t *bits;
-    const int32_t *s_rs, *s_off;
-    const unsigned long long *s_sig;
-    int cnt, X, tailY, n;
+    int cnt, X, tailY, n, mcap;
     uint32_t sideX, keyNext;
-    int *tail;
-    unsigned long long *next_dsum;
-    volatile int *met;
     bool bsh, watch;
 };
 
@@ -441,18 +498,21 @@ struct ExpandCtx {
 // independent loads in flight.  No block barrier is needed: an unlabelled
 // vertex can only become keyNext during the round (only side X labels, and
 // every earlier label has its bit set), so claims and path-count pushes commute,
-// and a fresh vertex's push need not wait for its claim's answer.  Returns true
-// (for the whole warp) when the run has stopped and this sample may give up.
-__device__ __forceinline__ bool expand_items(const SampleArgs &a, const ExpandCtx &c, int first, int stride,
-                                             int total, unsigned long long &pred_next, unsigned long long &pred_m) {
+// and a fresh vertex's push need not wait for its claim's answer.  The arc that
+// first marks a meeting vertex records it in M.  Returns true (for the whole
+// warp) when the run has stopped and this sample may give up.
+template <int BLOCK>
+__device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &sm, const ExpandCtx &c, int first,
+                                             int stride, int total, unsigned long long &pred_next,
+                                             unsigned long long &pred_m) {
     const int lane = threadIdx.x & 31;
     // lane 0 looks at the stop flag and every lane at the meeting flag (both
     // issued here, used below)
     int stop_now = 0;
     if (lane == 0 && c.watch) stop_now = *(volatile int *)&a.ctl->stop;
-    const int met_before = *c.met;
+    const int met_before = sm.met;
     int vv[KAD_ITEMS];
-    int ix[KAD_ITEMS]; // frontier entry of the arc (its sigma is s_sig[ix])
+    int ix[KAD_ITEMS]; // frontier entry of the arc (its sigma is sm.sig[ix])
     uint32_t ll[KAD_ITEMS];
 #pragma unroll
     for (int k = 0; k < KAD_ITEMS; k++) {
@@ -464,12 +524,12 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, const ExpandCt
             int lo = 0, hi = c.cnt - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (c.s_off[mid] <= e)
+                if (sm.off[mid] <= e)
                     lo = mid;
                 else
                     hi = mid - 1;
             }
-            vv[k] = __ldg(a.col + c.s_rs[lo] + (e - c.s_off[lo]));
+            vv[k] = __ldg(a.col + sm.rs[lo] + (e - sm.off[lo]));
             ix[k] = lo;
         }
     }
@@ -492,7 +552,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, const ExpandCt
         if (ll[k] != 0u && (ll[k] & KAD_SIDE) != c.sideX) reaches_y = 1;
     const bool warp_meets = __any_sync(FULL_MASK, reaches_y) != 0;
     if (__shfl_sync(FULL_MASK, stop_now, 0)) return true;
-    if (warp_meets && lane == 0) *c.met = 1;
+    if (warp_meets && lane == 0) sm.met = 1;
     const bool meeting_seen = warp_meets || met_before != 0;
     uint32_t old[KAD_ITEMS];
     unsigned long long prev[KAD_ITEMS];
@@ -507,17 +567,21 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, const ExpandCt
             if (meeting_seen) continue;
             old[k] = atomicCAS(c.label + v, 0u, c.keyNext);
             kind[k] = 1;
-            prev[k] = atomicAdd(c.sigma + v, c.s_sig[ix[k]]);
+            prev[k] = atomicAdd(c.sigma + v, sm.sig[ix[k]]);
         } else if (ll[k] != 0u) {
             const uint32_t lv = ll[k];
             if ((lv & KAD_KEY) == c.keyNext) {
                 kind[k] = 1;
-                prev[k] = atomicAdd(c.sigma + v, c.s_sig[ix[k]]);
+                prev[k] = atomicAdd(c.sigma + v, sm.sig[ix[k]]);
             } else if ((lv & KAD_SIDE) != c.sideX) {
-                // v is on the other side's frontier: the searches meet.
+                // v is on the other side's frontier: the searches meet.  The arc
+                // that first marks v records it in M.
                 kind[k] = 2;
-                if (!(lv & KAD_INM)) atomicOr(c.label + v, KAD_INM);
-                prev[k] = atomicAdd(c.sigma2 + v, c.s_sig[ix[k]]);
+                if (!(lv & KAD_INM) && !(atomicOr(c.label + v, KAD_INM) & KAD_INM)) {
+                    const int slot = atomicAdd(&sm.mcount, 1);
+                    if (slot < c.mcap) sm.m_id[slot] = v;
+                }
+                prev[k] = atomicAdd(c.sigma2 + v, sm.sig[ix[k]]);
             }
         }
     }
@@ -531,6 +595,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, const ExpandCt
         }
     }
     bool claimed[KAD_ITEMS];
+    bool any_m = false;
 #pragma unroll
     for (int k = 0; k < KAD_ITEMS; k++) {
         claimed[k] = fresh[k] && kind[k] == 1 && old[k] == 0u;
@@ -539,13 +604,14 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, const ExpandCt
         if (claimed[k]) bits_set(c.bsh, c.bits, vv[k]);
         if (kind[k] == 1) {
             pred_next++;
-            if (prev[k] + c.s_sig[ix[k]] < prev[k]) atomicOr(c.label + vv[k], KAD_OVF);
+            if (prev[k] + sm.sig[ix[k]] < prev[k]) atomicOr(c.label + vv[k], KAD_OVF);
         } else if (kind[k] == 2) {
             pred_m++;
-            *c.met = 1;
-            if (prev[k] + c.s_sig[ix[k]] < prev[k]) atomicOr(c.label + vv[k], KAD_OVF2);
+            any_m = true;
+            if (prev[k] + sm.sig[ix[k]] < prev[k]) atomicOr(c.label + vv[k], KAD_OVF2);
         }
     }
+    if (any_m) sm.met = 1;
     // new vertices: one list reservation and one degree-sum update per warp
     unsigned mask[KAD_ITEMS];
     int nclaim = 0;
@@ -558,7 +624,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, const ExpandCt
     }
     if (nclaim) {
         int pos0 = 0;
-        if (lane == 0) pos0 = atomicAdd(c.tail, nclaim);
+        if (lane == 0) pos0 = atomicAdd(&sm.tail[c.X], nclaim);
         pos0 = __shfl_sync(FULL_MASK, pos0, 0);
 #pragma unroll
         for (int k = 0; k < KAD_ITEMS; k++) {
@@ -572,211 +638,12 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, const ExpandCt
             pos0 += __popc(mask[k]);
         }
         const unsigned long long ds = warp_sum_u64(mydeg);
-        if (lane == 0) atomicAdd(c.next_dsum, ds);
+        if (lane == 0) atomicAdd(&sm.next_dsum, ds);
     }
     return false;
 }
 
-#define KAD_WARP_CHUNK (32 * KAD_ITEMS) // arcs a warp expands per call in a shared expansion
-#define KAD_WARP_GRAB (4 * KAD_WARP_CHUNK) // arcs a warp takes at a time
-#define KAD_HELP_WAIT 20000000          // bound of the owner's wait for stragglers (x ~100 ns)
-
-// One warp works through a shared expansion: take a chunk of arcs (the next one
-// is taken before the current one is expanded, hiding the atomic's latency) and
-// expand it, until no arcs are left.  After the run has stopped the warp still
-// takes chunks, without expanding them.  The warp's arc counts go to the record.
-// Every chunk handed out is finished by the warp that took it before that
-// warp's block leaves (helpers) or passes its barrier (owner), so once the
-// owner's warps are through and no helper is inside, the level is complete.
-// Returns whether this warp saw the stop.
-__device__ __forceinline__ bool help_warp_loop(const SampleArgs &a, KadHelp *h, const ExpandCtx &c, int total) {
-    const int lane = threadIdx.x & 31;
-    unsigned long long pn = 0, pm = 0;
-    bool stopped = false;
-    int ci = 0;
-    if (lane == 0) ci = atomicAdd(&h->next, KAD_WARP_GRAB);
-    ci = __shfl_sync(FULL_MASK, ci, 0);
-    while (ci < total) {
-        int cn = 0;
-        if (lane == 0) cn = atomicAdd(&h->next, KAD_WARP_GRAB);
-        const int end = min(total, ci + KAD_WARP_GRAB);
-        for (int q = ci; q < end && !stopped; q += KAD_WARP_CHUNK)
-            stopped = expand_items(a, c, q + lane, 32, end, pn, pm);
-        ci = __shfl_sync(FULL_MASK, cn, 0);
-    }
-    pn = warp_sum_u64(pn);
-    pm = warp_sum_u64(pm);
-    if (lane == 0) {
-        if (pn) atomicAdd(&h->pred_next, pn);
-        if (pm) atomicAdd(&h->pred_m, pm);
-        if (stopped) atomicExch(&h->stopped, 1);
-    }
-    return stopped;
-}
-
-// Owner side: publish the chunk as a shared expansion if a record is free;
-// returns the record index (the same in every thread) or -1.
-template <int BLOCK>
-__device__ int help_open(const SampleArgs &a, Smem<BLOCK> &sm, const ExpandCtx &c, int total) {
-    if (threadIdx.x == 0) {
-        int j = -1;
-        const int start = (int)(blockIdx.x % KAD_HELP_SLOTS);
-        for (int q = 0; q < KAD_HELP_SLOTS; q++) {
-            const int cand = (start + q) % KAD_HELP_SLOTS;
-            if (*(volatile int *)&a.help[cand].state == 0 && atomicCAS(&a.help[cand].state, 0, 3) == 0) {
-                j = cand;
-                break;
-            }
-        }
-        sm.help_j = j;
-    }
-    __syncthreads();
-    const int j = sm.help_j;
-    if (j < 0) return -1;
-    KadHelp *h = a.help + j;
-    for (int i = threadIdx.x; i < c.cnt; i += BLOCK) {
-        h->rs[i] = c.s_rs[i];
-        h->off[i] = c.s_off[i];
-        h->sig[i] = c.s_sig[i];
-    }
-    if (threadIdx.x == 0) {
-        h->owner = blockIdx.x;
-        h->X = c.X;
-        h->tailY = c.tailY;
-        h->cnt = c.cnt;
-        h->total = total;
-        h->watch = c.watch ? 1 : 0;
-        h->keyNext = c.keyNext;
-        h->sideX = c.sideX;
-        h->next = 0;
-        h->tail = *c.tail;
-        h->met = *c.met;
-        h->stopped = 0;
-        h->next_dsum = 0;
-        h->pred_next = 0;
-        h->pred_m = 0;
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicExch(&h->state, 1); // open: the fields above are published
-        atomicAdd(&a.ctl->help_open, 1);
-    }
-    return j;
-}
-
-// Owner side: expand with every warp, then close the record to newcomers and
-// wait (bounded) until no helper is inside; take the results, free the record.
-template <int BLOCK>
-__device__ void help_own(const SampleArgs &a, Smem<BLOCK> &sm, int j, const ExpandCtx &c0, int total, int X) {
-    KadHelp *h = a.help + j;
-    ExpandCtx c = c0;
-    c.tail = &h->tail;
-    c.next_dsum = &h->next_dsum;
-    c.met = &h->met;
-    help_warp_loop(a, h, c, total);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicExch(&h->state, 2); // closing: no new helper enters
-        kad_fence_sc();
-        int it = 0;
-        while (*(volatile int *)&h->helpers != 0 && it < KAD_HELP_WAIT) {
-            __nanosleep(100);
-            it++;
-        }
-        if (it >= KAD_HELP_WAIT) kad_set_err(a.ctl, KAD_DERR_HELP);
-        __threadfence();
-        sm.tail[X] = *(volatile int *)&h->tail;
-        sm.next_dsum += *(volatile unsigned long long *)&h->next_dsum;
-        if (*(volatile int *)&h->met) sm.met = 1;
-        // arcs skipped after the stop (by any warp) leave the level incomplete:
-        // the sample gives up
-        if (*(volatile int *)&h->stopped) sm.abort = 1;
-        sm.help_pn = *(volatile unsigned long long *)&h->pred_next;
-        sm.help_pm = *(volatile unsigned long long *)&h->pred_m;
-        atomicSub(&a.ctl->help_open, 1);
-        atomicExch(&h->state, 0);
-    }
-    __syncthreads();
-}
-
-// Helper side, between two samples of this block: join an open shared
-// expansion if there is one, work through it, leave.
-template <int BLOCK>
-__device__ void help_others(const SampleArgs &a, Smem<BLOCK> &sm, int32_t n) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (tid < 32) {
-        const int st = (lane < KAD_HELP_SLOTS) ? *(volatile int *)&a.help[lane].state : 0;
-        unsigned m = __ballot_sync(FULL_MASK, st == 1);
-        if (lane == 0) {
-            int j = -1;
-            const int rot = (int)(blockIdx.x % 32);
-            m = (m >> rot) | (rot ? (m << (32 - rot)) : 0u); // start looking at this block's own offset
-            while (m) {
-                const int cand = (__ffs(m) - 1 + rot) % 32;
-                m &= m - 1;
-                KadHelp *h = a.help + cand;
-                const int inside = atomicAdd(&h->helpers, 1);
-                kad_fence_sc();
-                if (inside < a.help_max && *(volatile int *)&h->state == 1 &&
-                    *(volatile int *)&h->next < *(volatile int *)&h->total) {
-                    j = cand;
-                    break;
-                }
-                atomicSub(&h->helpers, 1);
-            }
-            sm.help_j = j;
-            if (j >= 0) {
-                KadHelp *h = a.help + j;
-                sm.h_owner = *(volatile int *)&h->owner;
-                sm.h_X = *(volatile int *)&h->X;
-                sm.h_tailY = *(volatile int *)&h->tailY;
-                sm.h_cnt = *(volatile int *)&h->cnt;
-                sm.h_total = *(volatile int *)&h->total;
-                sm.h_watch = *(volatile int *)&h->watch;
-                sm.h_keyNext = *(volatile uint32_t *)&h->keyNext;
-                sm.h_sideX = *(volatile uint32_t *)&h->sideX;
-            }
-        }
-    }
-    __syncthreads();
-    const int j = sm.help_j;
-    if (j < 0) return;
-    KadHelp *h = a.help + j;
-    const int cnt = min(sm.h_cnt, BLOCK); // every block of a launch has BLOCK threads: cnt <= BLOCK
-    for (int i = tid; i < cnt; i += BLOCK) {
-        sm.rs[i] = __ldcg(h->rs + i);
-        sm.off[i] = __ldcg(h->off + i);
-        sm.sig[i] = __ldcg(h->sig + i);
-    }
-    __syncthreads();
-    const size_t soff = (size_t)sm.h_owner * (size_t)n;
-    ExpandCtx c;
-    c.label = a.label + soff;
-    c.sigma = a.sigma + soff;
-    c.sigma2 = a.sigma2 + soff;
-    c.list = a.list + soff;
-    c.bits = a.bits + (size_t)sm.h_owner * (size_t)a.nw;
-    c.s_rs = sm.rs;
-    c.s_off = sm.off;
-    c.s_sig = sm.sig;
-    c.cnt = cnt;
-    c.X = sm.h_X;
-    c.tailY = sm.h_tailY;
-    c.n = n;
-    c.sideX = sm.h_sideX;
-    c.keyNext = sm.h_keyNext;
-    c.tail = &h->tail;
-    c.next_dsum = &h->next_dsum;
-    c.met = &h->met;
-    c.bsh = false;
-    c.watch = sm.h_watch != 0;
-    help_warp_loop(a, h, c, sm.h_total);
-    __threadfence(); // this thread's writes to the owner's scratch, before leaving
-    __syncthreads();
-    if (tid == 0) atomicSub(&h->helpers, 1);
-}
-
+// ---------------------------------------------------------------- closer
 // Fold epoch k (sample rows of ring slot k mod R) into the counts, then
 // evaluate the stop rule on the consistent state after k+1 epochs.
 template <int BLOCK>
@@ -917,22 +784,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     if (a.mode == KAD_MODE_RING && blockIdx.x == 0) run_closer<BLOCK>(a, sm);
 
     for (;;) {
-        // ---------------------------------------------------- help, then next sample index
-        // A block between two samples first helps with another block's long level
-        // if one is open (before taking an index, so that no sample of its own
-        // waits meanwhile).
-        if (a.help) {
-            if (tid == 0) sm.help_open = *(volatile int *)&a.ctl->help_open;
-            __syncthreads();
-            if (sm.help_open > 0) {
-                const long long h0 = clock64();
-                help_others<BLOCK>(a, sm, n);
-                if (tid == 0) {
-                    sm.acc[7] += (unsigned long long)(clock64() - h0);
-                    if (sm.help_j >= 0) sm.acc[15]++;
-                }
-            }
-        }
+        // ---------------------------------------------------- next sample index
         if (tid == 0) {
             unsigned long long idx = ~0ull;
             int calib = 0;
@@ -974,6 +826,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             sm.tail[0] = sm.tail[1] = 0;
             sm.D = 0;
             sm.abort = 0;
+            sm.mcount = 0;
             if (__ldg(a.comp + s) == __ldg(a.comp + t)) {
                 label[s] = 1u;            // s side, level 0
                 label[t] = KAD_SIDE | 1u; // t side, level 0
@@ -1103,7 +956,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     for (int k = 0; k < 4; k++) {
                         prev[k] = 0;
                         if (!hit[k]) continue;
-                        atomicOr(label + pw[k], KAD_INM);
+                        if (!(atomicOr(label + pw[k], KAD_INM) & KAD_INM)) {
+                            const int slot = atomicAdd(&sm.mcount, 1);
+                            if (slot < mcap) sm.m_id[slot] = pw[k];
+                        }
                         prev[k] = atomicAdd(sigma2 + pw[k], sm.sig[pi[k]]);
                     }
 #pragma unroll
@@ -1146,35 +1002,19 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 ec.sigma2 = sigma2;
                 ec.list = list;
                 ec.bits = bits;
-                ec.s_rs = sm.rs;
-                ec.s_off = sm.off;
-                ec.s_sig = sm.sig;
                 ec.cnt = (levX == 0) ? 1 : cnt;
                 ec.X = X;
                 ec.tailY = tailY;
                 ec.n = n;
                 ec.sideX = sideX;
                 ec.keyNext = keyNext;
-                ec.tail = &sm.tail[X];
-                ec.next_dsum = &sm.next_dsum;
-                ec.met = &sm.met;
+                ec.mcap = mcap;
                 ec.bsh = bsh;
                 ec.watch = watch_stop;
-                // a chunk with many arcs (hub rows) is shared with blocks between samples
-                const int hj = (a.help && !bsh && total >= a.help_min) ? help_open<BLOCK>(a, sm, ec, total) : -1;
-                if (hj >= 0) {
-                    help_own<BLOCK>(a, sm, hj, ec, total, X);
-                    if (tid == 0) {
-                        pred_next += sm.help_pn;
-                        pred_m += sm.help_pm;
-                        sm.acc[14]++;
-                    }
-                } else {
-                    for (int base = 0; base < total; base += BLOCK * KAD_ITEMS) {
-                        if (expand_items(a, ec, base + tid, BLOCK, total, pred_next, pred_m)) {
-                            if (lane == 0) sm.abort = 1;
-                            break;
-                        }
+                for (int base = 0; base < total; base += BLOCK * KAD_ITEMS) {
+                    if (expand_items<BLOCK>(a, sm, ec, base + tid, BLOCK, total, pred_next, pred_m)) {
+                        if (lane == 0) sm.abort = 1;
+                        break;
                     }
                 }
                 __syncthreads();
@@ -1216,9 +1056,23 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
         if (D > 0) {
             const int Y = 1 - X;
             const int yb = sm.fb[Y], ye = sm.fe[Y];
-            if (tid == 0) sm.mcount = 0;
+            const bool recorded = sm.mcount <= mcap;
+            __syncthreads();
+            if (tid == 0 && !recorded) sm.mcount = 0;
             __syncthreads();
             unsigned long long part = 0;
+            if (recorded) {
+                // M was recorded by the arcs that first reached its members
+                for (int i = tid; i < sm.mcount; i += BLOCK) {
+                    const int v = sm.m_id[i];
+                    const uint32_t lv = kad_ld_u32(label + v);
+                    const unsigned long long sx = (lv & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + v);
+                    const unsigned long long sy = (lv & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + v);
+                    const unsigned long long w = kad_sat_mul(sx, sy);
+                    part = kad_sat_add(part, w);
+                    sm.m_w[i] = w;
+                }
+            } else
             for (int j = yb + tid; j < ye; j += BLOCK) {
                 const int v = __ldcg(list + phys(Y, j, n));
                 const uint32_t lv = kad_ld_u32(label + v);
@@ -1239,6 +1093,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 sm.sst = sst;
                 sm.r = st.uniform(sst ? sst : 1ull, a.ctl);
                 sm.mid = -1;
+                sm.st_w0 = st.w0;
+                sm.st_w1 = st.w1;
+                sm.st_blk = st.blk;
+                sm.st_pos = st.pos;
             }
             __syncthreads();
             const int mc = sm.mcount;
@@ -1322,60 +1180,77 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
         else if (a.mode == KAD_MODE_RECORD)
             row = (size_t)(idx - a.i0);
         int32_t *const out = calib ? nullptr : a.paths + row * (size_t)a.cap;
-        if (D > 0 && wid == 0) {
-            const int Y = 1 - X;
-            const int mid = sm.mid;
-            if (mid < 0 || mid >= n) {
-                if (lane == 0) kad_set_err(a.ctl, KAD_DERR_SELECT);
-            } else {
-                // distance and path count of the meeting vertex on each side:
-                // side X reaches it at level lev[X]+1 (count in sigma2), side Y
-                // holds it at level lev[Y] (count in sigma)
-                const uint32_t lm = kad_ld_u32(label + mid);
-                const int dX = sm.lev[X] + 1, dY = sm.lev[Y];
-                const unsigned long long gX = (lm & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + mid);
-                const unsigned long long gY = (lm & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + mid);
-                if (lane == 0) emit(a, out, D, (X == 0) ? dX : dY, mid);
-                const int rsM = __ldg(a.rp + mid), reM = __ldg(a.rp + mid + 1);
-                for (int z = 0; z < 2; z++) {
-                    int cur = mid, d = (z == X) ? dX : dY;
-                    unsigned long long sc = (z == X) ? gX : gY;
-                    int rsC = rsM, reC = reM;
-                    while (d >= 1) {
-                        unsigned long long r = 0;
-                        if (lane == 0) r = st.uniform(sc, a.ctl);
-                        r = __shfl_sync(FULL_MASK, r, 0);
-                        int p_sel = -1, rs_sel = 0, re_sel = 0;
-                        unsigned long long s_sel = 0;
-                        const int ls = (d <= KAD_MAXLV) ? sm.lvs[z][d - 1] : 0;
-                        const int lcnt = (d <= KAD_MAXLV) ? sm.lvs[z][d] - ls : KAD_LCAP + 1;
-                        if (d == 1) {
-                            // the only vertex at distance 0 is the root
-                            p_sel = z ? sm.t : sm.s;
-                            s_sel = 1ull;
-                        } else if (!(a.debug & KAD_DEBUG_TRACE_SCAN) && reC - rsC > KAD_DEG_SCAN && lcnt <= KAD_LCAP) {
-                            trace_from_level<BLOCK>(a, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel,
-                                                    s_sel, sm.acc[4]);
-                            if (p_sel >= 0) {
-                                rs_sel = __ldg(a.rp + p_sel);
-                                re_sel = __ldg(a.rp + p_sel + 1);
-                            }
-                        } else {
-                            trace_scan(a, label, bsh, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, rs_sel, re_sel,
-                                       sm.acc[4]);
-                        }
-                        if (p_sel < 0) {
-                            if (lane == 0) kad_set_err(a.ctl, KAD_DERR_TRACE);
-                            break;
-                        }
-                        d--;
-                        if (lane == 0 && d >= 1) emit(a, out, D, z == 0 ? d : D - d, p_sel);
-                        cur = p_sel;
-                        sc = s_sel;
-                        rsC = rs_sel;
-                        reC = re_sel;
-                    }
-                }
+        // The s side (warp 0) and the t side (warp 1) are traced at the same
+        // time.  The t side's draws follow the s side's in the stream; warp 1
+        // starts where the s side ends if none of its draws is rejected (each
+        // then takes one word) and buffers its vertices.  If warp 0 ends
+        // elsewhere (a rejection, probability below 2^-24 per draw for counts
+        // under 2^40), warp 0 traces the t side again from the right place.
+        const int mid = sm.mid;
+        const bool traced = D > 0 && mid >= 0 && mid < n;
+        if (D > 0 && !traced && tid == 0) kad_set_err(a.ctl, KAD_DERR_SELECT);
+        int dz[2] = {0, 0};
+        unsigned long long gz[2] = {0, 0};
+        int rsM = 0, reM = 0;
+        if (traced && wid < 2) {
+            // distance and path count of the meeting vertex on each side: side X
+            // reaches it at level lev[X]+1 (count in sigma2), side Y holds it at
+            // level lev[Y] (count in sigma)
+            const uint32_t lm = kad_ld_u32(label + mid);
+            const int dX = sm.lev[X] + 1, dY = sm.lev[1 - X];
+            const unsigned long long gX = (lm & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + mid);
+            const unsigned long long gY = (lm & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + mid);
+            dz[0] = (X == 0) ? dX : dY;
+            dz[1] = (X == 1) ? dX : dY;
+            gz[0] = (X == 0) ? gX : gY;
+            gz[1] = (X == 1) ? gX : gY;
+            rsM = __ldg(a.rp + mid);
+            reM = __ldg(a.rp + mid + 1);
+        }
+        const bool spec = traced && dz[1] <= KAD_TBUF && !(a.debug & KAD_DEBUG_SERIAL_TRACE);
+        if (traced && wid == 0) {
+            if (lane == 0) emit(a, out, D, dz[0], mid);
+            trace_side<BLOCK>(a, sm, st, label, bsh, bits, sigma, list, n, 0, dz[0], gz[0], mid, rsM, reM, D, out,
+                              nullptr, nullptr, sm.acc[4]);
+            if (lane == 0) {
+                sm.st_end_blk = st.blk;
+                sm.st_end_pos = st.pos;
+            }
+            if (!spec)
+                trace_side<BLOCK>(a, sm, st, label, bsh, bits, sigma, list, n, 1, dz[1], gz[1], mid, rsM, reM, D,
+                                  out, nullptr, nullptr, sm.acc[4]);
+        } else if (spec && wid == 1) {
+            Stream s1;
+            unsigned long long wt = 0;
+            if (lane == 0) {
+                s1.k0 = a.key0;
+                s1.k1 = a.key1;
+                s1.idx = idx;
+                s1.dom = sm.dom;
+                s1.blk = sm.st_blk;
+                s1.pos = sm.st_pos;
+                s1.w0 = sm.st_w0;
+                s1.w1 = sm.st_w1;
+                for (int q = 0; q < dz[0]; q++) s1.next(); // one word per s-side step
+                sm.st_spec_blk = s1.blk;
+                sm.st_spec_pos = s1.pos;
+            }
+            const int nb = trace_side<BLOCK>(a, sm, s1, label, bsh, bits, sigma, list, n, 1, dz[1], gz[1], mid, rsM,
+                                             reM, D, out, sm.tbuf_v, sm.tbuf_j, wt);
+            if (lane == 0) {
+                sm.tcount = nb;
+                sm.wt1 = wt;
+            }
+        }
+        __syncthreads();
+        if (spec) {
+            if (sm.st_end_blk == sm.st_spec_blk && sm.st_end_pos == sm.st_spec_pos) {
+                if (wid == 1 && lane < sm.tcount) emit(a, out, D, sm.tbuf_j[lane], sm.tbuf_v[lane]);
+                if (wid == 1 && lane + 32 < sm.tcount) emit(a, out, D, sm.tbuf_j[lane + 32], sm.tbuf_v[lane + 32]);
+                if (tid == 0) sm.acc[4] += sm.wt1;
+            } else if (wid == 0) {
+                trace_side<BLOCK>(a, sm, st, label, bsh, bits, sigma, list, n, 1, dz[1], gz[1], mid, rsM, reM, D, out,
+                                  nullptr, nullptr, sm.acc[4]);
             }
         }
         if (tid == 0) {

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libkad.so")
 
 KAD_GRAPH_TRUSTED = 1
 KAD_RUN_TIMING = 1
-KAD_RUN_NO_AUTOTUNE = 2
+KAD_RUN_AUTOTUNE = 2
 WORK_NAMES = ("expanded", "scanned", "labelled", "pred_arcs", "trace_arcs", "increments")
 
 
@@ -29,8 +29,7 @@ class Options(ctypes.Structure):
     _fields_ = [("epoch_size", ctypes.c_uint32), ("calib_div", ctypes.c_uint32), ("ring_epochs", ctypes.c_uint32),
                 ("slots", ctypes.c_int32), ("mcap", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("flags", ctypes.c_uint32), ("debug", ctypes.c_uint32),
-                ("max_epochs", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
-                ("share_min_arcs", ctypes.c_int32), ("share_max_helpers", ctypes.c_int32)]
+                ("max_epochs", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):
@@ -48,8 +47,7 @@ class Result(ctypes.Structure):
                 ("phase_cycles", ctypes.c_uint64 * 6), ("t_host_ms", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
                 ("t_table_ms", ctypes.c_double), ("t_dev_calib_ms", ctypes.c_double),
                 ("t_dev_first_close_ms", ctypes.c_double), ("t_dev_stop_ms", ctypes.c_double),
-                ("t_dev_end_ms", ctypes.c_double), ("issued_at_stop", ctypes.c_uint64),
-                ("shared_levels", ctypes.c_uint64), ("helper_joins", ctypes.c_uint64), ("help_cycles", ctypes.c_uint64)]
+                ("t_dev_end_ms", ctypes.c_double), ("issued_at_stop", ctypes.c_uint64)]
 
 PHASE_NAMES = ("draw", "bfs", "meet", "trace", "reset", "close")
 
@@ -279,8 +277,7 @@ def _result_scalars(r):
                                     "t_calib_ms", "t_ads_ms", "t_ads_kernel_ms", "ads_launches", "slots_used",
                                     "kernel_launches", "block_threads_used", "blocks_per_sm_used", "t_host_ms",
                                     "t_setup_ms", "t_table_ms", "t_dev_calib_ms", "t_dev_first_close_ms",
-                                    "t_dev_stop_ms", "t_dev_end_ms", "issued_at_stop", "shared_levels",
-                                    "helper_joins", "help_cycles")}
+                                    "t_dev_stop_ms", "t_dev_end_ms", "issued_at_stop")}
     d["counters"] = dict(zip(WORK_NAMES, (int(x) for x in r.work)))
     d["phase_cycles"] = dict(zip(PHASE_NAMES, (int(x) for x in r.phase_cycles)))
     return d

@@ -93,9 +93,9 @@ def test_full_run_matches_oracle(kad, name):
                                  dict(block_threads=512, blocks_per_sm=2), dict(block_threads=256, blocks_per_sm=4), dict(slots=1), dict(slots=7),
                                  dict(mcap=0), dict(mcap=1), dict(ring_epochs=2), dict(slots=3, ring_epochs=2),
                                  dict(epoch_size=250), dict(debug=1), dict(debug=2), dict(debug=4),
-                                 dict(debug=2, block_threads=512, blocks_per_sm=2), dict(debug=8), dict(debug=16),
-                                 dict(debug=16, block_threads=128), dict(debug=16, slots=7),
-                                 dict(debug=16, block_threads=1024)])
+                                 dict(debug=2, block_threads=512, blocks_per_sm=2), dict(debug=8),
+                                 dict(block_threads=128, blocks_per_sm=8),
+                                 dict(block_threads=1024, blocks_per_sm=1)])
 def test_result_independent_of_launch_configuration(kad, opt):
     g = gen.rmat(12, 8, seed=1)
     eps, delta, seed = 0.03, 0.1, 11
@@ -123,19 +123,17 @@ def test_meeting_round_methods_agree_on_hub_graph(kad):
         assert a["counters"][k] == orc["counters"][k] == b["counters"][k], k
 
 
-def test_shared_expansions_on_hub_graph(kad):
-    # Levels expanded jointly by their owner and blocks between samples (every
-    # level with at least 256 arcs is shared) give the oracle's records, work
-    # counters and full-run counts; so does expanding every level alone.
+def test_hub_graph_records_and_runs_per_variant(kad):
+    # A graph with hub rows (long levels, meetings found mid-level, samples
+    # abandoned after the stop): records, work counters and full-run counts
+    # equal the oracle's under several kernel variants.
     g = gen.rmat(15, 16, seed=5)
     orc = O.samples(g, 21, 0, 2000)
     ref = O.kadabra(g, 0.02, 0.1, 21)
     with kad.Graph.from_csr(g) as G:
-        shared = G.sample_records(21, 0, 2000, debug=16)
-        alone = G.sample_records(21, 0, 2000, debug=8)
-        runs = [G.run(0.02, 0.1, 21, debug=d, block_threads=bt, blocks_per_sm=bps)
-                for d, bt, bps in ((16, 512, 2), (16, 256, 4), (0, 512, 2), (8, 512, 2))]
-    for rec in (shared, alone):
+        recs = [G.sample_records(21, 0, 2000, block_threads=bt, blocks_per_sm=bps) for bt, bps in ((512, 2), (256, 4))]
+        runs = [G.run(0.02, 0.1, 21, block_threads=bt, blocks_per_sm=bps) for bt, bps in ((512, 2), (256, 4), (128, 8))]
+    for rec in recs:
         compare_records(rec, orc)
         for k in ("expanded", "scanned", "labelled", "pred_arcs", "increments"):
             assert rec["counters"][k] == orc["counters"][k], k
@@ -184,11 +182,13 @@ def test_autotuner_keeps_results_and_choice(kad):
     assert g.n >= 16384
     ref = O.kadabra(g, 0.05, 0.1, 8)
     with kad.Graph.from_csr(g) as G:
-        r1 = G.run(0.05, 0.1, 8)
-        r2 = G.run(0.05, 0.1, 8)
+        r1 = G.run(0.05, 0.1, 8, flags=kad.KAD_RUN_AUTOTUNE)
+        r2 = G.run(0.05, 0.1, 8, flags=kad.KAD_RUN_AUTOTUNE)
+        r3 = G.run(0.05, 0.1, 8)  # without the flag: 512x2
     assert (r1["block_threads_used"], r1["blocks_per_sm_used"]) in {(512, 2), (256, 4), (256, 2), (1024, 1), (128, 8)}
     assert (r1["block_threads_used"], r1["blocks_per_sm_used"]) == (r2["block_threads_used"], r2["blocks_per_sm_used"])
-    for r in (r1, r2):
+    assert (r3["block_threads_used"], r3["blocks_per_sm_used"]) == (512, 2)
+    for r in (r1, r2, r3):
         assert r["tau"] == ref["tau"]
         np.testing.assert_array_equal(r["counts"], ref["counts"])
 
