@@ -425,7 +425,7 @@ __device__ __forceinline__ void trace_from_level(const SampleArgs &a, const uint
 // vertex goes out directly (buf == nullptr) or into buf_v/buf_j for later.
 // Called by one warp.  Returns the number of buffered vertices, or -1 on error.
 template <int BLOCK>
-__device__ __noinline__ int trace_side(const SampleArgs &a, Smem<BLOCK> &sm, Stream &st, const uint32_t *label,
+__device__ __forceinline__ int trace_side(const SampleArgs &a, Smem<BLOCK> &sm, Stream &st, const uint32_t *label,
                                           bool bsh, const uint32_t *bits, const unsigned long long *sigma,
                                           const int32_t *list, int n, int z, int d, unsigned long long sc, int cur,
                                           int rsC, int reC, int D, int32_t *out, int32_t *buf_v, int32_t *buf_j,
@@ -1024,11 +1024,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             w_pred += met ? pred_m : pred_next;
             __syncthreads();
             if (tid == 0) {
-                if (sm.abort || (watch_stop && !met && *(volatile int *)&a.ctl->stop)) {
-                    // The run has stopped: this sample lies beyond the stop epoch and
-                    // is never counted.  Give up (the reset below also clears sigma2
-                    // on the other side's frontier, where a meeting may have begun).
-                    sm.abort = 1;
+                if (sm.abort) {
+                    // An expansion pass saw the run's stop: this sample lies beyond
+                    // the stop epoch and is never counted.  Give up (the reset below
+                    // also clears sigma2 on the other side's frontier, where a
+                    // meeting may have begun).
                     sm.D = 0;
                 } else if (met) {
                     sm.D = sm.lev[X] + 1 + sm.lev[Y];
@@ -1208,50 +1208,60 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             reM = __ldg(a.rp + mid + 1);
         }
         const bool spec = traced && dz[1] <= KAD_TBUF && !(a.debug & KAD_DEBUG_SERIAL_TRACE);
-        if (traced && wid == 0) {
-            if (lane == 0) emit(a, out, D, dz[0], mid);
-            trace_side<BLOCK>(a, sm, st, label, bsh, bits, sigma, list, n, 0, dz[0], gz[0], mid, rsM, reM, D, out,
-                              nullptr, nullptr, sm.acc[4]);
-            if (lane == 0) {
-                sm.st_end_blk = st.blk;
-                sm.st_end_pos = st.pos;
-            }
-            if (!spec)
-                trace_side<BLOCK>(a, sm, st, label, bsh, bits, sigma, list, n, 1, dz[1], gz[1], mid, rsM, reM, D,
-                                  out, nullptr, nullptr, sm.acc[4]);
-        } else if (spec && wid == 1) {
-            Stream s1;
-            unsigned long long wt = 0;
-            if (lane == 0) {
-                s1.k0 = a.key0;
-                s1.k1 = a.key1;
-                s1.idx = idx;
-                s1.dom = sm.dom;
-                s1.blk = sm.st_blk;
-                s1.pos = sm.st_pos;
-                s1.w0 = sm.st_w0;
-                s1.w1 = sm.st_w1;
-                for (int q = 0; q < dz[0]; q++) s1.next(); // one word per s-side step
-                sm.st_spec_blk = s1.blk;
-                sm.st_spec_pos = s1.pos;
-            }
-            const int nb = trace_side<BLOCK>(a, sm, s1, label, bsh, bits, sigma, list, n, 1, dz[1], gz[1], mid, rsM,
-                                             reM, D, out, sm.tbuf_v, sm.tbuf_j, wt);
-            if (lane == 0) {
-                sm.tcount = nb;
-                sm.wt1 = wt;
-            }
+        if (spec && wid == 1 && lane == 0) {
+            // warp 1's stream: the one after the meeting draw, one word further per s-side step
+            st.k0 = a.key0;
+            st.k1 = a.key1;
+            st.idx = idx;
+            st.dom = sm.dom;
+            st.blk = sm.st_blk;
+            st.pos = sm.st_pos;
+            st.w0 = sm.st_w0;
+            st.w1 = sm.st_w1;
+            for (int q = 0; q < dz[0]; q++) st.next();
+            sm.st_spec_blk = st.blk;
+            sm.st_spec_pos = st.pos;
         }
-        __syncthreads();
-        if (spec) {
-            if (sm.st_end_blk == sm.st_spec_blk && sm.st_end_pos == sm.st_spec_pos) {
-                if (wid == 1 && lane < sm.tcount) emit(a, out, D, sm.tbuf_j[lane], sm.tbuf_v[lane]);
-                if (wid == 1 && lane + 32 < sm.tcount) emit(a, out, D, sm.tbuf_j[lane + 32], sm.tbuf_v[lane + 32]);
-                if (tid == 0) sm.acc[4] += sm.wt1;
+        // Two phases with one trace loop.  Phase 0: warp 0 traces the s side and
+        // warp 1 the t side into its buffer.  Phase 1: the buffer goes out if the
+        // stream positions agree; else (or without speculation) warp 0 traces
+        // the t side from its own stream.
+        for (int ph = 0; ph < 2 && traced; ph++) {
+            int z = -1;
+            bool buffered = false;
+            if (ph == 0) {
+                if (wid == 0) z = 0;
+                if (wid == 1 && spec) {
+                    z = 1;
+                    buffered = true;
+                }
             } else if (wid == 0) {
-                trace_side<BLOCK>(a, sm, st, label, bsh, bits, sigma, list, n, 1, dz[1], gz[1], mid, rsM, reM, D, out,
-                                  nullptr, nullptr, sm.acc[4]);
+                if (!spec || sm.st_end_blk != sm.st_spec_blk || sm.st_end_pos != sm.st_spec_pos) z = 1;
+            } else if (wid == 1 && spec && sm.st_end_blk == sm.st_spec_blk && sm.st_end_pos == sm.st_spec_pos) {
+                if (lane < sm.tcount) emit(a, out, D, sm.tbuf_j[lane], sm.tbuf_v[lane]);
+                if (lane + 32 < sm.tcount) emit(a, out, D, sm.tbuf_j[lane + 32], sm.tbuf_v[lane + 32]);
+                if (lane == 0) sm.acc[4] += sm.wt1;
             }
+            if (z >= 0) {
+                unsigned long long wt = 0;
+                if (z == 0 && lane == 0) emit(a, out, D, dz[0], mid);
+                const int nb = trace_side<BLOCK>(a, sm, st, label, bsh, bits, sigma, list, n, z, z ? dz[1] : dz[0],
+                                                 z ? gz[1] : gz[0], mid, rsM, reM, D, out,
+                                                 buffered ? sm.tbuf_v : nullptr, buffered ? sm.tbuf_j : nullptr, wt);
+                if (lane == 0) {
+                    if (buffered) {
+                        sm.tcount = nb;
+                        sm.wt1 = wt;
+                    } else {
+                        sm.acc[4] += wt;
+                    }
+                    if (ph == 0 && z == 0) {
+                        sm.st_end_blk = st.blk;
+                        sm.st_end_pos = st.pos;
+                    }
+                }
+            }
+            __syncthreads();
         }
         if (tid == 0) {
             const int inc = (D > 0) ? D - 1 : 0;
