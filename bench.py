@@ -41,10 +41,12 @@ UNIT = "samples/s"
 # counted: they depend on how the predecessors are found, not on the sample.
 BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=0, increments=4)
 
-# DRAM traffic of the adaptive-phase sampling kernel measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum), bytes per computed sample, for
-# the kernel source it was taken on; None when not measured for the current kernel.
-NCU_TRAFFIC_PER_SAMPLE = {}
+# DRAM traffic of the sampling kernel measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum), bytes per computed sample, for the current kernel source;
+# a workload without an entry reports traffic null.  rmat20: 5.17 GB over a launch
+# of 31,000 samples; rmat18: 1.67 GB over 31,000 (profiles/k_sample_rmat20_dram.md,
+# profiles/k_sample_rmat18_full.md).
+NCU_TRAFFIC_PER_SAMPLE = {"rmat20": 166_792, "rmat18": 53_892}
 
 
 def alg_bytes(counters):
