@@ -147,6 +147,19 @@ def dist_setup(n_gpus):
     return rank, world, dist
 
 
+def reduce_ranks(dist, total_ms, samples, computed, device):
+    """Whole-job figures of the replicas: the slowest rank's time, the samples of
+    all ranks.  Without a process group the rank's own figures."""
+    if not dist:
+        return total_ms, samples, computed
+    import torch
+    t = torch.tensor([total_ms, float(samples), float(computed)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return mx[0].item(), t[1].item(), t[2].item()
+
+
 def graph_for(workload):
     from paper_1903_09422_gb300 import gen
     w = gen.WORKLOADS[workload]
@@ -406,14 +419,7 @@ def main():
     total_ms = sum(step_ms)
     samples = sum(r["tau"] + r["calib_samples"] for r in results)
     computed = sum(r["samples_computed"] for r in results)  # calibration + adaptive
-    if dist:
-        t = torch.tensor([total_ms, float(samples), float(computed)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_all, samples_all, computed_all = mx[0].item(), t[1].item(), t[2].item()
-    else:
-        total_ms_all, samples_all, computed_all = total_ms, samples, computed
+    total_ms_all, samples_all, computed_all = reduce_ranks(dist, total_ms, samples, computed, dev)
 
     # ---- end to end through the C ABI with host buffers: pinned CSR -> graph
     # create (copy + set-up) -> run -> b~ back to pinned host memory
