@@ -146,9 +146,12 @@ struct Smem {
     int root_rs[2];
     int lvs[2][KAD_MAXLV + 2]; // logical list start of level l, l <= KAD_MAXLV + 1
     unsigned long long dsum[2];
-    unsigned long long next_dsum;
-    volatile int met;
+    // per round r, slot r & 1: the next frontier's degree sum and the meeting
+    // flag (two slots, so the next round's are cleared while this round's are read)
+    unsigned long long next_dsum[2];
+    volatile int met[2];
     int abort; // the run stopped while this (adaptive) sample was in its BFS
+    int chunk_total; // arcs of a one-vertex chunk
     int mcount;    // members of M recorded (the first m_cap ids are in m_id)
     int mid;
     int D;
@@ -181,6 +184,8 @@ struct Smem {
 
 template <int BLOCK>
 __device__ __forceinline__ int block_excl_scan(int v, int *wtmp, int &total) {
+    // one barrier: every thread adds up the warp totals it needs (wtmp is not
+    // written again before the caller's next barrier)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int x = v;
 #pragma unroll
@@ -190,20 +195,15 @@ __device__ __forceinline__ int block_excl_scan(int v, int *wtmp, int &total) {
     }
     if (lane == 31) wtmp[wid] = x;
     __syncthreads();
-    if (wid == 0) {
-        int w = (lane < BLOCK / 32) ? wtmp[lane] : 0;
+    int pre = 0, tot = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL_MASK, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < BLOCK / 32) wtmp[lane] = w;
+    for (int w = 0; w < BLOCK / 32; w++) {
+        const int t = wtmp[w];
+        pre += (w < wid) ? t : 0;
+        tot += t;
     }
-    __syncthreads();
-    const int res = ((wid > 0) ? wtmp[wid - 1] : 0) + x - v;
-    total = wtmp[BLOCK / 32 - 1];
-    __syncthreads();
-    return res;
+    total = tot;
+    return pre + x - v;
 }
 
 // Saturating sum over the block (saturating addition is associative and
@@ -488,6 +488,7 @@ struct ExpandCtx {
     int32_t *list;
     uint32_t *bits;
     int cnt, X, tailY, n, mcap;
+    int rb; // round parity: slot of sm.met / sm.next_dsum
     uint32_t sideX, keyNext;
     bool bsh, watch;
 };
@@ -510,7 +511,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
     // issued here, used below)
     int stop_now = 0;
     if (lane == 0 && c.watch) stop_now = *(volatile int *)&a.ctl->stop;
-    const int met_before = sm.met;
+    const int met_before = sm.met[c.rb];
     int vv[KAD_ITEMS];
     int ix[KAD_ITEMS]; // frontier entry of the arc (its sigma is sm.sig[ix])
     uint32_t ll[KAD_ITEMS];
@@ -552,7 +553,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
         if (ll[k] != 0u && (ll[k] & KAD_SIDE) != c.sideX) reaches_y = 1;
     const bool warp_meets = __any_sync(FULL_MASK, reaches_y) != 0;
     if (__shfl_sync(FULL_MASK, stop_now, 0)) return true;
-    if (warp_meets && lane == 0) sm.met = 1;
+    if (warp_meets && lane == 0) sm.met[c.rb] = 1;
     const bool meeting_seen = warp_meets || met_before != 0;
     uint32_t old[KAD_ITEMS];
     unsigned long long prev[KAD_ITEMS];
@@ -611,7 +612,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
             if (prev[k] + sm.sig[ix[k]] < prev[k]) atomicOr(c.label + vv[k], KAD_OVF2);
         }
     }
-    if (any_m) sm.met = 1;
+    if (any_m) sm.met[c.rb] = 1;
     // new vertices: one list reservation and one degree-sum update per warp
     unsigned mask[KAD_ITEMS];
     int nclaim = 0;
@@ -638,7 +639,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
             pos0 += __popc(mask[k]);
         }
         const unsigned long long ds = warp_sum_u64(mydeg);
-        if (lane == 0) atomicAdd(&sm.next_dsum, ds);
+        if (lane == 0) atomicAdd(&sm.next_dsum[c.rb], ds);
     }
     return false;
 }
@@ -847,6 +848,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 sm.dsum[0] = (unsigned long long)(__ldg(a.rp + s + 1) - sm.root_rs[0]);
                 sm.dsum[1] = (unsigned long long)(__ldg(a.rp + t + 1) - sm.root_rs[1]);
                 sm.D = -1; // searching
+                // round 0: its flags, and its expansion counted ahead (one root)
+                sm.met[0] = 0;
+                sm.next_dsum[0] = 0;
+                sm.acc[0] += 1ull;
+                sm.acc[1] += (sm.dsum[0] <= sm.dsum[1]) ? sm.dsum[0] : sm.dsum[1];
             }
             __threadfence_block();
         }
@@ -858,15 +864,21 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             sm.tmark = now;
         }
         // ---------------------------------------------------- balanced bidirectional BFS
+        // Barriers per round: the degree scan (one or two), the end of each
+        // chunk, and the round's close.  The round's state is read without one:
+        // thread 0 writes it only in the round's close, after a barrier, and the
+        // next round's flags and counters are prepared there too (slot rb ^ 1).
         int X = 0;
+        int rnd = 0;
         while (sm.D < 0) {
+            const int rb = rnd & 1;
             X = (sm.dsum[0] <= sm.dsum[1]) ? 0 : 1;
             const int Y = 1 - X;
             const int fb = sm.fb[X], fe = sm.fe[X];
             const int levX = sm.lev[X];
             const int tailY = sm.tail[Y];
-            __syncthreads();
             if (fb == fe || levX + 2 > (int)KAD_LVL) {
+                __syncthreads(); // everyone has read the round's state
                 if (tid == 0) {
                     if (fb != fe) kad_set_err(a.ctl, KAD_DERR_LEVEL);
                     sm.D = 0; // no path
@@ -884,13 +896,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             // this round, and the expansion below runs as usual.
             const bool pairs = !(a.debug & KAD_DEBUG_FULL_SCAN) && fx <= BLOCK && sm.dsum[X] >= KAD_PAIR_MIN_ARCS &&
                                (unsigned long long)fx * (unsigned long long)fy * KAD_PAIR_COST < sm.dsum[X];
-            if (tid == 0) {
-                sm.acc[0] += (unsigned long long)(fe - fb);
-                sm.acc[1] += sm.dsum[X];
-                sm.met = 0;
-                sm.next_dsum = 0;
-            }
-            __syncthreads();
             unsigned long long pred_next = 0, pred_m = 0;
             if (pairs) {
                 if (tid < fx) {
@@ -966,14 +971,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     for (int k = 0; k < 4; k++) {
                         if (!hit[k]) continue;
                         pred_m++;
-                        sm.met = 1;
+                        sm.met[rb] = 1;
                         if (prev[k] + sm.sig[pi[k]] < prev[k]) atomicOr(label + pw[k], KAD_OVF2);
                     }
                 }
                 __syncthreads();
             }
             // a meeting found by the pairwise test completes the round
-            const int expand_end = (pairs && sm.met) ? fb : fe;
+            const int expand_end = (pairs && sm.met[rb]) ? fb : fe;
             for (int cb = fb; cb < expand_end; cb += BLOCK) {
                 const int cnt = min(BLOCK, fe - cb);
                 int d = 0;
@@ -992,10 +997,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     sm.sig[tid] = (lu & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + u);
                     d = re - rs;
                 }
+                // exclusive degree offsets of the chunk: a single vertex needs no scan
                 int total;
-                const int excl = block_excl_scan<BLOCK>(d, sm.wtmp, total);
-                if (tid < cnt) sm.off[tid] = excl;
-                __syncthreads();
+                if (cnt == 1) {
+                    if (tid == 0) {
+                        sm.off[0] = 0;
+                        sm.chunk_total = d;
+                    }
+                    __syncthreads();
+                    total = sm.chunk_total;
+                } else {
+                    const int excl = block_excl_scan<BLOCK>(d, sm.wtmp, total);
+                    if (tid < cnt) sm.off[tid] = excl;
+                    __syncthreads();
+                }
                 ExpandCtx ec;
                 ec.label = label;
                 ec.sigma = sigma;
@@ -1009,6 +1024,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 ec.sideX = sideX;
                 ec.keyNext = keyNext;
                 ec.mcap = mcap;
+                ec.rb = rb;
                 ec.bsh = bsh;
                 ec.watch = watch_stop;
                 for (int base = 0; base < total; base += BLOCK * KAD_ITEMS) {
@@ -1020,9 +1036,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 __syncthreads();
                 if (sm.abort) break;
             }
-            const int met = sm.met;
+            // every warp's passes ended at the chunk's barrier: this round's flag is final
+            const int met = sm.met[rb];
             w_pred += met ? pred_m : pred_next;
-            __syncthreads();
             if (tid == 0) {
                 if (sm.abort) {
                     // An expansion pass saw the run's stop: this sample lies beyond
@@ -1039,10 +1055,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     sm.fe[X] = tl;
                     sm.lev[X] = levX + 1;
                     if (levX + 2 <= KAD_MAXLV + 1) sm.lvs[X][levX + 2] = tl;
-                    sm.dsum[X] = sm.next_dsum;
+                    sm.dsum[X] = sm.next_dsum[rb];
+                    // the next round: its flags, and its expansion counted ahead
+                    const int Xn = (sm.dsum[0] <= sm.dsum[1]) ? 0 : 1;
+                    sm.met[rb ^ 1] = 0;
+                    sm.next_dsum[rb ^ 1] = 0;
+                    sm.acc[0] += (unsigned long long)(sm.fe[Xn] - sm.fb[Xn]);
+                    sm.acc[1] += sm.dsum[Xn];
                 }
             }
             __syncthreads();
+            rnd++;
         }
 
         if (tid == 0) {
