@@ -235,12 +235,12 @@ def serve_graphs(count, seed=20261203):
     return out
 
 
-def open_loop(kad, graphs, workers, qg, qe, qseed, arrivals):
+def open_loop(kad, graphs, workers, qg, qe, qseed, arrivals, policy=0):
     """Submit query q at arrivals[q] seconds (Poisson process) to a server with
     `workers` workers; return (makespan s, latencies ms incl. queueing, samples)."""
     import threading
     Q = len(arrivals)
-    with kad.Server(workers=workers) as S:
+    with kad.Server(workers=workers, policy=policy) as S:
         gids = [S.add_graph(g, trusted=True) for g in graphs]
         for q in range(min(5, Q)):  # warm-up
             S.wait(S.submit(gids[qg[q]], qe[q], 0.1, int(qseed[q]), want_bc=False))
@@ -273,7 +273,8 @@ def run_serve(args):
     """Serving stream: resident graphs, Poisson arrivals at several loads.  Each
     load runs the same arrival sequence twice: 'plain' (one query at a time with
     every sampling slot of the GPU, first come first served) and 'served' (the
-    query server with several workers: queries overlap on the device)."""
+    query server with several workers: queries overlap on the device, and the
+    next query is the one with the highest response ratio)."""
     import torch
     from paper_1903_09422_gb300 import build, kad
     torch.cuda.set_device(0)
@@ -289,7 +290,7 @@ def run_serve(args):
 
     # capacity of plain: back-to-back queries, one at a time
     plain_n = min(Q, args.serve_plain)
-    with kad.Server(workers=1) as P:
+    with kad.Server(workers=1, policy=1) as P:
         gids = [P.add_graph(g, trusted=True) for g in graphs]
         for q in range(min(5, Q)):  # warm-up
             P.wait(P.submit(gids[qg[q]], qe[q], 0.1, int(qseed[q]), want_bc=False))
@@ -308,8 +309,8 @@ def run_serve(args):
         lam = load * plain_qps
         arrivals = np.cumsum(np.random.default_rng(11).exponential(1.0 / lam, Q))
         row = {"load": load, "arrival_qps": lam}
-        row["plain"] = summary(*open_loop(kad, graphs, 1, qg, qe, qseed, arrivals))
-        row["served"] = summary(*open_loop(kad, graphs, args.serve_workers, qg, qe, qseed, arrivals))
+        row["plain"] = summary(*open_loop(kad, graphs, 1, qg, qe, qseed, arrivals, policy=1))
+        row["served"] = summary(*open_loop(kad, graphs, args.serve_workers, qg, qe, qseed, arrivals, policy=0))
         print(json.dumps({"load": load, "plain": row["plain"], "served": row["served"]}), file=sys.stderr, flush=True)
         sweep.append(row)
     top = sweep[-1]
@@ -321,7 +322,8 @@ def run_serve(args):
                                f"n log-uniform 1e4..1e6), {Q} queries per arm and load, Poisson arrivals at "
                                f"{args.serve_load} x the plain back-to-back throughput, eps in {{.05,.02,.01}}, "
                                f"delta .1, seed = query index + 1",
-                   "workers": args.serve_workers,
+                   "workers": args.serve_workers, "served_policy": "highest response ratio next",
+                   "plain_policy": "arrival order",
                    "value": "served queries/s at the highest load"},
         "plain_capacity_qps": plain_qps,
         "sweep": sweep,

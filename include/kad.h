@@ -258,6 +258,10 @@ typedef struct {
                                 device memory free at creation); a query larger than the budget runs alone */
     int32_t block_threads;   /* sampling-kernel variant for every query (0 = 512 threads, 2 blocks/SM) */
     int32_t blocks_per_sm;
+    int32_t policy;          /* which fitting queued query starts next: 0 = highest response ratio
+                                (waited + expected) / expected, expected = the query's omega + tau0
+                                samples times the graph's measured device time per sample (short
+                                queries first, long ones aged in); 1 = arrival order */
 } kad_server_options;
 
 /* Starts the worker threads on the current CUDA device.  opt NULL = defaults. */

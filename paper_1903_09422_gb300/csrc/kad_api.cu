@@ -874,6 +874,8 @@ struct ServerQuery {
     uint64_t seed = 0;
     double *bc_out = nullptr;
     size_t footprint = 0;
+    uint64_t samples_max = 0; // omega + tau0: the most samples the query can use
+    double est_ms = 0;        // expected service time when it was last looked at
     kad_result result;
     kad_status status = KAD_OK;
     bool done = false;
@@ -895,6 +897,9 @@ struct kad_server {
     uint64_t next_ticket = 1;
     int running = 0; // queries on workers
     bool stopping = false;
+    int policy = 0;  // 0: highest response ratio next, 1: arrival order
+    std::vector<double> ms_per_sample; // per graph: running mean of device time per used sample (0 = none yet)
+    double ms_per_sample_all = 0;       // the same over every graph
     std::vector<std::thread> pool;
 };
 
@@ -917,6 +922,17 @@ size_t query_footprint(const kad_graph *g, double eps, double delta, int slots) 
            ((size_t)tau0 + 1) * 16;
 }
 
+// Expected service time of a query (caller holds the lock): the most samples it
+// can use times the graph's mean device time per sample, or the mean over every
+// graph before the graph has answered a query (1 us per sample before any).
+double expected_ms(const kad_server *S, const ServerQuery *q) {
+    double per = S->ms_per_sample[q->gid];
+    if (per <= 0) per = S->ms_per_sample_all;
+    if (per <= 0) per = 1e-3;
+    const double e = per * (double)q->samples_max;
+    return e > 1e-3 ? e : 1e-3;
+}
+
 void server_worker(kad_server *S) {
     cudaSetDevice(S->device);
     cudaStream_t st = nullptr;
@@ -937,18 +953,34 @@ void server_worker(kad_server *S) {
                 if (share < 1) share = 1;
                 slots = S->slots_per_query > 0 ? S->slots_per_query : S->resident / share;
                 if (slots < 1) slots = 1;
-                // the first queued query whose footprint fits next to those in flight;
-                // a query larger than the whole budget runs when nothing else does
+                // Among the queued queries whose footprint fits next to those in
+                // flight (a query larger than the whole budget runs when nothing
+                // else does): the first in arrival order, or the one with the
+                // highest response ratio (waited + expected) / expected, which
+                // serves short queries first without starving long ones.
+                const double now = now_ms();
+                auto pick = S->pending.end();
+                double best = -1.0;
                 for (auto it = S->pending.begin(); it != S->pending.end(); ++it) {
                     const size_t fp = query_footprint(S->graphs[(*it)->gid], (*it)->eps, (*it)->delta, slots);
-                    if (S->inflight + fp <= S->budget || S->running == 0) {
-                        q = *it;
-                        q->footprint = fp;
-                        S->pending.erase(it);
+                    if (!(S->inflight + fp <= S->budget || S->running == 0)) continue;
+                    (*it)->footprint = fp;
+                    if (S->policy == 1) {
+                        pick = it;
                         break;
                     }
+                    const double est = expected_ms(S, *it);
+                    const double ratio = (now - (*it)->t_submit + est) / est;
+                    if (ratio > best) {
+                        best = ratio;
+                        pick = it;
+                    }
                 }
-                if (q) break;
+                if (pick != S->pending.end()) {
+                    q = *pick;
+                    S->pending.erase(pick);
+                    break;
+                }
                 S->cv_work.wait(lk);
             }
             if (!q) break;
@@ -971,6 +1003,12 @@ void server_worker(kad_server *S) {
         const double t_end = now_ms();
         {
             std::lock_guard<std::mutex> lk(S->mu);
+            if (status == KAD_OK && r.t_total_ms > 0 && r.tau + r.calib_samples > 0) {
+                const double per = r.t_total_ms / (double)(r.tau + r.calib_samples);
+                double &g_per = S->ms_per_sample[q->gid];
+                g_per = (g_per > 0) ? 0.75 * g_per + 0.25 * per : per;
+                S->ms_per_sample_all = (S->ms_per_sample_all > 0) ? 0.9 * S->ms_per_sample_all + 0.1 * per : per;
+            }
             q->t_end = t_end;
             q->result = r;
             q->status = status;
@@ -1181,6 +1219,7 @@ kad_status kad_server_create(const kad_server_options *opt, kad_server **out) {
     if (S->workers > 64) S->workers = 64;
     if (opt && opt->block_threads > 0) S->threads = opt->block_threads;
     if (opt && opt->blocks_per_sm > 0) S->per_sm = opt->blocks_per_sm;
+    if (opt && opt->policy == 1) S->policy = 1;
     kad_options o;
     fill_defaults(&o);
     o.block_threads = S->threads;
@@ -1213,6 +1252,7 @@ kad_status kad_server_add_graph(kad_server *S, int32_t n, const int32_t *row_ptr
     if (st != KAD_OK) return st;
     std::lock_guard<std::mutex> lk(S->mu);
     S->graphs.push_back(g);
+    S->ms_per_sample.push_back(0.0);
     *gid = (int32_t)S->graphs.size() - 1;
     return KAD_OK;
 }
@@ -1235,6 +1275,11 @@ kad_status kad_submit(kad_server *S, int32_t gid, double eps, double delta, uint
         q->delta = delta;
         q->seed = seed;
         q->bc_out = bc_out;
+        {
+            const kad_graph *g = S->graphs[gid];
+            const uint64_t om = run_omega(g->vd, eps, delta);
+            q->samples_max = om + run_calib(om, kDefaultEpoch, kDefaultCalibDiv);
+        }
         memset(&q->result, 0, sizeof(q->result));
         q->t_submit = now_ms();
         S->queries[q->ticket] = q;

@@ -54,7 +54,7 @@ PHASE_NAMES = ("draw", "bfs", "meet", "trace", "reset", "close")
 
 class ServerOptions(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("slots_per_query", ctypes.c_int32), ("hbm_budget", ctypes.c_int64),
-                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("policy", ctypes.c_int32)]
 
 
 EXPORTS = ("kad_graph_create", "kad_graph_create_device", "kad_graph_free", "kad_graph_info", "kad_options_default",
@@ -306,9 +306,9 @@ class Server:
     ctypes releases the GIL during every call, so a Python thread can submit
     while another waits."""
 
-    def __init__(self, workers=0, slots_per_query=0, hbm_budget=0, block_threads=0, blocks_per_sm=0):
+    def __init__(self, workers=0, slots_per_query=0, hbm_budget=0, block_threads=0, blocks_per_sm=0, policy=0):
         lib = load()
-        o = ServerOptions(workers, slots_per_query, hbm_budget, block_threads, blocks_per_sm)
+        o = ServerOptions(workers, slots_per_query, hbm_budget, block_threads, blocks_per_sm, policy)
         h = ctypes.c_void_p()
         _check(lib.kad_server_create(ctypes.byref(o), ctypes.byref(h)), "kad_server_create")
         self._h = h

@@ -48,6 +48,20 @@ def test_results_alone_equal_results_in_the_mix(kad):
         np.testing.assert_array_equal(mixed[qi]["bc"], ref["bc"])
 
 
+def test_scheduling_policy_does_not_change_results(kad):
+    graphs = mixed_graphs()[:4]
+    queries = [(i % 4, (0.05, 0.03)[i % 2], 300 + i) for i in range(16)]
+    out = {}
+    for policy in (0, 1):
+        with kad.Server(workers=3, policy=policy) as S:
+            gids = [S.add_graph(g) for g in graphs]
+            tickets = [S.submit(gids[qg], eps, 0.1, seed) for qg, eps, seed in queries]
+            out[policy] = [S.wait(t) for t in tickets]
+    for a, b in zip(out[0], out[1]):
+        assert a["tau"] == b["tau"]
+        np.testing.assert_array_equal(a["bc"], b["bc"])
+
+
 def test_admission_by_footprint_still_answers_everything(kad):
     graphs = mixed_graphs()[:3]
     with kad.Server(workers=4, hbm_budget=1) as S:  # every query exceeds the budget: one at a time
