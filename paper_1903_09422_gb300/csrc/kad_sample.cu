@@ -42,6 +42,8 @@
 #define KAD_DEG_SCAN 64 // adjacency lists up to this length are always scanned
 #define KAD_PAIR_MIN_ARCS 1024 // rounds with fewer arcs always expand by scanning
 #define KAD_PAIR_COST 16       // one pairwise adjacency test counts as this many arc reads
+#define KAD_WARP_SCAN 256       // adjacency lists up to this length are traced by one warp
+#define KAD_TITEMS 2            // consecutive arcs per thread and pass of a team's adjacency scan
 #define KAD_TBUF 64            // t-side trace steps warp 1 can buffer (longer: warp 0 traces both sides)
 
 namespace {
@@ -173,6 +175,14 @@ struct Smem {
     int st_end_pos, st_spec_pos;
     int tcount;
     unsigned long long wt1;
+    // trace teams (team t = threads [t*BLOCK/2, (t+1)*BLOCK/2)): the step's random
+    // number, per-warp partial sums, the first crossing position (two slots, by
+    // pass parity) and the chosen predecessor with its row
+    unsigned long long t_r[2];
+    unsigned long long t_wsum[2][BLOCK / 64];
+    int t_min[2][2];
+    int t_p[2], t_rs[2], t_re[2];
+    unsigned long long t_s[2];
     int32_t tbuf_v[KAD_TBUF], tbuf_j[KAD_TBUF];
     unsigned long long sst;
     unsigned long long idx;
@@ -419,23 +429,37 @@ __device__ __forceinline__ void trace_from_level(const SampleArgs &a, const uint
     if (lane == 0) w_trace += pr;
 }
 
+// Barrier of one trace team (named barrier t+1 over the team's BLOCK/2 threads).
+__device__ __forceinline__ void team_bar(int t, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(t + 1), "r"(nthreads) : "memory");
+}
+
 // Trace one side z of the sample from the meeting vertex `cur` (distance d,
-// path count sc, row [rsC, reC)) back to its root, drawing one bounded number
-// per step from the stream (lane 0's copy; the warp follows).  Each chosen
-// vertex goes out directly (buf == nullptr) or into buf_v/buf_j for later.
-// Called by one warp.  Returns the number of buffered vertices, or -1 on error.
+// path count sc, row [rsC, reC)) back to its root with team t (half of the
+// block).  Per step the team leader draws a bounded number from the stream (its
+// copy of it); each chosen vertex goes out directly (buf_v == nullptr) or into
+// buf_v/buf_j for later.  The candidates of a step are the neighbours of cur at
+// distance d-1, in ascending id (CSR) order, and the first whose running sum of
+// sigma exceeds the draw is chosen (Appendix C.1: the path is rebuilt from G
+// and the distance labels).  A short adjacency list is scanned by the team's
+// first warp, a long one by the whole team (KAD_TITEMS consecutive arcs per
+// thread and pass).  Called by every thread of the team; returns the number of
+// buffered vertices, or -1 on error.
 template <int BLOCK>
-__device__ __forceinline__ int trace_side(const SampleArgs &a, Smem<BLOCK> &sm, Stream &st, const uint32_t *label,
-                                          bool bsh, const uint32_t *bits, const unsigned long long *sigma,
-                                          const int32_t *list, int n, int z, int d, unsigned long long sc, int cur,
-                                          int rsC, int reC, int D, int32_t *out, int32_t *buf_v, int32_t *buf_j,
-                                          unsigned long long &w_trace) {
-    const int lane = threadIdx.x & 31;
-    int nb = 0;
+__device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> &sm, Stream &st, int t,
+                                               const uint32_t *label, bool bsh, const uint32_t *bits,
+                                               const unsigned long long *sigma, const int32_t *list, int n, int z, int d,
+                                               unsigned long long sc, int cur, int rsC, int reC, int D, int32_t *out,
+                                               int32_t *buf_v, int32_t *buf_j, unsigned long long &w_trace) {
+    constexpr int TT = BLOCK / 2, TW = TT / 32;
+    const int tl = (int)threadIdx.x - t * TT;
+    const int lane = threadIdx.x & 31, tw = tl >> 5;
+    const bool leader = tl == 0;
+    int nb = 0, par = 0;
     while (d >= 1) {
-        unsigned long long r = 0;
-        if (lane == 0) r = st.uniform(sc, a.ctl);
-        r = __shfl_sync(FULL_MASK, r, 0);
+        if (leader) sm.t_r[t] = st.uniform(sc, a.ctl);
+        team_bar(t, TT);
+        const unsigned long long r = sm.t_r[t];
         int p_sel = -1, rs_sel = 0, re_sel = 0;
         unsigned long long s_sel = 0;
         const int ls = (d <= KAD_MAXLV) ? sm.lvs[z][d - 1] : 0;
@@ -445,26 +469,134 @@ __device__ __forceinline__ int trace_side(const SampleArgs &a, Smem<BLOCK> &sm, 
             p_sel = z ? sm.t : sm.s;
             s_sel = 1ull;
         } else if (!(a.debug & KAD_DEBUG_TRACE_SCAN) && reC - rsC > KAD_DEG_SCAN && lcnt <= KAD_LCAP) {
-            trace_from_level<BLOCK>(a, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel, s_sel, w_trace);
-            if (p_sel >= 0) {
-                rs_sel = __ldg(a.rp + p_sel);
-                re_sel = __ldg(a.rp + p_sel + 1);
+            // few vertices at distance d-1: the team's first warp tests each of
+            // them for adjacency to cur
+            if (tw == 0) {
+                trace_from_level<BLOCK>(a, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel, s_sel, w_trace);
+                if (lane == 0) {
+                    sm.t_p[t] = p_sel;
+                    sm.t_s[t] = s_sel;
+                    sm.t_rs[t] = (p_sel >= 0) ? __ldg(a.rp + p_sel) : 0;
+                    sm.t_re[t] = (p_sel >= 0) ? __ldg(a.rp + p_sel + 1) : 0;
+                }
             }
+            team_bar(t, TT);
+            p_sel = sm.t_p[t];
+            s_sel = sm.t_s[t];
+            rs_sel = sm.t_rs[t];
+            re_sel = sm.t_re[t];
+        } else if (reC - rsC <= KAD_WARP_SCAN) {
+            // a short row: the team's first warp scans it
+            if (tw == 0) {
+                trace_scan(a, label, bsh, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, rs_sel, re_sel, w_trace);
+                if (lane == 0) {
+                    sm.t_p[t] = p_sel;
+                    sm.t_s[t] = s_sel;
+                    sm.t_rs[t] = rs_sel;
+                    sm.t_re[t] = re_sel;
+                }
+            }
+            team_bar(t, TT);
+            p_sel = sm.t_p[t];
+            s_sel = sm.t_s[t];
+            rs_sel = sm.t_rs[t];
+            re_sel = sm.t_re[t];
         } else {
-            trace_scan(a, label, bsh, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, rs_sel, re_sel, w_trace);
+            // scan adj(cur): thread tl takes KAD_TITEMS consecutive arcs of each pass;
+            // only vertices at distance d-1 on side z count
+            const uint32_t key = (z ? KAD_SIDE : 0u) | (uint32_t)d;
+            const bool direct = reC - rsC <= 32;
+            unsigned long long carry = 0;
+            for (int base = rsC; base < reC; base += KAD_TITEMS * TT) {
+                const int e0 = base + KAD_TITEMS * tl;
+                int pp[KAD_TITEMS];
+                uint32_t lp[KAD_TITEMS];
+                unsigned long long wk[KAD_TITEMS];
+#pragma unroll
+                for (int k = 0; k < KAD_TITEMS; k++) pp[k] = (e0 + k < reC) ? __ldg(a.col + e0 + k) : -1;
+                if (direct) {
+#pragma unroll
+                    for (int k = 0; k < KAD_TITEMS; k++) lp[k] = (pp[k] >= 0) ? kad_ld_u32(label + pp[k]) : 0u;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < KAD_TITEMS; k++) lp[k] = (pp[k] >= 0) ? bits_ld(bsh, bits, pp[k] >> 5) : 0u;
+#pragma unroll
+                    for (int k = 0; k < KAD_TITEMS; k++)
+                        lp[k] = (pp[k] >= 0 && ((lp[k] >> (pp[k] & 31)) & 1u)) ? kad_ld_u32(label + pp[k]) : 0u;
+                }
+                unsigned long long mine = 0;
+#pragma unroll
+                for (int k = 0; k < KAD_TITEMS; k++) {
+                    wk[k] = 0;
+                    if (pp[k] >= 0 && (lp[k] & KAD_KEY) == key)
+                        wk[k] = (lp[k] & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + pp[k]);
+                    mine = kad_sat_add(mine, wk[k]);
+                }
+                // running sums in CSR order (saturating addition is associative):
+                // warp scan, then the team's per-warp sums
+                const unsigned long long incl = warp_incl_sat_scan(mine);
+                unsigned long long excl = __shfl_up_sync(FULL_MASK, incl, 1);
+                if (lane == 0) excl = 0;
+                if (lane == 31) sm.t_wsum[t][tw] = incl;
+                if (leader) sm.t_min[t][par] = 0x7fffffff;
+                team_bar(t, TT);
+                unsigned long long c = carry, tot = carry;
+#pragma unroll
+                for (int w = 0; w < TW; w++) {
+                    const unsigned long long x = sm.t_wsum[t][w];
+                    if (w < tw) c = kad_sat_add(c, x);
+                    tot = kad_sat_add(tot, x);
+                }
+                c = kad_sat_add(c, excl);
+                int hit = 0x7fffffff, hp = -1;
+                unsigned long long hs = 0;
+#pragma unroll
+                for (int k = 0; k < KAD_TITEMS; k++) {
+                    const unsigned long long c2 = kad_sat_add(c, wk[k]);
+                    if (wk[k] && c2 > r && hit == 0x7fffffff) {
+                        hit = e0 + k;
+                        hp = pp[k];
+                        hs = wk[k];
+                    }
+                    c = c2;
+                }
+                const int wmin = __reduce_min_sync(FULL_MASK, hit);
+                if (lane == 0 && wmin != 0x7fffffff) atomicMin(&sm.t_min[t][par], wmin);
+                team_bar(t, TT);
+                const int sel = sm.t_min[t][par];
+                par ^= 1;
+                if (sel != 0x7fffffff) {
+                    if (hit == sel) {
+                        sm.t_p[t] = hp;
+                        sm.t_s[t] = hs;
+                        sm.t_rs[t] = __ldg(a.rp + hp);
+                        sm.t_re[t] = __ldg(a.rp + hp + 1);
+                    }
+                    team_bar(t, TT);
+                    p_sel = sm.t_p[t];
+                    s_sel = sm.t_s[t];
+                    rs_sel = sm.t_rs[t];
+                    re_sel = sm.t_re[t];
+                    if (leader) w_trace += (unsigned long long)(sel - rsC + 1);
+                    break;
+                }
+                carry = tot;
+            }
         }
         if (p_sel < 0) {
-            if (lane == 0) kad_set_err(a.ctl, KAD_DERR_TRACE);
+            if (leader) kad_set_err(a.ctl, KAD_DERR_TRACE);
             return -1;
         }
         d--;
         if (d >= 1) {
             const int j = (z == 0) ? d : D - d;
-            if (!buf_v) {
-                if (lane == 0) emit(a, out, D, j, p_sel);
-            } else if (lane == 0) {
-                buf_v[nb] = p_sel;
-                buf_j[nb] = j;
+            if (leader) {
+                if (!buf_v) {
+                    emit(a, out, D, j, p_sel);
+                } else {
+                    buf_v[nb] = p_sel;
+                    buf_j[nb] = j;
+                }
             }
             nb++;
         }
@@ -1203,19 +1335,21 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
         else if (a.mode == KAD_MODE_RECORD)
             row = (size_t)(idx - a.i0);
         int32_t *const out = calib ? nullptr : a.paths + row * (size_t)a.cap;
-        // The s side (warp 0) and the t side (warp 1) are traced at the same
-        // time.  The t side's draws follow the s side's in the stream; warp 1
-        // starts where the s side ends if none of its draws is rejected (each
-        // then takes one word) and buffers its vertices.  If warp 0 ends
-        // elsewhere (a rejection, probability below 2^-24 per draw for counts
-        // under 2^40), warp 0 traces the t side again from the right place.
+        // The s side (team 0, the first half of the block) and the t side (team
+        // 1) are traced at the same time.  The t side's draws follow the s side's
+        // in the stream; team 1 starts where the s side ends if none of its draws
+        // is rejected (each then takes one word) and buffers its vertices.  If
+        // team 0 ends elsewhere (a rejection, probability below 2^-24 per draw
+        // for counts under 2^40), team 0 traces the t side again from there.
         const int mid = sm.mid;
         const bool traced = D > 0 && mid >= 0 && mid < n;
         if (D > 0 && !traced && tid == 0) kad_set_err(a.ctl, KAD_DERR_SELECT);
         int dz[2] = {0, 0};
         unsigned long long gz[2] = {0, 0};
         int rsM = 0, reM = 0;
-        if (traced && wid < 2) {
+        constexpr int TT = BLOCK / 2;
+        const int team = tid / TT, tl = tid - team * TT;
+        if (traced) {
             // distance and path count of the meeting vertex on each side: side X
             // reaches it at level lev[X]+1 (count in sigma2), side Y holds it at
             // level lev[Y] (count in sigma)
@@ -1231,8 +1365,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             reM = __ldg(a.rp + mid + 1);
         }
         const bool spec = traced && dz[1] <= KAD_TBUF && !(a.debug & KAD_DEBUG_SERIAL_TRACE);
-        if (spec && wid == 1 && lane == 0) {
-            // warp 1's stream: the one after the meeting draw, one word further per s-side step
+        if (spec && team == 1 && tl == 0) {
+            // team 1's stream: the one after the meeting draw, one word further per s-side step
             st.k0 = a.key0;
             st.k1 = a.key1;
             st.idx = idx;
@@ -1245,33 +1379,32 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             sm.st_spec_blk = st.blk;
             sm.st_spec_pos = st.pos;
         }
-        // Two phases with one trace loop.  Phase 0: warp 0 traces the s side and
-        // warp 1 the t side into its buffer.  Phase 1: the buffer goes out if the
-        // stream positions agree; else (or without speculation) warp 0 traces
+        // Two phases with one trace loop.  Phase 0: team 0 traces the s side and
+        // team 1 the t side into its buffer.  Phase 1: the buffer goes out if the
+        // stream positions agree; else (or without speculation) team 0 traces
         // the t side from its own stream.
         for (int ph = 0; ph < 2 && traced; ph++) {
             int z = -1;
             bool buffered = false;
             if (ph == 0) {
-                if (wid == 0) z = 0;
-                if (wid == 1 && spec) {
+                if (team == 0) z = 0;
+                if (team == 1 && spec) {
                     z = 1;
                     buffered = true;
                 }
-            } else if (wid == 0) {
+            } else if (team == 0) {
                 if (!spec || sm.st_end_blk != sm.st_spec_blk || sm.st_end_pos != sm.st_spec_pos) z = 1;
-            } else if (wid == 1 && spec && sm.st_end_blk == sm.st_spec_blk && sm.st_end_pos == sm.st_spec_pos) {
-                if (lane < sm.tcount) emit(a, out, D, sm.tbuf_j[lane], sm.tbuf_v[lane]);
-                if (lane + 32 < sm.tcount) emit(a, out, D, sm.tbuf_j[lane + 32], sm.tbuf_v[lane + 32]);
-                if (lane == 0) sm.acc[4] += sm.wt1;
+            } else if (spec && sm.st_end_blk == sm.st_spec_blk && sm.st_end_pos == sm.st_spec_pos) {
+                if (tl < sm.tcount) emit(a, out, D, sm.tbuf_j[tl], sm.tbuf_v[tl]);
+                if (tl == 0) sm.acc[4] += sm.wt1;
             }
             if (z >= 0) {
                 unsigned long long wt = 0;
-                if (z == 0 && lane == 0) emit(a, out, D, dz[0], mid);
-                const int nb = trace_side<BLOCK>(a, sm, st, label, bsh, bits, sigma, list, n, z, z ? dz[1] : dz[0],
-                                                 z ? gz[1] : gz[0], mid, rsM, reM, D, out,
-                                                 buffered ? sm.tbuf_v : nullptr, buffered ? sm.tbuf_j : nullptr, wt);
-                if (lane == 0) {
+                if (z == 0 && tl == 0) emit(a, out, D, dz[0], mid);
+                const int nb = trace_side_team<BLOCK>(a, sm, st, team, label, bsh, bits, sigma, list, n, z,
+                                                      z ? dz[1] : dz[0], z ? gz[1] : gz[0], mid, rsM, reM, D, out,
+                                                      buffered ? sm.tbuf_v : nullptr, buffered ? sm.tbuf_j : nullptr, wt);
+                if (tl == 0) {
                     if (buffered) {
                         sm.tcount = nb;
                         sm.wt1 = wt;
