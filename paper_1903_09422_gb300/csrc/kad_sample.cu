@@ -183,6 +183,8 @@ struct Smem {
     int t_min[2][2];
     int t_p[2], t_rs[2], t_re[2];
     unsigned long long t_s[2];
+    int32_t c_p[2][KAD_LCAP];           // predecessor candidates of a team step (-1: not adjacent)
+    unsigned long long c_s[2][KAD_LCAP];
     int32_t tbuf_v[KAD_TBUF], tbuf_j[KAD_TBUF];
     unsigned long long sst;
     unsigned long long idx;
@@ -356,82 +358,132 @@ __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *
     }
 }
 
-__device__ __forceinline__ bool row_contains(const int32_t *col, int lo, int hi, int key, int &probes) {
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const int v = __ldg(col + mid);
-        probes++;
-        if (v < key)
-            lo = mid + 1;
-        else if (v > key)
-            hi = mid;
-        else
-            return true;
-    }
-    return false;
+// Barrier of one trace team (named barrier t+1 over the team's BLOCK/2 threads).
+__device__ __forceinline__ void team_bar(int t, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(t + 1), "r"(nthreads) : "memory");
 }
 
-// When cur has many neighbours but level d-1 of side z has at most KAD_LCAP
-// vertices, test each of those for adjacency to cur (binary search in the
-// shorter of the two sorted rows) and select among the adjacent ones in
-// ascending id order: the same candidates, order and choice as the scan.
+// A trace step at `cur` (side z, distance d) when level d-1 has lcnt <= KAD_LCAP
+// vertices: each of them is tested for adjacency to cur by G = BLOCK/128 threads
+// of the team together (a search in the shorter of the two sorted rows with
+// P = max(G-1, 1) probes per round, splitting the range into P+1 parts), the
+// adjacent ones with their path counts go to shared memory, and the team's first
+// warp selects among them in ascending id order: the same candidates, order and
+// choice as scanning adj(cur).  Every thread of the team calls it; the choice is
+// returned to the first warp.  The probes are counted into the trace counter.
 template <int BLOCK>
-__device__ __forceinline__ void trace_from_level(const SampleArgs &a, const uint32_t *label,
-                                                 const unsigned long long *sigma, const int32_t *list, int n, int z,
-                                                 int ls, int lcnt, int cur, int rsC, int reC, unsigned long long r,
-                                                 int &p_sel, unsigned long long &s_sel, unsigned long long &w_trace) {
-    const int lane = threadIdx.x & 31;
-    int pc[2];
-    unsigned long long wc[2];
+__device__ __forceinline__ void team_from_level(const SampleArgs &a, Smem<BLOCK> &sm, int t, const uint32_t *label,
+                                                const unsigned long long *sigma, const int32_t *list, int n, int z,
+                                                int ls, int lcnt, int cur, int rsC, int reC, unsigned long long r,
+                                                int &p_sel, unsigned long long &s_sel) {
+    constexpr int TT = BLOCK / 2;
+    constexpr int G = (TT / KAD_LCAP >= 2) ? TT / KAD_LCAP : 1; // threads per candidate (a power of two)
+    constexpr int P = (G > 1) ? G - 1 : 1;                       // probes per round
+    const int tl = (int)threadIdx.x - t * TT;
+    const int lane = threadIdx.x & 31, tw = tl >> 5;
+    const int j = tl / G, sub = tl % G;
+    const bool mine = j < lcnt;
+    int p = -1, lo = 0, hi = 0, key = 0;
+    if (mine) {
+        p = __ldcg(list + phys(z, ls + j, n));
+        const int rsP = __ldg(a.rp + p), reP = __ldg(a.rp + p + 1);
+        if (reP - rsP <= reC - rsC) {
+            lo = rsP;
+            hi = reP;
+            key = cur;
+        } else {
+            lo = rsC;
+            hi = reC;
+            key = p;
+        }
+    }
+    bool done = !mine, found = false;
     int probes = 0;
+    while (__any_sync(FULL_MASK, !done)) {
+        const int len = hi - lo;
+        if (!done && len <= G) {
+            // the last few positions: one per thread of the group
+            found = sub < len && __ldg(a.col + lo + sub) == key;
+            probes += (sub < len) ? 1 : 0;
+            done = true;
+        }
+        // the group's P probes split [lo, hi) into P+1 parts; every probe lies
+        // inside the range, so each round shrinks it or finds the key
+        int v = 0, q = 0;
+        const bool probe = !done && sub < P;
+        if (probe) {
+            q = lo + (int)(((long long)len * (sub + 1)) / (P + 1));
+            v = __ldg(a.col + q);
+            probes++;
+        }
+        int nlo = (probe && v < key) ? q + 1 : -0x7fffffff;
+        int nhi = (probe && v > key) ? q : 0x7fffffff;
+        int eq = (probe && v == key) ? 1 : 0;
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const int j = lane + 32 * k;
-        pc[k] = -1;
-        wc[k] = 0;
-        if (j < lcnt) {
-            const int p = __ldcg(list + phys(z, ls + j, n));
-            const int rsP = __ldg(a.rp + p), reP = __ldg(a.rp + p + 1);
-            const bool adj = (reP - rsP <= reC - rsC) ? row_contains(a.col, rsP, reP, cur, probes)
-                                                      : row_contains(a.col, rsC, reC, p, probes);
-            if (adj) {
-                const uint32_t lp = kad_ld_u32(label + p);
-                pc[k] = p;
-                wc[k] = (lp & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + p);
+        for (int o = 1; o < G; o <<= 1) {
+            nlo = max(nlo, __shfl_xor_sync(FULL_MASK, nlo, o, G));
+            nhi = min(nhi, __shfl_xor_sync(FULL_MASK, nhi, o, G));
+            eq |= __shfl_xor_sync(FULL_MASK, eq, o, G);
+        }
+        if (!done) {
+            if (eq) {
+                found = true;
+                done = true;
+            } else {
+                lo = max(lo, nlo);
+                hi = min(hi, nhi);
+                if (lo >= hi) done = true;
             }
         }
     }
-    // exclusive prefix of each candidate in id order
-    unsigned long long ex[2] = {0ull, 0ull};
+    // the group's result (found by any of its threads)
+    int f = found ? 1 : 0;
 #pragma unroll
-    for (int slot = 0; slot < 2; slot++) {
-        for (int q = 0; q < 32; q++) {
-            const int pq = __shfl_sync(FULL_MASK, pc[slot], q);
-            const unsigned long long wq = __shfl_sync(FULL_MASK, wc[slot], q);
-#pragma unroll
-            for (int k = 0; k < 2; k++)
-                if (pq >= 0 && pc[k] >= 0 && pq < pc[k]) ex[k] = kad_sat_add(ex[k], wq);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const bool win = pc[k] >= 0 && ex[k] <= r && kad_sat_add(ex[k], wc[k]) > r;
-        const unsigned hit = __ballot_sync(FULL_MASK, win);
-        if (hit) {
-            const int fl = __ffs(hit) - 1;
-            p_sel = __shfl_sync(FULL_MASK, pc[k], fl);
-            s_sel = __shfl_sync(FULL_MASK, wc[k], fl);
+    for (int o = 1; o < G; o <<= 1) f |= __shfl_xor_sync(FULL_MASK, f, o, G);
+    if (mine && sub == 0) {
+        sm.c_p[t][j] = f ? p : -1;
+        if (f) {
+            const uint32_t lp = kad_ld_u32(label + p);
+            sm.c_s[t][j] = (lp & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + p);
         }
     }
     unsigned long long pr = probes;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) pr += __shfl_xor_sync(FULL_MASK, pr, o);
-    if (lane == 0) w_trace += pr;
-}
-
-// Barrier of one trace team (named barrier t+1 over the team's BLOCK/2 threads).
-__device__ __forceinline__ void team_bar(int t, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(t + 1), "r"(nthreads) : "memory");
+    if (lane == 0 && pr) atomicAdd(&sm.acc[4], pr);
+    team_bar(t, TT);
+    if (tw == 0) {
+        int pc[2];
+        unsigned long long wc[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const int jj = lane + 32 * k;
+            pc[k] = (jj < lcnt) ? sm.c_p[t][jj] : -1;
+            wc[k] = (pc[k] >= 0) ? sm.c_s[t][jj] : 0ull;
+        }
+        // exclusive prefix of each candidate in id order
+        unsigned long long ex[2] = {0ull, 0ull};
+#pragma unroll
+        for (int slot = 0; slot < 2; slot++) {
+            for (int qq = 0; qq < 32; qq++) {
+                const int pq = __shfl_sync(FULL_MASK, pc[slot], qq);
+                const unsigned long long wq = __shfl_sync(FULL_MASK, wc[slot], qq);
+#pragma unroll
+                for (int k = 0; k < 2; k++)
+                    if (pq >= 0 && pc[k] >= 0 && pq < pc[k]) ex[k] = kad_sat_add(ex[k], wq);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const bool win = pc[k] >= 0 && ex[k] <= r && kad_sat_add(ex[k], wc[k]) > r;
+            const unsigned hitm = __ballot_sync(FULL_MASK, win);
+            if (hitm) {
+                const int fl = __ffs(hitm) - 1;
+                p_sel = __shfl_sync(FULL_MASK, pc[k], fl);
+                s_sel = __shfl_sync(FULL_MASK, wc[k], fl);
+            }
+        }
+    }
 }
 
 // Trace one side z of the sample from the meeting vertex `cur` (distance d,
@@ -469,10 +521,10 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
             p_sel = z ? sm.t : sm.s;
             s_sel = 1ull;
         } else if (!(a.debug & KAD_DEBUG_TRACE_SCAN) && reC - rsC > KAD_DEG_SCAN && lcnt <= KAD_LCAP) {
-            // few vertices at distance d-1: the team's first warp tests each of
-            // them for adjacency to cur
+            // few vertices at distance d-1: the team tests each of them for
+            // adjacency to cur
+            team_from_level<BLOCK>(a, sm, t, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel, s_sel);
             if (tw == 0) {
-                trace_from_level<BLOCK>(a, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel, s_sel, w_trace);
                 if (lane == 0) {
                     sm.t_p[t] = p_sel;
                     sm.t_s[t] = s_sel;
@@ -886,7 +938,7 @@ __device__ void run_closer(const SampleArgs &a, Smem<BLOCK> &sm) {
 template <int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     __shared__ Smem<BLOCK> sm;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int32_t n = a.n;
     const size_t soff = (size_t)blockIdx.x * (size_t)n;
     uint32_t *const label = a.label + soff;
@@ -1396,7 +1448,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 if (!spec || sm.st_end_blk != sm.st_spec_blk || sm.st_end_pos != sm.st_spec_pos) z = 1;
             } else if (spec && sm.st_end_blk == sm.st_spec_blk && sm.st_end_pos == sm.st_spec_pos) {
                 if (tl < sm.tcount) emit(a, out, D, sm.tbuf_j[tl], sm.tbuf_v[tl]);
-                if (tl == 0) sm.acc[4] += sm.wt1;
+                if (tl == 0) atomicAdd(&sm.acc[4], sm.wt1);
             }
             if (z >= 0) {
                 unsigned long long wt = 0;
@@ -1409,7 +1461,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                         sm.tcount = nb;
                         sm.wt1 = wt;
                     } else {
-                        sm.acc[4] += wt;
+                        atomicAdd(&sm.acc[4], wt);
                     }
                     if (ph == 0 && z == 0) {
                         sm.st_end_blk = st.blk;
