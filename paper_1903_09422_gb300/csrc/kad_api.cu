@@ -134,6 +134,14 @@ void ws_free_all(Workspace &w) {
     w = Workspace();
 }
 
+// A freed graph's workspace is kept for the next graph on the same device (one
+// per device), so that creating, running and freeing graphs in a loop reuses
+// the slot scratch instead of allocating and clearing gigabytes every time.
+// kad_trim releases what is kept.
+std::mutex g_ws_cache_mu;
+Workspace g_ws_cache[64];
+bool g_ws_cached[64];
+
 template <typename T> cudaError_t dalloc(T **p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
@@ -606,6 +614,17 @@ kad_status autotune(kad_graph *g, Workspace &w, double eps, double delta, const 
     return KAD_OK;
 }
 
+// A graph without a workspace of its own takes the one kept from a freed graph.
+void ws_adopt(kad_graph *g) {
+    if (g->ws.ctl || g->device < 0 || g->device >= 64) return;
+    std::lock_guard<std::mutex> lk(g_ws_cache_mu);
+    if (g_ws_cached[g->device]) {
+        g->ws = g_ws_cache[g->device];
+        g_ws_cache[g->device] = Workspace();
+        g_ws_cached[g->device] = false;
+    }
+}
+
 kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64_t seed, cudaStream_t st,
                     const kad_options *opt_in, double *d_bc, uint32_t *d_counts, kad_result *out, bool host_out) {
     if (!g || !out) return KAD_ERR_INVALID_ARG;
@@ -1052,6 +1071,14 @@ void kad_graph_free(kad_graph *g) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(g->device);
+    if (!g->poisoned && g->ws.ctl && g->device >= 0 && g->device < 64) {
+        std::lock_guard<std::mutex> lk(g_ws_cache_mu);
+        if (!g_ws_cached[g->device]) {
+            g_ws_cache[g->device] = g->ws;
+            g_ws_cached[g->device] = true;
+            g->ws = Workspace();
+        }
+    }
     ws_free_all(g->ws);
     cudaFree(g->gd.rp);
     cudaFree(g->gd.col);
@@ -1072,12 +1099,14 @@ kad_status kad_graph_info(const kad_graph *g, int32_t *n, int64_t *m, int32_t *v
 kad_status kad_run(kad_graph *g, double eps, double delta, uint64_t seed, kad_stream_t stream, const kad_options *opt,
                    kad_result *out) {
     if (!g) return KAD_ERR_INVALID_ARG;
+    ws_adopt(g);
     return run_impl(g, g->ws, eps, delta, seed, (cudaStream_t)stream, opt, nullptr, nullptr, out, true);
 }
 
 kad_status kad_run_device(kad_graph *g, double eps, double delta, uint64_t seed, kad_stream_t stream,
                           const kad_options *opt, double *d_bc, uint32_t *d_counts, kad_result *out) {
     if (!g) return KAD_ERR_INVALID_ARG;
+    ws_adopt(g);
     return run_impl(g, g->ws, eps, delta, seed, (cudaStream_t)stream, opt, d_bc, d_counts, out, false);
 }
 
@@ -1092,6 +1121,7 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
     if (count == 0) return KAD_OK;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(g, cudaGetLastError());
+    ws_adopt(g);
     kad_options o;
     if (opt)
         o = *opt;
@@ -1363,6 +1393,19 @@ const char *kad_status_string(kad_status s) {
         return "device-side consistency check failed";
     }
     return "unknown status";
+}
+
+void kad_trim(void) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    std::lock_guard<std::mutex> lk(g_ws_cache_mu);
+    for (int d = 0; d < 64; d++) {
+        if (!g_ws_cached[d]) continue;
+        cudaSetDevice(d);
+        ws_free_all(g_ws_cache[d]);
+        g_ws_cached[d] = false;
+    }
+    cudaSetDevice(cur);
 }
 
 uint32_t kad_version(void) { return (0u << 16) | 1u; }

@@ -46,27 +46,65 @@ __global__ void k_validate_rows(const int32_t *__restrict__ rp, const int32_t *_
 
 // Every arc v->w needs its reverse w->v (binary search in the sorted row of w).
 // Runs only after k_validate_rows passed; the bounds checks stay as a guard.
+// Symmetry, given sorted duplicate-free rows: every arc (v, w) with w > v has its
+// reverse (v in row w), and there are as many arcs with w > v as with w < v.
+// (The reverse map sends the first kind into the second injectively; equal
+// counts make it a bijection, so every arc of the second kind has its reverse
+// as well.)  Only the upward arcs are searched for: on skewed graphs those are
+// mostly searches in short rows.  Arc-parallel: each thread takes 32 consecutive
+// arcs, finds the row of the first by binary search in row_ptr and walks on, so
+// a hub's row is spread over many threads.  counts[0] += arcs up, counts[1] +=
+// arcs down.  Runs after k_validate_rows has accepted row_ptr.
+#define KAD_SYM_CHUNK 32
 __global__ void k_validate_sym(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
-                               int64_t m, int *err) {
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-        const int a = rp[v], b = rp[v + 1];
-        if (a > b || a < 0 || (int64_t)b > m) continue;
-        for (int e = a + lane; e < b; e += 32) {
+                               int64_t m, int *err, unsigned long long *counts) {
+    unsigned long long up = 0, down = 0;
+    const int64_t chunks = (m + KAD_SYM_CHUNK - 1) / KAD_SYM_CHUNK;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e0 = c * KAD_SYM_CHUNK;
+        const int64_t e1 = (e0 + KAD_SYM_CHUNK < m) ? e0 + KAD_SYM_CHUNK : m;
+        // the row holding arc e0: the last v with rp[v] <= e0
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)rp[mid] <= e0)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        int v = lo;
+        int vend = rp[v + 1];
+        for (int64_t e = e0; e < e1; e++) {
+            while ((int64_t)vend <= e && v < n - 1) {
+                v++;
+                vend = rp[v + 1];
+            }
             const int w = col[e];
             if (w < 0 || w >= n) continue;
-            int lo = rp[w], hi = rp[w + 1];
-            if (lo > hi || lo < 0 || (int64_t)hi > m) continue;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (col[mid] < v)
-                    lo = mid + 1;
-                else
-                    hi = mid;
+            if (w < v) {
+                down++;
+                continue;
             }
-            if (lo >= rp[w + 1] || col[lo] != v) atomicOr(err, GERR_SYM);
+            up++;
+            int a = rp[w], b = rp[w + 1];
+            while (a < b) {
+                const int mid = (a + b) >> 1;
+                if (col[mid] < v)
+                    a = mid + 1;
+                else
+                    b = mid;
+            }
+            if (a >= rp[w + 1] || col[a] != v) atomicOr(err, GERR_SYM);
         }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        up += __shfl_xor_sync(0xffffffffu, up, o);
+        down += __shfl_xor_sync(0xffffffffu, down, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (up || down)) {
+        atomicAdd(counts, up);
+        atomicAdd(counts + 1, down);
     }
 }
 
@@ -160,14 +198,18 @@ __global__ void k_fill(int32_t *p, int32_t n, int32_t val) {
 
 // top-down: warp per frontier vertex, coalesced neighbour loads
 __global__ void k_bfs_td(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                         const int32_t *__restrict__ q, int qlen, int32_t *dist, int32_t *nq, int *nqlen,
+                         const int32_t *__restrict__ q, int qlen, int parts, int32_t *dist, int32_t *nq, int *nqlen,
                          unsigned long long *narcs, int level) {
+    // `parts` warps share each frontier vertex's row (a small frontier of hubs
+    // would otherwise leave one warp with a whole hub row)
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < qlen; i += warps) {
+    const int64_t items = (int64_t)qlen * parts;
+    for (int64_t it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += warps) {
+        const int i = (int)(it / parts), part = (int)(it % parts);
         const int u = q[i];
         const int a = rp[u], b = rp[u + 1];
-        for (int e = a + lane; e < b; e += 32) {
+        for (int e = a + 32 * part + lane; e < b; e += 32 * parts) {
             const int w = col[e];
             if (*(volatile int32_t *)(dist + w) < 0 && atomicCAS(dist + w, -1, level + 1) == -1) {
                 nq[atomicAdd(nqlen, 1)] = w;
@@ -217,10 +259,11 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
                            cudaError_t *cerr) {
     const int32_t n = gd.n;
     kad_status status = KAD_OK;
-    int *d_flags = nullptr; // [0] err, [1] qlen, [2] ncomp
+    int *d_flags = nullptr; // [0] err, [1] qlen, [2] ncomp, [4..7] two u64 arc counts
     int32_t *parent = nullptr, *dist = nullptr, *q0 = nullptr, *q1 = nullptr;
     unsigned long long *best = nullptr, *d_arcs = nullptr;
     int h_flags[3] = {0, 0, 0};
+    unsigned long long h_counts[2] = {0, 0};
     const int T = 256;
     const int gw = grid_for((int64_t)n * 32, T, 65535); // warp-per-vertex kernels
     const int gv = grid_for(n, T, 65535);
@@ -228,7 +271,7 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
     unsigned long long arcs = 0;
     int32_t *qa, *qb;
 
-    if (cudaMalloc(&d_flags, 3 * sizeof(int)) != cudaSuccess || cudaMalloc(&parent, (size_t)n * 4) != cudaSuccess ||
+    if (cudaMalloc(&d_flags, 8 * sizeof(int)) != cudaSuccess || cudaMalloc(&parent, (size_t)n * 4) != cudaSuccess ||
         cudaMalloc(&dist, (size_t)n * 4) != cudaSuccess || cudaMalloc(&q0, (size_t)n * 4) != cudaSuccess ||
         cudaMalloc(&q1, (size_t)n * 4) != cudaSuccess || cudaMalloc(&best, (size_t)n * 8) != cudaSuccess ||
         cudaMalloc(&d_arcs, 8) != cudaSuccess) {
@@ -236,7 +279,7 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
         status = KAD_ERR_OOM;
         goto done;
     }
-    GCHK(cudaMemsetAsync(d_flags, 0, 3 * sizeof(int), st));
+    GCHK(cudaMemsetAsync(d_flags, 0, 8 * sizeof(int), st));
     k_check_ends<<<1, 32, 0, st>>>(gd.rp, n, gd.m, d_flags);
     k_validate_rows<<<gw, T, 0, st>>>(gd.rp, gd.col, n, gd.m, d_flags);
     GCHK(cudaGetLastError());
@@ -247,11 +290,13 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
         goto done;
     }
     if (!(flags & KAD_GRAPH_TRUSTED)) {
-        k_validate_sym<<<gw, T, 0, st>>>(gd.rp, gd.col, n, gd.m, d_flags);
+        k_validate_sym<<<grid_for((gd.m + KAD_SYM_CHUNK - 1) / KAD_SYM_CHUNK, T, 65535), T, 0, st>>>(
+            gd.rp, gd.col, n, gd.m, d_flags, (unsigned long long *)(d_flags + 4));
         GCHK(cudaGetLastError());
         GCHK(cudaMemcpyAsync(h_flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GCHK(cudaMemcpyAsync(h_counts, d_flags + 4, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         GCHK(cudaStreamSynchronize(st));
-        if (h_flags[0]) {
+        if (h_flags[0] || h_counts[0] != h_counts[1]) {
             status = KAD_ERR_BAD_CSR;
             goto done;
         }
@@ -286,9 +331,12 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
         const bool bottom_up = (int64_t)arcs * 14 > gd.m && qlen > n / 64;
         if (bottom_up)
             k_bfs_bu<<<gv, T, 0, st>>>(gd.rp, gd.col, n, dist, qb, d_flags + 1, d_arcs, level);
-        else
-            k_bfs_td<<<grid_for((int64_t)qlen * 32, T, 65535), T, 0, st>>>(gd.rp, gd.col, qa, qlen, dist, qb,
-                                                                          d_flags + 1, d_arcs, level);
+        else {
+            // about 152 SMs x 64 warps in flight: split rows when the frontier is small
+            const int parts = (qlen >= 9728) ? 1 : (9728 + qlen - 1) / qlen;
+            k_bfs_td<<<grid_for((int64_t)qlen * parts * 32, T, 65535), T, 0, st>>>(gd.rp, gd.col, qa, qlen, parts,
+                                                                                  dist, qb, d_flags + 1, d_arcs, level);
+        }
         GCHK(cudaGetLastError());
         GCHK(cudaMemcpyAsync(h_flags + 1, d_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
         GCHK(cudaMemcpyAsync(&arcs, d_arcs, 8, cudaMemcpyDeviceToHost, st));

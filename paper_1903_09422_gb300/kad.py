@@ -60,7 +60,7 @@ class ServerOptions(ctypes.Structure):
 EXPORTS = ("kad_graph_create", "kad_graph_create_device", "kad_graph_free", "kad_graph_info", "kad_options_default",
            "kad_run", "kad_run_device", "kad_sample_records", "kad_sample_records_noalloc", "kad_eval_fg",
            "kad_server_create", "kad_server_add_graph", "kad_submit", "kad_poll", "kad_wait", "kad_server_free",
-           "kad_status_string", "kad_version")
+           "kad_status_string", "kad_version", "kad_trim")
 
 _lib = None
 
@@ -114,6 +114,8 @@ def load():
     lib.kad_status_string.restype = ctypes.c_char_p
     lib.kad_version.argtypes = []
     lib.kad_version.restype = u32
+    lib.kad_trim.argtypes = []
+    lib.kad_trim.restype = None
     _lib = lib
     return lib
 
@@ -385,6 +387,11 @@ def eval_fg(counts, c0, ltab, tau, omega):
     _check(lib.kad_eval_fg(counts.size, counts.ctypes.data, c0.ctypes.data, ltab.ctypes.data, ltab.size, tau, omega,
                            f.ctypes.data, g.ctypes.data), "kad_eval_fg")
     return f, g
+
+
+def trim():
+    """kad_trim: free the workspace kept from freed graphs."""
+    load().kad_trim()
 
 
 def version():

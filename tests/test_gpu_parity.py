@@ -245,6 +245,13 @@ def test_bad_csr_is_rejected(kad):
     col[-1] = 7  # last row (vertex 9) now points to 7 instead of 8
     with pytest.raises(kad.KadError):
         kad.Graph(h.row_ptr, col)
+    # asymmetric through an extra downward arc whose reverse is missing: every
+    # upward arc has its reverse, only the arc counts differ
+    rp = np.array(list(h.row_ptr[:-1]) + [h.row_ptr[-1] + 1], np.int32)
+    col = np.concatenate([h.col[:-1], np.array([7, 8], np.int32)])  # row 9 = [7, 8]
+    with pytest.raises(kad.KadError) as e:
+        kad.Graph(rp, col)
+    assert e.value.status == 2
     with pytest.raises(kad.KadError):
         kad.Graph(np.array([0, 1], np.int32), np.array([0], np.int32))  # n = 1
 
@@ -258,3 +265,20 @@ def test_invalid_run_arguments(kad):
             assert e.value.status == 1
         r = G.run(0.1, 0.1, 1)  # the handle stays usable
         assert r["tau"] > 0
+
+
+def test_workspace_kept_across_graphs(kad):
+    # A freed graph's workspace serves the next graph (larger and smaller n,
+    # records and full runs), and kad_trim releases it.
+    graphs = [gen.rmat(12, 8, seed=1), gen.grid(30, seed=2), gen.rmat(13, 8, seed=3), gen.er(120, 0.1, seed=4)]
+    for i, g in enumerate(graphs):
+        ref = O.kadabra(g, 0.05, 0.1, 5 + i)
+        with kad.Graph.from_csr(g) as G:
+            rec = G.sample_records(5 + i, 0, 300)
+            r = G.run(0.05, 0.1, 5 + i)
+        compare_records(rec, O.samples(g, 5 + i, 0, 300))
+        assert r["tau"] == ref["tau"]
+        np.testing.assert_array_equal(r["counts"], ref["counts"])
+        if i == 1:
+            kad.trim()
+    kad.trim()
