@@ -8,6 +8,7 @@
 // v0_C at once computes every ecc_C, since the components are disjoint.  The
 // BFS is level-synchronous and direction-optimising (top-down while the
 // frontier's arcs are few, bottom-up once they are a large share of the graph).
+#include <algorithm>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,30 +23,53 @@ namespace {
 #define GERR_ROWPTR 16
 #define GERR_CC 32
 
+// Row pointers non-decreasing within [0, m] (thread per vertex), and every arc
+// (v, w) with 0 <= w < n, w != v, and w above its predecessor in the row.  The
+// arcs are checked 32 consecutive ones per thread (the row of the first found
+// by binary search in row_ptr), so a hub's row is spread over many threads;
+// with a bad row_ptr those reads stay in bounds and the row_ptr flag decides.
+#define KAD_ROW_CHUNK 32
 __global__ void k_validate_rows(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
                                 int64_t m, int *err) {
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t v = t0; v < n; v += stride) {
         const int a = rp[v], b = rp[v + 1];
-        if (a > b || a < 0 || (int64_t)b > m) {
-            if (lane == 0) atomicOr(err, GERR_ROWPTR);
-            continue;
+        if (a > b || a < 0 || (int64_t)b > m) atomicOr(err, GERR_ROWPTR);
+    }
+    const int64_t chunks = (m + KAD_ROW_CHUNK - 1) / KAD_ROW_CHUNK;
+    for (int64_t c = t0; c < chunks; c += stride) {
+        const int64_t e0 = c * KAD_ROW_CHUNK;
+        const int64_t e1 = (e0 + KAD_ROW_CHUNK < m) ? e0 + KAD_ROW_CHUNK : m;
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int64_t)rp[mid] <= e0)
+                lo = mid;
+            else
+                hi = mid - 1;
         }
-        for (int e = a + lane; e < b; e += 32) {
+        int v = lo;
+        int64_t vbeg = rp[v], vend = rp[v + 1];
+        int prev = -1;
+        for (int64_t e = e0; e < e1; e++) {
+            while (vend <= e && v < n - 1) {
+                v++;
+                vbeg = rp[v];
+                vend = rp[v + 1];
+            }
             const int w = col[e];
             if (w < 0 || w >= n) {
                 atomicOr(err, GERR_RANGE);
-                continue;
+            } else {
+                if (w == v) atomicOr(err, GERR_SELF);
+                if (e > vbeg && (e == e0 ? col[e - 1] : prev) >= w) atomicOr(err, GERR_ORDER);
             }
-            if (w == v) atomicOr(err, GERR_SELF);
-            if (e > a && col[e - 1] >= w) atomicOr(err, GERR_ORDER);
+            prev = w;
         }
     }
 }
 
-// Every arc v->w needs its reverse w->v (binary search in the sorted row of w).
-// Runs only after k_validate_rows passed; the bounds checks stay as a guard.
 // Symmetry, given sorted duplicate-free rows: every arc (v, w) with w > v has its
 // reverse (v in row w), and there are as many arcs with w > v as with w < v.
 // (The reverse map sends the first kind into the second injectively; equal
@@ -132,35 +156,59 @@ __device__ __forceinline__ int cc_find(int32_t *parent, int x, int32_t n) {
     return x;
 }
 
-__global__ void k_cc_hook(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
-                          int32_t *parent, int *err) {
+// Join the trees of x and y: the larger root goes under the smaller (bounded
+// retries; a run-out sets GERR_CC).
+__device__ __forceinline__ void cc_link(int32_t *parent, int x, int y, int32_t n, int *err) {
+    int guard = 0;
+    for (;;) {
+        int rx = cc_find(parent, x, n), ry = cc_find(parent, y, n);
+        if (rx == ry) return;
+        if (rx < ry) {
+            const int t = rx;
+            rx = ry;
+            ry = t;
+        }
+        if (atomicCAS(parent + rx, rx, ry) == rx) return;
+        x = rx;
+        y = ry;
+        if (++guard > (1 << 20)) {
+            atomicOr(err, GERR_CC);
+            return;
+        }
+    }
+}
+
+// Components by neighbour sampling (the order of links does not matter: every
+// tree's root is its smallest id).  Rounds 0 and 1 link each vertex with its
+// r-th neighbour; after compression, the most frequent root in a sample of
+// vertices is taken as the large component, and only vertices outside it link
+// with all their neighbours.  Every edge between two trees is then seen from a
+// vertex outside the large one, so the result is the connected components.
+__global__ void k_cc_sample(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+                            int32_t *parent, int *err, int r) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (rp[v + 1] - rp[v] > r) cc_link(parent, v, col[rp[v] + r], n, err);
+}
+
+__global__ void k_cc_compress(int32_t *parent, int32_t n) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        parent[v] = cc_find(parent, v, n);
+}
+
+// roots of `count` vertices spread evenly over the ids
+__global__ void k_cc_probe(const int32_t *parent, int32_t n, int32_t *out, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        out[i] = parent[(int)(((int64_t)i * n) / count)];
+}
+
+__global__ void k_cc_rest(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+                          int32_t *parent, int *err, int big) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        if (*(volatile int32_t *)(parent + v) == big) continue; // inside the large tree
         const int a = rp[v], b = rp[v + 1];
-        for (int e = a + lane; e < b; e += 32) {
-            const int w = col[e];
-            if (w >= v) continue; // each undirected edge once
-            int x = v, y = w;
-            int guard = 0;
-            for (;;) {
-                int rx = cc_find(parent, x, n), ry = cc_find(parent, y, n);
-                if (rx == ry) break;
-                if (rx < ry) {
-                    const int t = rx;
-                    rx = ry;
-                    ry = t;
-                }
-                const int old = atomicCAS(parent + rx, rx, ry);
-                if (old == rx) break;
-                x = rx;
-                y = ry;
-                if (++guard > (1 << 20)) {
-                    atomicOr(err, GERR_CC);
-                    break;
-                }
-            }
-        }
+        for (int e = a + 2 + lane; e < b; e += 32) cc_link(parent, v, col[e], n, err);
     }
 }
 
@@ -173,10 +221,28 @@ __global__ void k_cc_flatten(int32_t *parent, int32_t *comp, int32_t n) {
 // largest degree, then smallest id.
 __global__ void k_best_root(const int32_t *__restrict__ rp, const int32_t *__restrict__ comp, int32_t n,
                             unsigned long long *best) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    // one atomic per warp when its vertices share a component (the common case:
+    // one large component), else one per vertex
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t v = base + threadIdx.x;
+        const bool in = v < n;
+        const int c = in ? comp[v] : -1;
         const unsigned long long key =
-            ((unsigned long long)(uint32_t)(rp[v + 1] - rp[v]) << 32) | (0xffffffffu - (uint32_t)v);
-        atomicMax(best + comp[v], key);
+            in ? (((unsigned long long)(uint32_t)(rp[v + 1] - rp[v]) << 32) | (0xffffffffu - (uint32_t)v)) : 0ull;
+        const int c0 = __shfl_sync(0xffffffffu, c, 0);
+        if (__all_sync(0xffffffffu, c == c0)) {
+            unsigned long long k = key;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, k, o);
+                k = (y > k) ? y : k;
+            }
+            if (lane == 0 && c0 >= 0) atomicMax(best + c0, k);
+        } else if (in) {
+            atomicMax(best + c, key);
+        }
     }
 }
 
@@ -281,7 +347,8 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
     }
     GCHK(cudaMemsetAsync(d_flags, 0, 8 * sizeof(int), st));
     k_check_ends<<<1, 32, 0, st>>>(gd.rp, n, gd.m, d_flags);
-    k_validate_rows<<<gw, T, 0, st>>>(gd.rp, gd.col, n, gd.m, d_flags);
+    k_validate_rows<<<grid_for(((gd.m > n ? gd.m : n) + KAD_ROW_CHUNK - 1) / KAD_ROW_CHUNK + 1, T, 65535), T, 0, st>>>(
+        gd.rp, gd.col, n, gd.m, d_flags);
     GCHK(cudaGetLastError());
     GCHK(cudaMemcpyAsync(h_flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     GCHK(cudaStreamSynchronize(st));
@@ -304,7 +371,29 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
 
     // components
     k_cc_init<<<gv, T, 0, st>>>(parent, n);
-    k_cc_hook<<<gw, T, 0, st>>>(gd.rp, gd.col, n, parent, d_flags);
+    for (int r = 0; r < 2; r++) k_cc_sample<<<gv, T, 0, st>>>(gd.rp, gd.col, n, parent, d_flags, r);
+    k_cc_compress<<<gv, T, 0, st>>>(parent, n);
+    {
+        const int probes = (n < 1024) ? n : 1024;
+        int32_t *d_probe = q1; // free until the BFS
+        int32_t h_probe[1024];
+        k_cc_probe<<<(probes + T - 1) / T, T, 0, st>>>(parent, n, d_probe, probes);
+        GCHK(cudaGetLastError());
+        GCHK(cudaMemcpyAsync(h_probe, d_probe, (size_t)probes * 4, cudaMemcpyDeviceToHost, st));
+        GCHK(cudaStreamSynchronize(st));
+        std::sort(h_probe, h_probe + probes);
+        int big = h_probe[0], best_run = 0;
+        for (int i = 0; i < probes;) {
+            int j = i;
+            while (j < probes && h_probe[j] == h_probe[i]) j++;
+            if (j - i > best_run) {
+                best_run = j - i;
+                big = h_probe[i];
+            }
+            i = j;
+        }
+        k_cc_rest<<<gw, T, 0, st>>>(gd.rp, gd.col, n, parent, d_flags, big);
+    }
     k_cc_flatten<<<gv, T, 0, st>>>(parent, gd.comp, n);
     GCHK(cudaGetLastError());
     GCHK(cudaMemsetAsync(best, 0, (size_t)n * 8, st));

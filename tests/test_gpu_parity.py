@@ -32,7 +32,24 @@ def diamond_chain(k, width=2):
     return gen.from_edges(prev + 1, edges)
 
 
+def mixed_components(seed=9):
+    # a large R-MAT component, a grid, small random pieces and isolated vertices,
+    # with the vertex ids shuffled so that no component is a contiguous id range
+    parts = [gen.rmat(13, 8, seed=2), gen.grid(25, seed=3)] + [gen.er(40, 0.12, seed=10 + i) for i in range(6)]
+    edges, base = [], 0
+    for g in parts:
+        src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+        up = g.col > src
+        edges.append(np.stack([src[up] + base, g.col[up] + base], axis=1))
+        base += g.n
+    n = base + 700  # isolated vertices at the end
+    perm = np.random.default_rng(seed).permutation(n)
+    e = perm[np.concatenate(edges)]
+    return gen.from_edges(n, e.tolist(), name="mixed_components")
+
+
 GRAPHS = {
+    "mixed_comp": mixed_components,
     "rmat12": lambda: gen.rmat(12, 8, seed=1),
     "rmat10_s5": lambda: gen.rmat(10, 4, seed=5),
     "er60": lambda: gen.er(60, 0.1, seed=2),
