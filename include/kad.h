@@ -222,7 +222,7 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
  * Outputs (device, count entries each): d_s, d_t, d_D, d_sigma_st, d_overflow
  * (0/1), and d_paths[count * cap] (interior vertices in order of distance from
  * s, -1 padding), exactly as kad_sample_records.
- * Limits: n <= 1,600,000 (the scratch holds at least one slot; smaller graphs
+ * Limits: n <= 1,436,032 (the scratch holds at least one slot; smaller graphs
  * get up to 64 slots), count <= 1,048,576 per call; larger values return
  * KAD_ERR_INVALID_ARG before any device work.  A path longer than cap returns
  * KAD_ERR_INVALID_ARG.

@@ -40,12 +40,12 @@ const uint64_t kTuneSeed = 0x6b61646162726174ull;
 
 struct Workspace {
     int slots = 0;            // sampling slots the scratch was last zeroed for
-    size_t scratch_elems = 0; // allocated entries of label / sigma / sigma2 / list (slots x n)
+    size_t scratch_elems = 0; // allocated entries (slots x n) of the label records, sigma2 and list
     size_t bits_words = 0;    // allocated words of the bitmap
     size_t n_cap = 0;         // allocated entries of cnt / c0
     size_t path_elems = 0;    // allocated entries of the epoch ring's path rows
-    uint32_t *label = nullptr;
-    unsigned long long *sigma = nullptr, *sigma2 = nullptr;
+    uint32_t *label = nullptr; // 16-byte records per vertex and slot: label, -, sigma
+    unsigned long long *sigma2 = nullptr;
     int32_t *list = nullptr;
     uint32_t *bits = nullptr; // labelled-vertex bitmap, nw words per slot
     // epoch ring (or record buffer)
@@ -96,12 +96,11 @@ namespace {
 
 void ws_free_slots(Workspace &w) {
     cudaFree(w.label);
-    cudaFree(w.sigma);
     cudaFree(w.sigma2);
     cudaFree(w.list);
     cudaFree(w.bits);
     w.label = nullptr;
-    w.sigma = w.sigma2 = nullptr;
+    w.sigma2 = nullptr;
     w.list = nullptr;
     w.bits = nullptr;
     w.slots = 0;
@@ -165,9 +164,9 @@ template <typename T> void dfree_s(T *&p, cudaStream_t st) {
 // geometric growth, so that a workspace meeting ever larger queries reallocates rarely
 size_t grow(size_t need, size_t have) { return (need > have + have / 2) ? need : have + have / 2; }
 
-// bytes of sampling scratch per slot and vertex: label 4, sigma 8, sigma2 8, list 4
-// (plus one bit of the labelled-vertex bitmap)
-const size_t kSlotBytesPerVertex = 25;
+// bytes of sampling scratch per slot and vertex: label record 16 (label, -,
+// sigma), sigma2 8, list 4 (plus one bit of the labelled-vertex bitmap)
+const size_t kSlotBytesPerVertex = 29;
 
 size_t nwords(int32_t n) { return ((size_t)n + 31) / 32; }
 
@@ -198,17 +197,14 @@ kad_status ensure_slots(kad_graph *g, Workspace &w, int slots, cudaStream_t st) 
     if (need > w.scratch_elems || need_bits > w.bits_words) {
         const size_t ne = grow(need, w.scratch_elems), nb = grow(need_bits, w.bits_words);
         dfree_s(w.label, st);
-        dfree_s(w.sigma, st);
         dfree_s(w.sigma2, st);
         dfree_s(w.list, st);
         dfree_s(w.bits, st);
         w.scratch_elems = w.bits_words = 0;
-        if (dalloc_s(&w.label, ne, st) != cudaSuccess || dalloc_s(&w.sigma, ne, st) != cudaSuccess ||
-            dalloc_s(&w.sigma2, ne, st) != cudaSuccess || dalloc_s(&w.list, ne, st) != cudaSuccess ||
-            dalloc_s(&w.bits, nb, st) != cudaSuccess) {
+        if (dalloc_s(&w.label, 4 * ne, st) != cudaSuccess || dalloc_s(&w.sigma2, ne, st) != cudaSuccess ||
+            dalloc_s(&w.list, ne, st) != cudaSuccess || dalloc_s(&w.bits, nb, st) != cudaSuccess) {
             cudaGetLastError();
             dfree_s(w.label, st);
-            dfree_s(w.sigma, st);
             dfree_s(w.sigma2, st);
             dfree_s(w.list, st);
             dfree_s(w.bits, st);
@@ -221,8 +217,7 @@ kad_status ensure_slots(kad_graph *g, Workspace &w, int slots, cudaStream_t st) 
     w.slots = slots;
     if (clear) {
         cudaError_t e;
-        if ((e = cudaMemsetAsync(w.label, 0, w.scratch_elems * 4, st)) != cudaSuccess) return fail(g, e);
-        if ((e = cudaMemsetAsync(w.sigma, 0, w.scratch_elems * 8, st)) != cudaSuccess) return fail(g, e);
+        if ((e = cudaMemsetAsync(w.label, 0, w.scratch_elems * 16, st)) != cudaSuccess) return fail(g, e);
         if ((e = cudaMemsetAsync(w.sigma2, 0, w.scratch_elems * 8, st)) != cudaSuccess) return fail(g, e);
         if ((e = cudaMemsetAsync(w.bits, 0, w.bits_words * 4, st)) != cudaSuccess) return fail(g, e);
         w.dirty = false;
@@ -542,7 +537,6 @@ SampleArgs base_args(kad_graph *g, const Workspace &w, uint64_t seed) {
     a.comp = g->gd.comp;
     a.n = g->gd.n;
     a.label = w.label;
-    a.sigma = w.sigma;
     a.sigma2 = w.sigma2;
     a.list = w.list;
     a.bits = w.bits;

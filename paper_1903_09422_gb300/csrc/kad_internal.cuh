@@ -73,14 +73,14 @@ struct SampleArgs {
     const int32_t *col;
     const int32_t *comp;
     int32_t n;
-    // per-slot scratch, slot-major: slot k uses [k*n, (k+1)*n)
+    // per-slot scratch, slot-major: slot k uses [k*n, (k+1)*n) of each array; the
+    // label array holds one 16-byte record per vertex (label, unused word, sigma)
     uint32_t *label;
     // per-slot bitmap of labelled vertices, slot k uses words [k*nw, (k+1)*nw);
     // small enough to stay in L2, it spares most label reads
     uint32_t *bits;
     int32_t nw;
     int bits_smem; // 1: the bitmap is in dynamic shared memory (nw words), bits unused
-    unsigned long long *sigma;
     unsigned long long *sigma2;
     int32_t *list;
     // random stream

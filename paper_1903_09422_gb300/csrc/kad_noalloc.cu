@@ -43,13 +43,13 @@ std::mutex g_scratch_mu;
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Bytes the slot area needs for n vertices and `slots` sampling slots: a zero
-// component array (used when the caller passes none), then label (4 B), sigma
-// (8 B), sigma2 (8 B) and list (4 B) per vertex and slot, and a bitmap of
-// labelled vertices (1 bit per vertex and slot).
+// component array (used when the caller passes none), then a 16-byte record
+// (label, unused word, sigma), sigma2 (8 B) and list (4 B) per vertex and slot,
+// and a bitmap of labelled vertices (1 bit per vertex and slot).
 size_t nwords(int64_t n) { return ((size_t)n + 31) / 32; }
 
 size_t slot_area_bytes(int64_t n, int64_t slots) {
-    return align256((size_t)n * 4) + align256((size_t)(slots * n) * 4) + 2 * align256((size_t)(slots * n) * 8) +
+    return align256((size_t)n * 4) + align256((size_t)(slots * n) * 16) + align256((size_t)(slots * n) * 8) +
            align256((size_t)(slots * n) * 4) + align256((size_t)slots * nwords(n) * 4);
 }
 
@@ -120,10 +120,8 @@ extern "C" kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row
     unsigned char *p = base + kSlotAreaOffset;
     int32_t *zero_comp = (int32_t *)p;
     p += align256((size_t)n * 4);
-    uint32_t *label = (uint32_t *)p;
-    p += align256(sn * 4);
-    unsigned long long *sigma = (unsigned long long *)p;
-    p += align256(sn * 8);
+    uint32_t *label = (uint32_t *)p; // 16-byte records: label, -, sigma
+    p += align256(sn * 16);
     unsigned long long *sigma2 = (unsigned long long *)p;
     p += align256(sn * 8);
     int32_t *list = (int32_t *)p;
@@ -138,8 +136,7 @@ extern "C" kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row
     // found disconnected by the search itself).
     cudaError_t e = cudaSuccess;
     if (!d_comp) e = cudaMemsetAsync(zero_comp, 0, (size_t)n * 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(label, 0, sn * 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sigma, 0, sn * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(label, 0, sn * 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sigma2, 0, sn * 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bits, 0, bw * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_paths, 0xff, (size_t)count * (size_t)cap * 4, st);
@@ -156,7 +153,6 @@ extern "C" kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row
     a.comp = d_comp ? d_comp : zero_comp;
     a.n = n;
     a.label = label;
-    a.sigma = sigma;
     a.sigma2 = sigma2;
     a.list = list;
     a.bits = bits;

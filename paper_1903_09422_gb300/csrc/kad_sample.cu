@@ -271,6 +271,28 @@ __device__ __forceinline__ void bits_clear_word(bool sh, uint32_t *g, int w) {
         g[w] = 0u;
 }
 
+// Per vertex and slot one 16-byte record: the label (word 0), an unused word,
+// and the path count sigma (words 2-3), so that a label and its count come in
+// one load and one 32-byte sector.
+__device__ __forceinline__ uint32_t *lab_at(uint32_t *vs, int v) { return vs + 4 * (size_t)v; }
+__device__ __forceinline__ const uint32_t *lab_at(const uint32_t *vs, int v) { return vs + 4 * (size_t)v; }
+__device__ __forceinline__ unsigned long long *sig_at(uint32_t *vs, int v) {
+    return (unsigned long long *)(vs + 4 * (size_t)v + 2);
+}
+__device__ __forceinline__ const unsigned long long *sig_at(const uint32_t *vs, int v) {
+    return (const unsigned long long *)(vs + 4 * (size_t)v + 2);
+}
+// label and sigma of v, read through L2 in one 16-byte load
+__device__ __forceinline__ void ld_vs(const uint32_t *vs, int v, uint32_t &lab, unsigned long long &sig) {
+    const uint4 x = __ldcg((const uint4 *)(vs + 4 * (size_t)v));
+    lab = x.x;
+    sig = (unsigned long long)x.z | ((unsigned long long)x.w << 32);
+}
+// the path count to use: saturated when the label says it wrapped
+__device__ __forceinline__ unsigned long long sig_val(uint32_t lab, unsigned long long sig) {
+    return (lab & KAD_OVF) ? KAD_U64MAX : sig;
+}
+
 // Physical list position of the j-th vertex labelled on side z: the s side
 // fills the slot's list from the front, the t side from the back.
 __device__ __forceinline__ int phys(int z, int j, int n) { return z ? (n - 1 - j) : j; }
@@ -302,7 +324,7 @@ __device__ __forceinline__ void emit(const SampleArgs &a, int32_t *row, int D, i
 // bitmap first.  The chosen predecessor's row bounds are fetched together with
 // its path count, ready for the next step.
 __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *label, bool bsh, const uint32_t *bits,
-                                           const unsigned long long *sigma, int z, int d, int rsC, int reC,
+                                           int z, int d, int rsC, int reC,
                                            unsigned long long r, int &p_sel, unsigned long long &s_sel, int &rs_sel,
                                            int &re_sel, unsigned long long &w_trace) {
     const int lane = threadIdx.x & 31;
@@ -319,13 +341,13 @@ __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *
         }
         if (direct) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? kad_ld_u32(label + pp[k]) : 0u;
+            for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? kad_ld_u32(lab_at(label, pp[k])) : 0u;
         } else {
 #pragma unroll
             for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? bits_ld(bsh, bits, pp[k] >> 5) : 0u;
 #pragma unroll
             for (int k = 0; k < 4; k++)
-                lp[k] = (pp[k] >= 0 && ((lp[k] >> (pp[k] & 31)) & 1u)) ? kad_ld_u32(label + pp[k]) : 0u;
+                lp[k] = (pp[k] >= 0 && ((lp[k] >> (pp[k] & 31)) & 1u)) ? kad_ld_u32(lab_at(label, pp[k])) : 0u;
         }
         unsigned long long wk[4];
         int rk[4], ek[4];
@@ -334,7 +356,7 @@ __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *
             wk[k] = 0;
             rk[k] = ek[k] = 0;
             if (pp[k] >= 0 && (lp[k] & KAD_KEY) == key) {
-                wk[k] = (lp[k] & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + pp[k]);
+                wk[k] = (lp[k] & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sig_at(label, pp[k]));
                 rk[k] = __ldg(a.rp + pp[k]);
                 ek[k] = __ldg(a.rp + pp[k] + 1);
             }
@@ -373,7 +395,7 @@ __device__ __forceinline__ void team_bar(int t, int nthreads) {
 // returned to the first warp.  The probes are counted into the trace counter.
 template <int BLOCK>
 __device__ __forceinline__ void team_from_level(const SampleArgs &a, Smem<BLOCK> &sm, int t, const uint32_t *label,
-                                                const unsigned long long *sigma, const int32_t *list, int n, int z,
+                                                const int32_t *list, int n, int z,
                                                 int ls, int lcnt, int cur, int rsC, int reC, unsigned long long r,
                                                 int &p_sel, unsigned long long &s_sel) {
     constexpr int TT = BLOCK / 2;
@@ -443,8 +465,10 @@ __device__ __forceinline__ void team_from_level(const SampleArgs &a, Smem<BLOCK>
     if (mine && sub == 0) {
         sm.c_p[t][j] = f ? p : -1;
         if (f) {
-            const uint32_t lp = kad_ld_u32(label + p);
-            sm.c_s[t][j] = (lp & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + p);
+            uint32_t lp;
+            unsigned long long sp;
+            ld_vs(label, p, lp, sp);
+            sm.c_s[t][j] = sig_val(lp, sp);
         }
     }
     unsigned long long pr = probes;
@@ -500,7 +524,7 @@ __device__ __forceinline__ void team_from_level(const SampleArgs &a, Smem<BLOCK>
 template <int BLOCK>
 __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> &sm, Stream &st, int t,
                                                const uint32_t *label, bool bsh, const uint32_t *bits,
-                                               const unsigned long long *sigma, const int32_t *list, int n, int z, int d,
+                                               const int32_t *list, int n, int z, int d,
                                                unsigned long long sc, int cur, int rsC, int reC, int D, int32_t *out,
                                                int32_t *buf_v, int32_t *buf_j, unsigned long long &w_trace) {
     constexpr int TT = BLOCK / 2, TW = TT / 32;
@@ -523,7 +547,7 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
         } else if (!(a.debug & KAD_DEBUG_TRACE_SCAN) && reC - rsC > KAD_DEG_SCAN && lcnt <= KAD_LCAP) {
             // few vertices at distance d-1: the team tests each of them for
             // adjacency to cur
-            team_from_level<BLOCK>(a, sm, t, label, sigma, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel, s_sel);
+            team_from_level<BLOCK>(a, sm, t, label, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel, s_sel);
             if (tw == 0) {
                 if (lane == 0) {
                     sm.t_p[t] = p_sel;
@@ -540,7 +564,7 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
         } else if (reC - rsC <= KAD_WARP_SCAN) {
             // a short row: the team's first warp scans it
             if (tw == 0) {
-                trace_scan(a, label, bsh, bits, sigma, z, d, rsC, reC, r, p_sel, s_sel, rs_sel, re_sel, w_trace);
+                trace_scan(a, label, bsh, bits, z, d, rsC, reC, r, p_sel, s_sel, rs_sel, re_sel, w_trace);
                 if (lane == 0) {
                     sm.t_p[t] = p_sel;
                     sm.t_s[t] = s_sel;
@@ -568,20 +592,20 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
                 for (int k = 0; k < KAD_TITEMS; k++) pp[k] = (e0 + k < reC) ? __ldg(a.col + e0 + k) : -1;
                 if (direct) {
 #pragma unroll
-                    for (int k = 0; k < KAD_TITEMS; k++) lp[k] = (pp[k] >= 0) ? kad_ld_u32(label + pp[k]) : 0u;
+                    for (int k = 0; k < KAD_TITEMS; k++) lp[k] = (pp[k] >= 0) ? kad_ld_u32(lab_at(label, pp[k])) : 0u;
                 } else {
 #pragma unroll
                     for (int k = 0; k < KAD_TITEMS; k++) lp[k] = (pp[k] >= 0) ? bits_ld(bsh, bits, pp[k] >> 5) : 0u;
 #pragma unroll
                     for (int k = 0; k < KAD_TITEMS; k++)
-                        lp[k] = (pp[k] >= 0 && ((lp[k] >> (pp[k] & 31)) & 1u)) ? kad_ld_u32(label + pp[k]) : 0u;
+                        lp[k] = (pp[k] >= 0 && ((lp[k] >> (pp[k] & 31)) & 1u)) ? kad_ld_u32(lab_at(label, pp[k])) : 0u;
                 }
                 unsigned long long mine = 0;
 #pragma unroll
                 for (int k = 0; k < KAD_TITEMS; k++) {
                     wk[k] = 0;
                     if (pp[k] >= 0 && (lp[k] & KAD_KEY) == key)
-                        wk[k] = (lp[k] & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + pp[k]);
+                        wk[k] = (lp[k] & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sig_at(label, pp[k]));
                     mine = kad_sat_add(mine, wk[k]);
                 }
                 // running sums in CSR order (saturating addition is associative):
@@ -667,8 +691,8 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
 // (sm.rs, sm.off, sm.sig), and so are the list tail, the next frontier's degree
 // sum, the meeting flag and the recorded meeting set.
 struct ExpandCtx {
-    uint32_t *label;
-    unsigned long long *sigma, *sigma2;
+    uint32_t *label; // 16-byte records: label, -, sigma
+    unsigned long long *sigma2;
     int32_t *list;
     uint32_t *bits;
     int cnt, X, tailY, n, mcap;
@@ -727,7 +751,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
     for (int k = 0; k < KAD_ITEMS; k++) {
         const bool set = vv[k] >= 0 && ((bw[k] >> (vv[k] & 31)) & 1u);
         fresh[k] = vv[k] >= 0 && !set;
-        ll[k] = set ? kad_ld_u32(c.label + vv[k]) : 0u;
+        ll[k] = set ? kad_ld_u32(lab_at(c.label, vv[k])) : 0u;
     }
     // Does an arc of this warp reach the other side's frontier?  Then the round
     // meets and no new vertex needs claiming (other warps learn it through met).
@@ -750,19 +774,19 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
         const int v = vv[k];
         if (fresh[k]) {
             if (meeting_seen) continue;
-            old[k] = atomicCAS(c.label + v, 0u, c.keyNext);
+            old[k] = atomicCAS(lab_at(c.label, v), 0u, c.keyNext);
             kind[k] = 1;
-            prev[k] = atomicAdd(c.sigma + v, sm.sig[ix[k]]);
+            prev[k] = atomicAdd(sig_at(c.label, v), sm.sig[ix[k]]);
         } else if (ll[k] != 0u) {
             const uint32_t lv = ll[k];
             if ((lv & KAD_KEY) == c.keyNext) {
                 kind[k] = 1;
-                prev[k] = atomicAdd(c.sigma + v, sm.sig[ix[k]]);
+                prev[k] = atomicAdd(sig_at(c.label, v), sm.sig[ix[k]]);
             } else if ((lv & KAD_SIDE) != c.sideX) {
                 // v is on the other side's frontier: the searches meet.  The arc
                 // that first marks v records it in M.
                 kind[k] = 2;
-                if (!(lv & KAD_INM) && !(atomicOr(c.label + v, KAD_INM) & KAD_INM)) {
+                if (!(lv & KAD_INM) && !(atomicOr(lab_at(c.label, v), KAD_INM) & KAD_INM)) {
                     const int slot = atomicAdd(&sm.mcount, 1);
                     if (slot < c.mcap) sm.m_id[slot] = v;
                 }
@@ -789,11 +813,11 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
         if (claimed[k]) bits_set(c.bsh, c.bits, vv[k]);
         if (kind[k] == 1) {
             pred_next++;
-            if (prev[k] + sm.sig[ix[k]] < prev[k]) atomicOr(c.label + vv[k], KAD_OVF);
+            if (prev[k] + sm.sig[ix[k]] < prev[k]) atomicOr(lab_at(c.label, vv[k]), KAD_OVF);
         } else if (kind[k] == 2) {
             pred_m++;
             any_m = true;
-            if (prev[k] + sm.sig[ix[k]] < prev[k]) atomicOr(c.label + vv[k], KAD_OVF2);
+            if (prev[k] + sm.sig[ix[k]] < prev[k]) atomicOr(lab_at(c.label, vv[k]), KAD_OVF2);
         }
     }
     if (any_m) sm.met[c.rb] = 1;
@@ -941,8 +965,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int32_t n = a.n;
     const size_t soff = (size_t)blockIdx.x * (size_t)n;
-    uint32_t *const label = a.label + soff;
-    unsigned long long *const sigma = a.sigma + soff;
+    uint32_t *const label = a.label + 4 * soff; // 16-byte records (label, -, sigma)
     unsigned long long *const sigma2 = a.sigma2 + soff;
     int32_t *const list = a.list + soff;
     uint32_t *const bits = a.bits + (size_t)blockIdx.x * (size_t)a.nw;
@@ -1013,12 +1036,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             sm.abort = 0;
             sm.mcount = 0;
             if (__ldg(a.comp + s) == __ldg(a.comp + t)) {
-                label[s] = 1u;            // s side, level 0
-                label[t] = KAD_SIDE | 1u; // t side, level 0
+                *(uint4 *)lab_at(label, s) = make_uint4(1u, 0u, 1u, 0u);            // s side, level 0, sigma 1
+                *(uint4 *)lab_at(label, t) = make_uint4(KAD_SIDE | 1u, 0u, 1u, 0u); // t side, level 0, sigma 1
                 bits_set(bsh, bits, s);
                 bits_set(bsh, bits, t);
-                sigma[s] = 1ull;
-                sigma[t] = 1ull;
                 list[0] = s;
                 list[n - 1] = t;
                 sm.tail[0] = sm.tail[1] = 1;
@@ -1084,11 +1105,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             if (pairs) {
                 if (tid < fx) {
                     const int u = __ldcg(list + phys(X, fb + tid, n));
-                    const uint32_t lu = kad_ld_u32(label + u);
+                    uint32_t lu;
+                    unsigned long long su;
+                    ld_vs(label, u, lu, su);
                     sm.uid[tid] = u;
                     sm.rs[tid] = __ldg(a.rp + u);
                     sm.off[tid] = __ldg(a.rp + u + 1);
-                    sm.sig[tid] = (lu & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + u);
+                    sm.sig[tid] = sig_val(lu, su);
                 }
                 __syncthreads();
                 const long long np = (long long)fx * (long long)fy;
@@ -1145,7 +1168,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     for (int k = 0; k < 4; k++) {
                         prev[k] = 0;
                         if (!hit[k]) continue;
-                        if (!(atomicOr(label + pw[k], KAD_INM) & KAD_INM)) {
+                        if (!(atomicOr(lab_at(label, pw[k]), KAD_INM) & KAD_INM)) {
                             const int slot = atomicAdd(&sm.mcount, 1);
                             if (slot < mcap) sm.m_id[slot] = pw[k];
                         }
@@ -1156,7 +1179,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                         if (!hit[k]) continue;
                         pred_m++;
                         sm.met[rb] = 1;
-                        if (prev[k] + sm.sig[pi[k]] < prev[k]) atomicOr(label + pw[k], KAD_OVF2);
+                        if (prev[k] + sm.sig[pi[k]] < prev[k]) atomicOr(lab_at(label, pw[k]), KAD_OVF2);
                     }
                 }
                 __syncthreads();
@@ -1176,9 +1199,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 } else if (tid < cnt) {
                     const int u = __ldcg(list + phys(X, cb + tid, n));
                     const int rs = __ldg(a.rp + u), re = __ldg(a.rp + u + 1);
-                    const uint32_t lu = kad_ld_u32(label + u);
+                    uint32_t lu;
+                    unsigned long long su;
+                    ld_vs(label, u, lu, su);
                     sm.rs[tid] = rs;
-                    sm.sig[tid] = (lu & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + u);
+                    sm.sig[tid] = sig_val(lu, su);
                     d = re - rs;
                 }
                 // exclusive degree offsets of the chunk: a single vertex needs no scan
@@ -1197,7 +1222,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 }
                 ExpandCtx ec;
                 ec.label = label;
-                ec.sigma = sigma;
                 ec.sigma2 = sigma2;
                 ec.list = list;
                 ec.bits = bits;
@@ -1272,9 +1296,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 // M was recorded by the arcs that first reached its members
                 for (int i = tid; i < sm.mcount; i += BLOCK) {
                     const int v = sm.m_id[i];
-                    const uint32_t lv = kad_ld_u32(label + v);
-                    const unsigned long long sx = (lv & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + v);
-                    const unsigned long long sy = (lv & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + v);
+                    uint32_t lv;
+                    unsigned long long s1;
+                    const unsigned long long s2 = kad_ld_u64(sigma2 + v); // issued with the record's load
+                    ld_vs(label, v, lv, s1);
+                    const unsigned long long sx = (lv & KAD_OVF2) ? KAD_U64MAX : s2;
+                    const unsigned long long sy = sig_val(lv, s1);
                     const unsigned long long w = kad_sat_mul(sx, sy);
                     part = kad_sat_add(part, w);
                     sm.m_w[i] = w;
@@ -1282,10 +1309,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             } else
             for (int j = yb + tid; j < ye; j += BLOCK) {
                 const int v = __ldcg(list + phys(Y, j, n));
-                const uint32_t lv = kad_ld_u32(label + v);
+                uint32_t lv;
+                unsigned long long s1;
+                ld_vs(label, v, lv, s1);
                 if (lv & KAD_INM) {
                     const unsigned long long sx = (lv & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + v);
-                    const unsigned long long sy = (lv & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + v);
+                    const unsigned long long sy = sig_val(lv, s1);
                     const unsigned long long w = kad_sat_mul(sx, sy);
                     part = kad_sat_add(part, w);
                     const int slot = atomicAdd(&sm.mcount, 1);
@@ -1334,13 +1363,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     __syncthreads();
                     for (int j = yb + tid; j < ye; j += BLOCK) {
                         const int v = __ldcg(list + phys(Y, j, n));
-                        const uint32_t lv = kad_ld_u32(label + v);
+                        const uint32_t lv = kad_ld_u32(lab_at(label, v));
                         if (!(lv & KAD_INM)) continue;
                         if (((unsigned long long)(unsigned)v >> (shift + 4)) !=
                             ((unsigned long long)prefix >> (shift + 4)))
                             continue;
                         const unsigned long long sx = (lv & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + v);
-                        const unsigned long long sy = (lv & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + v);
+                        const unsigned long long sy = (lv & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sig_at(label, v));
                         const unsigned long long w = kad_sat_mul(sx, sy);
                         const int b = ((unsigned)v >> shift) & 15;
                         const unsigned long long old = atomicAdd(&sm.bin_lo[b], w);
@@ -1405,10 +1434,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             // distance and path count of the meeting vertex on each side: side X
             // reaches it at level lev[X]+1 (count in sigma2), side Y holds it at
             // level lev[Y] (count in sigma)
-            const uint32_t lm = kad_ld_u32(label + mid);
+            uint32_t lm;
+            unsigned long long sm1;
+            const unsigned long long sm2 = kad_ld_u64(sigma2 + mid);
+            ld_vs(label, mid, lm, sm1);
             const int dX = sm.lev[X] + 1, dY = sm.lev[1 - X];
-            const unsigned long long gX = (lm & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + mid);
-            const unsigned long long gY = (lm & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sigma + mid);
+            const unsigned long long gX = (lm & KAD_OVF2) ? KAD_U64MAX : sm2;
+            const unsigned long long gY = sig_val(lm, sm1);
             dz[0] = (X == 0) ? dX : dY;
             dz[1] = (X == 1) ? dX : dY;
             gz[0] = (X == 0) ? gX : gY;
@@ -1453,7 +1485,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             if (z >= 0) {
                 unsigned long long wt = 0;
                 if (z == 0 && tl == 0) emit(a, out, D, dz[0], mid);
-                const int nb = trace_side_team<BLOCK>(a, sm, st, team, label, bsh, bits, sigma, list, n, z,
+                const int nb = trace_side_team<BLOCK>(a, sm, st, team, label, bsh, bits, list, n, z,
                                                       z ? dz[1] : dz[0], z ? gz[1] : gz[0], mid, rsM, reM, D, out,
                                                       buffered ? sm.tbuf_v : nullptr, buffered ? sm.tbuf_j : nullptr, wt);
                 if (tl == 0) {
@@ -1510,8 +1542,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     if (vr[k] < 0) continue;
-                    label[vr[k]] = 0u;
-                    sigma[vr[k]] = 0ull;
+                    *(uint4 *)lab_at(label, vr[k]) = make_uint4(0u, 0u, 0u, 0u);
                     bits_clear_word(bsh, bits, vr[k] >> 5); // every set bit of the word is a listed vertex
                 }
             }

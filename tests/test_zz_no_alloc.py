@@ -72,6 +72,6 @@ def test_noalloc_without_component_labels_on_a_disconnected_graph(kad):
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(kad):
     lib = kad.load()
-    big = 2_000_000  # above the scratch's 1.6M-vertex limit; rejected before any device work
+    big = 2_000_000  # above the scratch's 1.44M-vertex limit; rejected before any device work
     assert lib.kad_sample_records_noalloc(big, 8, 8, None, 1, 0, 0, 10, None, 8, 8, 8, 8, 8, 8, 4) == 1
     assert lib.kad_sample_records_noalloc(100, 8, 8, None, 1, 0, 0, (1 << 20) + 1, None, 8, 8, 8, 8, 8, 8, 4) == 1
