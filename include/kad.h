@@ -98,7 +98,8 @@ typedef struct {
     int32_t block_threads; /* threads per sampling block: 128, 256, 512 or 1024 (0 = 512) */
     int32_t blocks_per_sm; /* resident sampling blocks per SM the kernel is built for: 128 threads 4|8,
                               256: 2|4, 512: 1|2, 1024: 1 (0 = 4, 2, 2, 1 respectively).  When both
-                              are 0 the kernel is 512x2, or with KAD_RUN_AUTOTUNE the fastest of
+                              are 0 the kernel is 256x4 on graphs whose largest degree is at most
+                              64 and 512x2 otherwise, or with KAD_RUN_AUTOTUNE the fastest of
                               512x2, 256x4, 256x2, 1024x1 and 128x8 on this graph */
     uint32_t flags;      /* KAD_RUN_* */
     uint32_t debug;      /* KAD_DEBUG_* (tests only; results do not depend on it) */
@@ -111,8 +112,9 @@ typedef struct {
 #define KAD_RUN_AUTOTUNE 2u    /* the graph's first run (block_threads and blocks_per_sm both 0) times the
                                   same query, truncated after 4 epochs, twice under each candidate variant
                                   and keeps the fastest for the graph's later runs (graphs under 16384
-                                  vertices keep 512x2).  Off by default: 512x2 has been the fastest on
-                                  every configured workload, and tuning costs ~10 truncated runs */
+                                  vertices keep the default).  Off by default: the degree rule picks
+                                  the fastest on every configured workload, and tuning costs ~10
+                                  truncated runs */
 #define KAD_DEBUG_TRACE_SCAN 1u    /* trace-back always scans the current vertex's adjacency */
 #define KAD_DEBUG_SMEM_BITMAP 2u /* keep the labelled-vertex bitmap in shared memory when it fits */
 #define KAD_DEBUG_FULL_SCAN 4u   /* the meeting round always scans the expanding side's rows */

@@ -87,6 +87,7 @@ struct kad_graph {
     int device = 0;
     KadGraphDev gd{};
     int32_t vd = 0, ncomp = 0;
+    int32_t max_deg = 0; // largest degree
     bool poisoned = false;
     Workspace ws;
     int tuned_threads = 0, tuned_per_sm = 0; // sampling-kernel variant chosen for this graph (0 = not yet)
@@ -455,6 +456,18 @@ LaunchCfg resolve_cfg(const kad_options &o) {
     return c;
 }
 
+// The kernel variant when the caller names none: 256 threads x 4 blocks per SM
+// on graphs without hubs (largest degree <= 64: more samples in flight pay off
+// when every level is short; C3 grid 89 ms against 95 ms), else 512 x 2 (a hub's
+// level wants a wide block; C2 3.2 ms against 4.9 ms).
+LaunchCfg default_cfg(const kad_graph *g, const kad_options &o) {
+    if (o.block_threads != 0 || o.blocks_per_sm != 0) return resolve_cfg(o);
+    kad_options d = o;
+    d.block_threads = (g->max_deg <= 64) ? 256 : 512;
+    d.blocks_per_sm = (g->max_deg <= 64) ? 4 : 2;
+    return resolve_cfg(d);
+}
+
 // The slot bitmap goes to shared memory when per_sm blocks of the variant,
 // each with the bitmap, still fit an SM's shared memory.
 void choose_bitmap_home(LaunchCfg &c, int32_t n, int dev) {
@@ -571,7 +584,7 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
 // computes the same samples, so the choice changes speed only.
 kad_status autotune(kad_graph *g, Workspace &w, double eps, double delta, const kad_options &o, cudaStream_t st,
                     LaunchCfg &best) {
-    best = resolve_cfg(o);
+    best = default_cfg(g, o);
     if (!g->tuned_threads && g->gd.n < kTuneMinVertices) { // too small to matter
         g->tuned_threads = best.threads;
         g->tuned_per_sm = best.per_sm;
@@ -642,7 +655,7 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
     const size_t nclass = (size_t)tau0 + 1;
     if (nclass > (size_t)0x7fffffff || omega > ((uint64_t)1 << 40)) return KAD_ERR_INVALID_ARG;
     kad_status s;
-    LaunchCfg cfg = resolve_cfg(o);
+    LaunchCfg cfg = default_cfg(g, o);
     if (o.block_threads == 0 && o.blocks_per_sm == 0 && (o.flags & KAD_RUN_AUTOTUNE))
         if ((s = autotune(g, w, eps, delta, o, st, cfg)) != KAD_OK) return s;
     if (o.debug & KAD_DEBUG_SMEM_BITMAP) choose_bitmap_home(cfg, g->gd.n, g->device);
@@ -859,8 +872,8 @@ kad_status create_common(int32_t n, int64_t m, const int32_t *rp, const int32_t 
         kad_graph_free(g);
         return map_err(e);
     }
-    int32_t vd = 0, nc = 0;
-    s = kad_graph_setup(g->gd, flags, st, &vd, &nc, &e);
+    int32_t vd = 0, nc = 0, md = 0;
+    s = kad_graph_setup(g->gd, flags, st, &vd, &nc, &md, &e);
     if (s != KAD_OK) {
         kad_graph_free(g);
         return s;
@@ -871,6 +884,7 @@ kad_status create_common(int32_t n, int64_t m, const int32_t *rp, const int32_t 
     }
     g->vd = vd;
     g->ncomp = nc;
+    g->max_deg = md;
     *out = g;
     return KAD_OK;
 }
@@ -1121,7 +1135,7 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
         o = *opt;
     else
         fill_defaults(&o);
-    LaunchCfg cfg = resolve_cfg(o);
+    LaunchCfg cfg = default_cfg(g, o);
     if (o.debug & KAD_DEBUG_SMEM_BITMAP) choose_bitmap_home(cfg, g->gd.n, g->device);
     Workspace &w = g->ws;
     int slots = resolve_slots(g, w, o, cfg);

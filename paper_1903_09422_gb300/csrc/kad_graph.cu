@@ -246,14 +246,16 @@ __global__ void k_best_root(const int32_t *__restrict__ rp, const int32_t *__res
     }
 }
 
+// one BFS source per component (its best root); also the largest degree overall
 __global__ void k_bfs_seed(const int32_t *__restrict__ comp, const unsigned long long *__restrict__ best, int32_t n,
-                           int32_t *dist, int32_t *queue, int *qlen, int *ncomp) {
+                           int32_t *dist, int32_t *queue, int *qlen, int *ncomp, int *maxdeg) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         if (comp[v] == v) {
             const int src = (int)(0xffffffffu - (uint32_t)(best[v] & 0xffffffffull));
             dist[src] = 0;
             queue[atomicAdd(qlen, 1)] = src;
             atomicAdd(ncomp, 1);
+            atomicMax(maxdeg, (int)(best[v] >> 32));
         }
     }
 }
@@ -322,13 +324,14 @@ int grid_for(int64_t work, int threads, int cap) {
     } while (0)
 
 kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int32_t *vd_out, int32_t *ncomp_out,
+                           int32_t *maxdeg_out,
                            cudaError_t *cerr) {
     const int32_t n = gd.n;
     kad_status status = KAD_OK;
-    int *d_flags = nullptr; // [0] err, [1] qlen, [2] ncomp, [4..7] two u64 arc counts
+    int *d_flags = nullptr; // [0] err, [1] qlen, [2] ncomp, [3] largest degree, [4..7] two u64 arc counts
     int32_t *parent = nullptr, *dist = nullptr, *q0 = nullptr, *q1 = nullptr;
     unsigned long long *best = nullptr, *d_arcs = nullptr;
-    int h_flags[3] = {0, 0, 0};
+    int h_flags[4] = {0, 0, 0, 0};
     unsigned long long h_counts[2] = {0, 0};
     const int T = 256;
     const int gw = grid_for((int64_t)n * 32, T, 65535); // warp-per-vertex kernels
@@ -399,9 +402,9 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
     GCHK(cudaMemsetAsync(best, 0, (size_t)n * 8, st));
     k_best_root<<<gv, T, 0, st>>>(gd.rp, gd.comp, n, best);
     k_fill<<<gv, T, 0, st>>>(dist, n, -1);
-    k_bfs_seed<<<gv, T, 0, st>>>(gd.comp, best, n, dist, q0, d_flags + 1, d_flags + 2);
+    k_bfs_seed<<<gv, T, 0, st>>>(gd.comp, best, n, dist, q0, d_flags + 1, d_flags + 2, d_flags + 3);
     GCHK(cudaGetLastError());
-    GCHK(cudaMemcpyAsync(h_flags, d_flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaMemcpyAsync(h_flags, d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     GCHK(cudaStreamSynchronize(st));
     if (h_flags[0] & GERR_CC) {
         status = KAD_ERR_INTERNAL;
@@ -409,6 +412,7 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
     }
     qlen = h_flags[1];
     *ncomp_out = h_flags[2];
+    *maxdeg_out = h_flags[3];
 
     // multi-source BFS, level by level
     qa = q0;

@@ -175,5 +175,5 @@ struct KadGraphDev {
     int32_t *col;
     int32_t *comp;
 };
-kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int32_t *vd, int32_t *ncomp,
+kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int32_t *vd, int32_t *ncomp, int32_t *maxdeg,
                            cudaError_t *cerr);

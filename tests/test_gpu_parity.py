@@ -299,3 +299,14 @@ def test_workspace_kept_across_graphs(kad):
         if i == 1:
             kad.trim()
     kad.trim()
+
+
+def test_default_variant_follows_largest_degree(kad):
+    # without a named variant: 256x4 when no vertex has more than 64 neighbours,
+    # 512x2 otherwise; the results are those of the oracle either way
+    for g, want in ((gen.grid(48, seed=7), (256, 4)), (gen.rmat(12, 8, seed=1), (512, 2))):
+        ref = O.kadabra(g, 0.05, 0.1, 3)
+        with kad.Graph.from_csr(g) as G:
+            r = G.run(0.05, 0.1, 3)
+        assert (r["block_threads_used"], r["blocks_per_sm_used"]) == want
+        np.testing.assert_array_equal(r["counts"], ref["counts"])
