@@ -15,11 +15,14 @@
 //   4. meeting draw: w in M with probability sigma_X(w) sigma_Y(w) / sigma_st,
 //      M walked in ascending vertex id;
 //   5. trace-back from w to s, then to t, rebuilt from G and the per-vertex
-//      level labels (no predecessor graph, Appendix C.1);
+//      level labels (no predecessor graph, Appendix C.1); the two sides are
+//      traced at once by the two halves of the block, the t side's draws taken
+//      from where the s side's end;
 //   6. output of the D-1 interior vertices.
-// A sample's labels, counts and frontier lists live in global scratch of its
-// slot and are cleared by walking the list of labelled vertices, so no Theta(n)
-// reset is needed (the purpose of Appendix C.1's timestamps).
+// A sample's labels and counts (one 16-byte record per vertex) and frontier
+// lists live in global scratch of its slot and are cleared by walking the list
+// of labelled vertices, so no Theta(n) reset is needed (the purpose of Appendix
+// C.1's timestamps).  Once the run has stopped, a sample in flight gives up.
 //
 // Epochs (Algorithm 2's consistency requirement, Section 3.1, with the fixed
 // sample-to-frame assignment of the indexed-frame algorithm, Appendix D.2):
@@ -44,7 +47,7 @@
 #define KAD_PAIR_COST 16       // one pairwise adjacency test counts as this many arc reads
 #define KAD_WARP_SCAN 256       // adjacency lists up to this length are traced by one warp
 #define KAD_TITEMS 2            // consecutive arcs per thread and pass of a team's adjacency scan
-#define KAD_TBUF 64            // t-side trace steps warp 1 can buffer (longer: warp 0 traces both sides)
+#define KAD_TBUF 64            // t-side trace steps team 1 can buffer (longer: team 0 traces both sides)
 
 namespace {
 
@@ -166,8 +169,8 @@ struct Smem {
     unsigned int prefix;
     unsigned long long P;
     unsigned long long r;
-    // the stream after the meeting draw (for the t-side trace in warp 1), the
-    // stream positions that must agree, and warp 1's buffered t-side vertices
+    // the stream after the meeting draw (for the t-side trace of team 1), the
+    // stream positions that must agree, and team 1's buffered t-side vertices
     unsigned long long st_w0, st_w1;
     uint32_t st_blk;
     int st_pos;
