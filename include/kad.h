@@ -118,7 +118,10 @@ typedef struct {
 #define KAD_DEBUG_TRACE_SCAN 1u    /* trace-back always scans the current vertex's adjacency */
 #define KAD_DEBUG_SMEM_BITMAP 2u /* keep the labelled-vertex bitmap in shared memory when it fits */
 #define KAD_DEBUG_FULL_SCAN 4u   /* the meeting round always scans the expanding side's rows */
-#define KAD_DEBUG_SERIAL_TRACE 8u /* one warp traces both sides (no speculative t-side trace) */
+#define KAD_DEBUG_SERIAL_TRACE 8u /* one team traces both sides (no speculative t-side trace) */
+#define KAD_DEBUG_NO_BITMAP 16u   /* read every neighbour's label directly (the default on graphs of
+                                     average degree 8 or less) */
+#define KAD_DEBUG_BITMAP 32u      /* filter label reads through the bitmap whatever its size */
 
 /* Initialises *opt to the defaults above. */
 void kad_options_default(kad_options *opt);

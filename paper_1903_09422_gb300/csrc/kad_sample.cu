@@ -326,13 +326,14 @@ __device__ __forceinline__ void emit(const SampleArgs &a, int32_t *row, int D, i
 // of up to 32 arcs read the labels directly; longer rows filter through the
 // bitmap first.  The chosen predecessor's row bounds are fetched together with
 // its path count, ready for the next step.
-__device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *label, bool bsh, const uint32_t *bits,
+__device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *label, bool bsh, bool nobits,
+                                           const uint32_t *bits,
                                            int z, int d, int rsC, int reC,
                                            unsigned long long r, int &p_sel, unsigned long long &s_sel, int &rs_sel,
                                            int &re_sel, unsigned long long &w_trace) {
     const int lane = threadIdx.x & 31;
     const uint32_t key = (z ? KAD_SIDE : 0u) | (uint32_t)d; // level d-1
-    const bool direct = reC - rsC <= 32;
+    const bool direct = nobits || reC - rsC <= 32;
     unsigned long long carry = 0;
     for (int base = rsC; base < reC; base += 128) {
         int pp[4];
@@ -526,7 +527,7 @@ __device__ __forceinline__ void team_from_level(const SampleArgs &a, Smem<BLOCK>
 // buffered vertices, or -1 on error.
 template <int BLOCK>
 __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> &sm, Stream &st, int t,
-                                               const uint32_t *label, bool bsh, const uint32_t *bits,
+                                               const uint32_t *label, bool bsh, bool nobits, const uint32_t *bits,
                                                const int32_t *list, int n, int z, int d,
                                                unsigned long long sc, int cur, int rsC, int reC, int D, int32_t *out,
                                                int32_t *buf_v, int32_t *buf_j, unsigned long long &w_trace) {
@@ -567,7 +568,7 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
         } else if (reC - rsC <= KAD_WARP_SCAN) {
             // a short row: the team's first warp scans it
             if (tw == 0) {
-                trace_scan(a, label, bsh, bits, z, d, rsC, reC, r, p_sel, s_sel, rs_sel, re_sel, w_trace);
+                trace_scan(a, label, bsh, nobits, bits, z, d, rsC, reC, r, p_sel, s_sel, rs_sel, re_sel, w_trace);
                 if (lane == 0) {
                     sm.t_p[t] = p_sel;
                     sm.t_s[t] = s_sel;
@@ -584,7 +585,7 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
             // scan adj(cur): thread tl takes KAD_TITEMS consecutive arcs of each pass;
             // only vertices at distance d-1 on side z count
             const uint32_t key = (z ? KAD_SIDE : 0u) | (uint32_t)d;
-            const bool direct = reC - rsC <= 32;
+            const bool direct = nobits || reC - rsC <= 32;
             unsigned long long carry = 0;
             for (int base = rsC; base < reC; base += KAD_TITEMS * TT) {
                 const int e0 = base + KAD_TITEMS * tl;
@@ -702,6 +703,7 @@ struct ExpandCtx {
     int rb; // round parity: slot of sm.met / sm.next_dsum
     uint32_t sideX, keyNext;
     bool bsh, watch;
+    bool nobits; // no labelled-vertex bitmap: labels are read directly
 };
 
 // Expand the arcs first + k*stride (k < KAD_ITEMS) below `total` of the chunk.
@@ -745,16 +747,24 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
             ix[k] = lo;
         }
     }
-    uint32_t bw[KAD_ITEMS];
+    bool fresh[KAD_ITEMS]; // unlabelled when the bitmap (or the label) was read
+    if (c.nobits) {
+        // no bitmap: every neighbour's label is read directly
 #pragma unroll
-    for (int k = 0; k < KAD_ITEMS; k++) bw[k] = (vv[k] >= 0) ? bits_ld(c.bsh, c.bits, vv[k] >> 5) : 0u;
-    // only vertices whose bit is set carry a label worth reading
-    bool fresh[KAD_ITEMS]; // unlabelled when the bitmap was read
+        for (int k = 0; k < KAD_ITEMS; k++) ll[k] = (vv[k] >= 0) ? kad_ld_u32(lab_at(c.label, vv[k])) : 0u;
 #pragma unroll
-    for (int k = 0; k < KAD_ITEMS; k++) {
-        const bool set = vv[k] >= 0 && ((bw[k] >> (vv[k] & 31)) & 1u);
-        fresh[k] = vv[k] >= 0 && !set;
-        ll[k] = set ? kad_ld_u32(lab_at(c.label, vv[k])) : 0u;
+        for (int k = 0; k < KAD_ITEMS; k++) fresh[k] = vv[k] >= 0 && ll[k] == 0u;
+    } else {
+        uint32_t bw[KAD_ITEMS];
+#pragma unroll
+        for (int k = 0; k < KAD_ITEMS; k++) bw[k] = (vv[k] >= 0) ? bits_ld(c.bsh, c.bits, vv[k] >> 5) : 0u;
+        // only vertices whose bit is set carry a label worth reading
+#pragma unroll
+        for (int k = 0; k < KAD_ITEMS; k++) {
+            const bool set = vv[k] >= 0 && ((bw[k] >> (vv[k] & 31)) & 1u);
+            fresh[k] = vv[k] >= 0 && !set;
+            ll[k] = set ? kad_ld_u32(lab_at(c.label, vv[k])) : 0u;
+        }
     }
     // Does an arc of this warp reach the other side's frontier?  Then the round
     // meets and no new vertex needs claiming (other warps learn it through met).
@@ -813,7 +823,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
         claimed[k] = fresh[k] && kind[k] == 1 && old[k] == 0u;
         if (fresh[k] && kind[k] == 1 && old[k] != 0u && old[k] != c.keyNext)
             kad_set_err(a.ctl, KAD_DERR_LEVEL); // cannot happen (see above)
-        if (claimed[k]) bits_set(c.bsh, c.bits, vv[k]);
+        if (claimed[k] && !c.nobits) bits_set(c.bsh, c.bits, vv[k]);
         if (kind[k] == 1) {
             pred_next++;
             if (prev[k] + sm.sig[ix[k]] < prev[k]) atomicOr(lab_at(c.label, vv[k]), KAD_OVF);
@@ -973,6 +983,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     int32_t *const list = a.list + soff;
     uint32_t *const bits = a.bits + (size_t)blockIdx.x * (size_t)a.nw;
     const bool bsh = a.bits_smem != 0;
+    const bool nobits = a.no_bits != 0 && !bsh;
     if (bsh) {
         for (int w = tid; w < a.nw; w += BLOCK) kad_dyn_bits[w] = 0u;
         __syncthreads();
@@ -1041,8 +1052,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             if (__ldg(a.comp + s) == __ldg(a.comp + t)) {
                 *(uint4 *)lab_at(label, s) = make_uint4(1u, 0u, 1u, 0u);            // s side, level 0, sigma 1
                 *(uint4 *)lab_at(label, t) = make_uint4(KAD_SIDE | 1u, 0u, 1u, 0u); // t side, level 0, sigma 1
-                bits_set(bsh, bits, s);
-                bits_set(bsh, bits, t);
+                if (!nobits) {
+                    bits_set(bsh, bits, s);
+                    bits_set(bsh, bits, t);
+                }
                 list[0] = s;
                 list[n - 1] = t;
                 sm.tail[0] = sm.tail[1] = 1;
@@ -1237,6 +1250,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 ec.mcap = mcap;
                 ec.rb = rb;
                 ec.bsh = bsh;
+                ec.nobits = nobits;
                 ec.watch = watch_stop;
                 for (int base = 0; base < total; base += BLOCK * KAD_ITEMS) {
                     if (expand_items<BLOCK>(a, sm, ec, base + tid, BLOCK, total, pred_next, pred_m)) {
@@ -1488,7 +1502,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             if (z >= 0) {
                 unsigned long long wt = 0;
                 if (z == 0 && tl == 0) emit(a, out, D, dz[0], mid);
-                const int nb = trace_side_team<BLOCK>(a, sm, st, team, label, bsh, bits, list, n, z,
+                const int nb = trace_side_team<BLOCK>(a, sm, st, team, label, bsh, nobits, bits, list, n, z,
                                                       z ? dz[1] : dz[0], z ? gz[1] : gz[0], mid, rsM, reM, D, out,
                                                       buffered ? sm.tbuf_v : nullptr, buffered ? sm.tbuf_j : nullptr, wt);
                 if (tl == 0) {
@@ -1546,7 +1560,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 for (int k = 0; k < 4; k++) {
                     if (vr[k] < 0) continue;
                     *(uint4 *)lab_at(label, vr[k]) = make_uint4(0u, 0u, 0u, 0u);
-                    bits_clear_word(bsh, bits, vr[k] >> 5); // every set bit of the word is a listed vertex
+                    if (!nobits) bits_clear_word(bsh, bits, vr[k] >> 5); // every set bit of the word is a listed vertex
                 }
             }
             if (D > 0 || sm.abort) {
