@@ -121,7 +121,9 @@ typedef struct {
 #define KAD_DEBUG_SERIAL_TRACE 8u /* one team traces both sides (no speculative t-side trace) */
 #define KAD_DEBUG_NO_BITMAP 16u   /* read every neighbour's label directly (the default on graphs of
                                      average degree 8 or less) */
-#define KAD_DEBUG_BITMAP 32u      /* filter label reads through the bitmap whatever its size */
+#define KAD_DEBUG_BITMAP 32u      /* filter label reads through the bitmap whatever the degree */
+#define KAD_DEBUG_COARSE_BITMAP 64u /* one bitmap bit per 8 vertices (the default only when the slots'
+                                       exact bitmaps would exceed 32 MB) */
 
 /* Initialises *opt to the defaults above. */
 void kad_options_default(kad_options *opt);

@@ -543,6 +543,13 @@ kad_status launch_phase(kad_graph *g, Workspace &w, const SampleArgs &a, int blo
     b.no_bits = (g->gd.m <= 8 * (int64_t)g->gd.n) ? 1 : 0;
     if (a.debug & KAD_DEBUG_NO_BITMAP) b.no_bits = 1;
     if (a.debug & KAD_DEBUG_BITMAP) b.no_bits = 0;
+    // One bit per group of 2^shift vertices, coarse enough that the slots'
+    // bitmaps take at most 32 MB of L2 (a sample labels a tiny fraction of the
+    // vertices, so a set group bit rarely hides an unlabelled vertex).
+    b.bits_shift = 0;
+    while (b.bits_shift < 5 && (size_t)blocks * nwords(g->gd.n >> b.bits_shift) * 4 > ((size_t)32 << 20)) b.bits_shift++;
+    if (a.debug & KAD_DEBUG_COARSE_BITMAP) b.bits_shift = 3;
+    if (b.bits_smem) b.bits_shift = 0;
     e = kad_launch_sample(b, blocks, cfg.threads, cfg.per_sm, cfg.dyn_smem, st);
     if (e == cudaSuccess && w.ev_launch) e = cudaEventRecord(w.ev_launch, st);
     if (e != cudaSuccess) return fail(g, e);

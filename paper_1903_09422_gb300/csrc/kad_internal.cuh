@@ -81,7 +81,8 @@ struct SampleArgs {
     uint32_t *bits;
     int32_t nw;
     int bits_smem; // 1: the bitmap is in dynamic shared memory (nw words), bits unused
-    int no_bits;   // 1: no bitmap at all (labels read directly; for graphs whose bitmaps exceed L2)
+    int no_bits;   // 1: no bitmap at all (labels read directly)
+    int bits_shift; // one bitmap bit per 2^bits_shift consecutive vertices
     unsigned long long *sigma2;
     int32_t *list;
     // random stream

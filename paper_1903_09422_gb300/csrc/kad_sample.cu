@@ -261,11 +261,13 @@ extern __shared__ uint32_t kad_dyn_bits[];
 __device__ __forceinline__ uint32_t bits_ld(bool sh, const uint32_t *g, int w) {
     return sh ? kad_dyn_bits[w] : __ldcg(g + w);
 }
-__device__ __forceinline__ void bits_set(bool sh, uint32_t *g, int v) {
+// b is a bit index: vertex v >> shift (one bit per 2^shift consecutive vertices;
+// a set bit means that some vertex of the group may be labelled)
+__device__ __forceinline__ void bits_set(bool sh, uint32_t *g, int b) {
     if (sh)
-        atomicOr(kad_dyn_bits + (v >> 5), 1u << (v & 31));
+        atomicOr(kad_dyn_bits + (b >> 5), 1u << (b & 31));
     else
-        atomicOr(g + (v >> 5), 1u << (v & 31));
+        atomicOr(g + (b >> 5), 1u << (b & 31));
 }
 __device__ __forceinline__ void bits_clear_word(bool sh, uint32_t *g, int w) {
     if (sh)
@@ -327,7 +329,7 @@ __device__ __forceinline__ void emit(const SampleArgs &a, int32_t *row, int D, i
 // bitmap first.  The chosen predecessor's row bounds are fetched together with
 // its path count, ready for the next step.
 __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *label, bool bsh, bool nobits,
-                                           const uint32_t *bits,
+                                           int gs, const uint32_t *bits,
                                            int z, int d, int rsC, int reC,
                                            unsigned long long r, int &p_sel, unsigned long long &s_sel, int &rs_sel,
                                            int &re_sel, unsigned long long &w_trace) {
@@ -348,10 +350,10 @@ __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *
             for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? kad_ld_u32(lab_at(label, pp[k])) : 0u;
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? bits_ld(bsh, bits, pp[k] >> 5) : 0u;
+            for (int k = 0; k < 4; k++) lp[k] = (pp[k] >= 0) ? bits_ld(bsh, bits, (pp[k] >> gs) >> 5) : 0u;
 #pragma unroll
             for (int k = 0; k < 4; k++)
-                lp[k] = (pp[k] >= 0 && ((lp[k] >> (pp[k] & 31)) & 1u)) ? kad_ld_u32(lab_at(label, pp[k])) : 0u;
+                lp[k] = (pp[k] >= 0 && ((lp[k] >> ((pp[k] >> gs) & 31)) & 1u)) ? kad_ld_u32(lab_at(label, pp[k])) : 0u;
         }
         unsigned long long wk[4];
         int rk[4], ek[4];
@@ -527,7 +529,7 @@ __device__ __forceinline__ void team_from_level(const SampleArgs &a, Smem<BLOCK>
 // buffered vertices, or -1 on error.
 template <int BLOCK>
 __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> &sm, Stream &st, int t,
-                                               const uint32_t *label, bool bsh, bool nobits, const uint32_t *bits,
+                                               const uint32_t *label, bool bsh, bool nobits, int gs, const uint32_t *bits,
                                                const int32_t *list, int n, int z, int d,
                                                unsigned long long sc, int cur, int rsC, int reC, int D, int32_t *out,
                                                int32_t *buf_v, int32_t *buf_j, unsigned long long &w_trace) {
@@ -568,7 +570,7 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
         } else if (reC - rsC <= KAD_WARP_SCAN) {
             // a short row: the team's first warp scans it
             if (tw == 0) {
-                trace_scan(a, label, bsh, nobits, bits, z, d, rsC, reC, r, p_sel, s_sel, rs_sel, re_sel, w_trace);
+                trace_scan(a, label, bsh, nobits, gs, bits, z, d, rsC, reC, r, p_sel, s_sel, rs_sel, re_sel, w_trace);
                 if (lane == 0) {
                     sm.t_p[t] = p_sel;
                     sm.t_s[t] = s_sel;
@@ -599,10 +601,12 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
                     for (int k = 0; k < KAD_TITEMS; k++) lp[k] = (pp[k] >= 0) ? kad_ld_u32(lab_at(label, pp[k])) : 0u;
                 } else {
 #pragma unroll
-                    for (int k = 0; k < KAD_TITEMS; k++) lp[k] = (pp[k] >= 0) ? bits_ld(bsh, bits, pp[k] >> 5) : 0u;
+                    for (int k = 0; k < KAD_TITEMS; k++)
+                        lp[k] = (pp[k] >= 0) ? bits_ld(bsh, bits, (pp[k] >> gs) >> 5) : 0u;
 #pragma unroll
                     for (int k = 0; k < KAD_TITEMS; k++)
-                        lp[k] = (pp[k] >= 0 && ((lp[k] >> (pp[k] & 31)) & 1u)) ? kad_ld_u32(lab_at(label, pp[k])) : 0u;
+                        lp[k] = (pp[k] >= 0 && ((lp[k] >> ((pp[k] >> gs) & 31)) & 1u)) ? kad_ld_u32(lab_at(label, pp[k]))
+                                                                                       : 0u;
                 }
                 unsigned long long mine = 0;
 #pragma unroll
@@ -704,6 +708,7 @@ struct ExpandCtx {
     uint32_t sideX, keyNext;
     bool bsh, watch;
     bool nobits; // no labelled-vertex bitmap: labels are read directly
+    int gs;      // bitmap group shift: one bit per 2^gs vertices
 };
 
 // Expand the arcs first + k*stride (k < KAD_ITEMS) below `total` of the chunk.
@@ -757,13 +762,13 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
     } else {
         uint32_t bw[KAD_ITEMS];
 #pragma unroll
-        for (int k = 0; k < KAD_ITEMS; k++) bw[k] = (vv[k] >= 0) ? bits_ld(c.bsh, c.bits, vv[k] >> 5) : 0u;
-        // only vertices whose bit is set carry a label worth reading
+        for (int k = 0; k < KAD_ITEMS; k++) bw[k] = (vv[k] >= 0) ? bits_ld(c.bsh, c.bits, (vv[k] >> c.gs) >> 5) : 0u;
+        // only vertices whose group bit is set may carry a label worth reading
 #pragma unroll
         for (int k = 0; k < KAD_ITEMS; k++) {
-            const bool set = vv[k] >= 0 && ((bw[k] >> (vv[k] & 31)) & 1u);
-            fresh[k] = vv[k] >= 0 && !set;
+            const bool set = vv[k] >= 0 && ((bw[k] >> ((vv[k] >> c.gs) & 31)) & 1u);
             ll[k] = set ? kad_ld_u32(lab_at(c.label, vv[k])) : 0u;
+            fresh[k] = vv[k] >= 0 && ll[k] == 0u;
         }
     }
     // Does an arc of this warp reach the other side's frontier?  Then the round
@@ -823,7 +828,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
         claimed[k] = fresh[k] && kind[k] == 1 && old[k] == 0u;
         if (fresh[k] && kind[k] == 1 && old[k] != 0u && old[k] != c.keyNext)
             kad_set_err(a.ctl, KAD_DERR_LEVEL); // cannot happen (see above)
-        if (claimed[k] && !c.nobits) bits_set(c.bsh, c.bits, vv[k]);
+        if (claimed[k] && !c.nobits) bits_set(c.bsh, c.bits, vv[k] >> c.gs);
         if (kind[k] == 1) {
             pred_next++;
             if (prev[k] + sm.sig[ix[k]] < prev[k]) atomicOr(lab_at(c.label, vv[k]), KAD_OVF);
@@ -984,6 +989,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     uint32_t *const bits = a.bits + (size_t)blockIdx.x * (size_t)a.nw;
     const bool bsh = a.bits_smem != 0;
     const bool nobits = a.no_bits != 0 && !bsh;
+    const int gs = a.bits_shift;
     if (bsh) {
         for (int w = tid; w < a.nw; w += BLOCK) kad_dyn_bits[w] = 0u;
         __syncthreads();
@@ -1053,8 +1059,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 *(uint4 *)lab_at(label, s) = make_uint4(1u, 0u, 1u, 0u);            // s side, level 0, sigma 1
                 *(uint4 *)lab_at(label, t) = make_uint4(KAD_SIDE | 1u, 0u, 1u, 0u); // t side, level 0, sigma 1
                 if (!nobits) {
-                    bits_set(bsh, bits, s);
-                    bits_set(bsh, bits, t);
+                    bits_set(bsh, bits, s >> gs);
+                    bits_set(bsh, bits, t >> gs);
                 }
                 list[0] = s;
                 list[n - 1] = t;
@@ -1251,6 +1257,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 ec.rb = rb;
                 ec.bsh = bsh;
                 ec.nobits = nobits;
+                ec.gs = gs;
                 ec.watch = watch_stop;
                 for (int base = 0; base < total; base += BLOCK * KAD_ITEMS) {
                     if (expand_items<BLOCK>(a, sm, ec, base + tid, BLOCK, total, pred_next, pred_m)) {
@@ -1502,7 +1509,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             if (z >= 0) {
                 unsigned long long wt = 0;
                 if (z == 0 && tl == 0) emit(a, out, D, dz[0], mid);
-                const int nb = trace_side_team<BLOCK>(a, sm, st, team, label, bsh, nobits, bits, list, n, z,
+                const int nb = trace_side_team<BLOCK>(a, sm, st, team, label, bsh, nobits, gs, bits, list, n, z,
                                                       z ? dz[1] : dz[0], z ? gz[1] : gz[0], mid, rsM, reM, D, out,
                                                       buffered ? sm.tbuf_v : nullptr, buffered ? sm.tbuf_j : nullptr, wt);
                 if (tl == 0) {
@@ -1560,7 +1567,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 for (int k = 0; k < 4; k++) {
                     if (vr[k] < 0) continue;
                     *(uint4 *)lab_at(label, vr[k]) = make_uint4(0u, 0u, 0u, 0u);
-                    if (!nobits) bits_clear_word(bsh, bits, vr[k] >> 5); // every set bit of the word is a listed vertex
+                    // every set bit of the word is a group with a listed vertex
+                    if (!nobits) bits_clear_word(bsh, bits, (vr[k] >> gs) >> 5);
                 }
             }
             if (D > 0 || sm.abort) {

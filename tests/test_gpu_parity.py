@@ -111,7 +111,8 @@ def test_full_run_matches_oracle(kad, name):
                                  dict(mcap=0), dict(mcap=1), dict(ring_epochs=2), dict(slots=3, ring_epochs=2),
                                  dict(epoch_size=250), dict(debug=1), dict(debug=2), dict(debug=4),
                                  dict(debug=2, block_threads=512, blocks_per_sm=2), dict(debug=8), dict(debug=16),
-                                 dict(debug=16, block_threads=256, blocks_per_sm=4),
+                                 dict(debug=16, block_threads=256, blocks_per_sm=4), dict(debug=64),
+                                 dict(debug=64 | 32, block_threads=128, blocks_per_sm=8),
                                  dict(block_threads=128, blocks_per_sm=8),
                                  dict(block_threads=1024, blocks_per_sm=1)])
 def test_result_independent_of_launch_configuration(kad, opt):
