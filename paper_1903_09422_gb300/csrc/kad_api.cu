@@ -457,14 +457,15 @@ LaunchCfg resolve_cfg(const kad_options &o) {
 }
 
 // The kernel variant when the caller names none: 256 threads x 4 blocks per SM
-// on graphs without hubs (largest degree <= 64: more samples in flight pay off
-// when every level is short; C3 grid 89 ms against 95 ms), else 512 x 2 (a hub's
-// level wants a wide block; C2 3.2 ms against 4.9 ms).
+// on graphs of average degree up to 32 (more samples in flight pay off when rows
+// are short: C3 grid 68 ms, C4 hyperbolic 29.6 against 31.7 ms), else 512 x 2
+// (R-MAT's dense hub rows want wide blocks: C2 3.2 ms against 4.9 ms).
 LaunchCfg default_cfg(const kad_graph *g, const kad_options &o) {
     if (o.block_threads != 0 || o.blocks_per_sm != 0) return resolve_cfg(o);
+    const bool sparse = g->gd.m <= 32 * (int64_t)g->gd.n;
     kad_options d = o;
-    d.block_threads = (g->max_deg <= 64) ? 256 : 512;
-    d.blocks_per_sm = (g->max_deg <= 64) ? 4 : 2;
+    d.block_threads = sparse ? 256 : 512;
+    d.blocks_per_sm = sparse ? 4 : 2;
     return resolve_cfg(d);
 }
 
