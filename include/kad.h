@@ -124,6 +124,8 @@ typedef struct {
 #define KAD_DEBUG_BITMAP 32u      /* filter label reads through the bitmap whatever the degree */
 #define KAD_DEBUG_COARSE_BITMAP 64u /* one bitmap bit per 8 vertices (the default only when the slots'
                                        exact bitmaps would exceed 32 MB) */
+#define KAD_DEBUG_NO_MEXT 128u   /* record at most mcap meeting-set members (in shared memory);
+                                    larger sets are re-collected from the other side's frontier */
 
 /* Initialises *opt to the defaults above. */
 void kad_options_default(kad_options *opt);

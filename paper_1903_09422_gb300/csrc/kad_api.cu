@@ -34,6 +34,7 @@ namespace {
 const int kDefaultEpoch = 1000;   // N = 1000 (Appendix C.2)
 const int kDefaultCalibDiv = 100; // tau0 ~ omega / 100
 const int kDefaultMcap = 256;
+const int kMext = 3840; // meeting-set members per slot recorded beyond the first mcap
 const int32_t kTuneMinVertices = 16384;   // smaller graphs keep the default variant
 const uint32_t kTuneEpochs = 4;           // epochs of the truncated query timed per candidate
 const uint64_t kTuneSeed = 0x6b61646162726174ull;
@@ -48,6 +49,9 @@ struct Workspace {
     unsigned long long *sigma2 = nullptr;
     int32_t *list = nullptr;
     uint32_t *bits = nullptr; // labelled-vertex bitmap, nw words per slot
+    size_t mext_rows = 0;     // slots the meeting-set extension holds (kMext entries each)
+    int32_t *mext_id = nullptr;
+    unsigned long long *mext_w = nullptr;
     // epoch ring (or record buffer)
     size_t rows = 0;
     int32_t cap = 0;
@@ -100,10 +104,15 @@ void ws_free_slots(Workspace &w) {
     cudaFree(w.sigma2);
     cudaFree(w.list);
     cudaFree(w.bits);
+    cudaFree(w.mext_id);
+    cudaFree(w.mext_w);
     w.label = nullptr;
     w.sigma2 = nullptr;
     w.list = nullptr;
     w.bits = nullptr;
+    w.mext_id = nullptr;
+    w.mext_w = nullptr;
+    w.mext_rows = 0;
     w.slots = 0;
     w.scratch_elems = 0;
     w.bits_words = 0;
@@ -214,6 +223,20 @@ kad_status ensure_slots(kad_graph *g, Workspace &w, int slots, cudaStream_t st) 
         w.scratch_elems = ne;
         w.bits_words = nb;
         clear = true;
+    }
+    if ((size_t)slots > w.mext_rows) {
+        // written before it is read by every sample: never cleared
+        const size_t nr = grow((size_t)slots, w.mext_rows);
+        dfree_s(w.mext_id, st);
+        dfree_s(w.mext_w, st);
+        w.mext_rows = 0;
+        if (dalloc_s(&w.mext_id, nr * kMext, st) != cudaSuccess || dalloc_s(&w.mext_w, nr * kMext, st) != cudaSuccess) {
+            cudaGetLastError();
+            dfree_s(w.mext_id, st);
+            dfree_s(w.mext_w, st);
+            return KAD_ERR_OOM;
+        }
+        w.mext_rows = nr;
     }
     w.slots = slots;
     if (clear) {
@@ -551,6 +574,11 @@ kad_status launch_phase(kad_graph *g, Workspace &w, const SampleArgs &a, int blo
     while (b.bits_shift < 5 && (size_t)blocks * nwords(g->gd.n >> b.bits_shift) * 4 > ((size_t)32 << 20)) b.bits_shift++;
     if (a.debug & KAD_DEBUG_COARSE_BITMAP) b.bits_shift = 3;
     if (b.bits_smem) b.bits_shift = 0;
+    // meeting sets of up to mcap + kMext members are recorded during the search
+    const bool ext = !(a.debug & KAD_DEBUG_NO_MEXT) && w.mext_id && (size_t)blocks <= w.mext_rows;
+    b.mext_id = ext ? w.mext_id : nullptr;
+    b.mext_w = ext ? w.mext_w : nullptr;
+    b.mext = ext ? kMext : 0;
     e = kad_launch_sample(b, blocks, cfg.threads, cfg.per_sm, cfg.dyn_smem, st);
     if (e == cudaSuccess && w.ev_launch) e = cudaEventRecord(w.ev_launch, st);
     if (e != cudaSuccess) return fail(g, e);
@@ -960,7 +988,7 @@ size_t query_footprint(const kad_graph *g, double eps, double delta, int slots) 
     const size_t max_ring = ((size_t)1 << 30) / ((size_t)kDefaultEpoch * row_bytes);
     if (ring > max_ring) ring = max_ring;
     if (ring < 2) ring = 2;
-    return (size_t)slots * n * kSlotBytesPerVertex + ring * kDefaultEpoch * row_bytes + 8 * n +
+    return (size_t)slots * (n * kSlotBytesPerVertex + (size_t)kMext * 12) + ring * kDefaultEpoch * row_bytes + 8 * n +
            ((size_t)tau0 + 1) * 16;
 }
 

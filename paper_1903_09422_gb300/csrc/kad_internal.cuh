@@ -85,6 +85,11 @@ struct SampleArgs {
     int bits_shift; // one bitmap bit per 2^bits_shift consecutive vertices
     unsigned long long *sigma2;
     int32_t *list;
+    // meeting-set members beyond the first mcap (kept in shared memory): mext
+    // ids and weights per slot, slot k uses [k*mext, (k+1)*mext); mext = 0: none
+    int32_t *mext_id;
+    unsigned long long *mext_w;
+    int mext;
     // random stream
     uint32_t key0, key1, domain;
     // index space of this launch: [0, calib_n) are calibration samples 0..calib_n-1

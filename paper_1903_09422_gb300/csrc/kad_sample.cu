@@ -704,6 +704,8 @@ struct ExpandCtx {
     int32_t *list;
     uint32_t *bits;
     int cnt, X, tailY, n, mcap;
+    int32_t *mext_id; // this slot's meeting-set extension (mext entries after the first mcap)
+    int mext;
     int rb; // round parity: slot of sm.met / sm.next_dsum
     uint32_t sideX, keyNext;
     bool bsh, watch;
@@ -807,6 +809,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
                 if (!(lv & KAD_INM) && !(atomicOr(lab_at(c.label, v), KAD_INM) & KAD_INM)) {
                     const int slot = atomicAdd(&sm.mcount, 1);
                     if (slot < c.mcap) sm.m_id[slot] = v;
+                    else if (slot - c.mcap < c.mext) c.mext_id[slot - c.mcap] = v;
                 }
                 prev[k] = atomicAdd(c.sigma2 + v, sm.sig[ix[k]]);
             }
@@ -986,6 +989,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     uint32_t *const label = a.label + 4 * soff; // 16-byte records (label, -, sigma)
     unsigned long long *const sigma2 = a.sigma2 + soff;
     int32_t *const list = a.list + soff;
+    // meeting-set members beyond the shared-memory part go to this slot's row of
+    // the global extension
+    const int mext = a.mext_id ? a.mext : 0;
+    int32_t *const mext_id = mext ? a.mext_id + (size_t)blockIdx.x * (size_t)mext : nullptr;
+    unsigned long long *const mext_w = mext ? a.mext_w + (size_t)blockIdx.x * (size_t)mext : nullptr;
     uint32_t *const bits = a.bits + (size_t)blockIdx.x * (size_t)a.nw;
     const bool bsh = a.bits_smem != 0;
     const bool nobits = a.no_bits != 0 && !bsh;
@@ -1193,6 +1201,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                         if (!(atomicOr(lab_at(label, pw[k]), KAD_INM) & KAD_INM)) {
                             const int slot = atomicAdd(&sm.mcount, 1);
                             if (slot < mcap) sm.m_id[slot] = pw[k];
+                            else if (slot - mcap < mext) mext_id[slot - mcap] = pw[k];
                         }
                         prev[k] = atomicAdd(sigma2 + pw[k], sm.sig[pi[k]]);
                     }
@@ -1254,6 +1263,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 ec.sideX = sideX;
                 ec.keyNext = keyNext;
                 ec.mcap = mcap;
+                ec.mext_id = mext_id;
+                ec.mext = mext;
                 ec.rb = rb;
                 ec.bsh = bsh;
                 ec.nobits = nobits;
@@ -1311,7 +1322,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
         if (D > 0) {
             const int Y = 1 - X;
             const int yb = sm.fb[Y], ye = sm.fe[Y];
-            const bool recorded = sm.mcount <= mcap;
+            // members recorded during the search: the first mcap in shared
+            // memory, the next mext in the slot's extension
+            const int mtot = mcap + mext;
+            const bool recorded = sm.mcount <= mtot;
             __syncthreads();
             if (tid == 0 && !recorded) sm.mcount = 0;
             __syncthreads();
@@ -1319,7 +1333,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             if (recorded) {
                 // M was recorded by the arcs that first reached its members
                 for (int i = tid; i < sm.mcount; i += BLOCK) {
-                    const int v = sm.m_id[i];
+                    const int v = (i < mcap) ? sm.m_id[i] : __ldcg(mext_id + (i - mcap));
                     uint32_t lv;
                     unsigned long long s1;
                     const unsigned long long s2 = kad_ld_u64(sigma2 + v); // issued with the record's load
@@ -1328,7 +1342,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     const unsigned long long sy = sig_val(lv, s1);
                     const unsigned long long w = kad_sat_mul(sx, sy);
                     part = kad_sat_add(part, w);
-                    sm.m_w[i] = w;
+                    if (i < mcap)
+                        sm.m_w[i] = w;
+                    else
+                        mext_w[i - mcap] = w;
                 }
             } else
             for (int j = yb + tid; j < ye; j += BLOCK) {
@@ -1363,18 +1380,44 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             const unsigned long long r = sm.r;
             if (mc <= mcap) {
                 // Small M: the exclusive prefix of each member in id order is the
-                // sum of the weights of the members with smaller ids.
-                for (int i = tid; i < mc; i += BLOCK) {
-                    const int id = sm.m_id[i];
-                    const unsigned long long w = sm.m_w[i];
-                    unsigned long long ex = 0;
-                    for (int j = 0; j < mc; j++)
-                        if (sm.m_id[j] < id) ex = kad_sat_add(ex, sm.m_w[j]);
-                    if (ex <= r && kad_sat_add(ex, w) > r) sm.mid = id;
+                // sum of the weights of the members with smaller ids.  P
+                // consecutive lanes share a member (each sums every P-th other
+                // member, in two independent exact sums) and combine by shuffles.
+                int P = 1;
+                while (P < 32 && 2 * P * mc <= BLOCK) P *= 2;
+                const int per = BLOCK / P, p = tid & (P - 1);
+                for (int base = 0; base < mc; base += per) {
+                    const int i = base + tid / P;
+                    int id = 0;
+                    unsigned long long w = 0, e0 = 0, e1 = 0;
+                    bool o0 = false, o1 = false; // an exact sum passed 2^64 - 1
+                    if (i < mc) {
+                        id = sm.m_id[i];
+                        w = sm.m_w[i];
+                        int j = p;
+                        for (; j + P < mc; j += 2 * P) {
+                            const unsigned long long a0 = (sm.m_id[j] < id) ? sm.m_w[j] : 0ull;
+                            const unsigned long long a1 = (sm.m_id[j + P] < id) ? sm.m_w[j + P] : 0ull;
+                            e0 += a0;
+                            o0 |= e0 < a0;
+                            e1 += a1;
+                            o1 |= e1 < a1;
+                        }
+                        if (j < mc) {
+                            const unsigned long long a0 = (sm.m_id[j] < id) ? sm.m_w[j] : 0ull;
+                            e0 += a0;
+                            o0 |= e0 < a0;
+                        }
+                    }
+                    unsigned long long ex = (o0 || o1) ? KAD_U64MAX : kad_sat_add(e0, e1);
+                    for (int o = 1; o < P; o <<= 1) ex = kad_sat_add(ex, __shfl_xor_sync(FULL_MASK, ex, o));
+                    if (i < mc && p == 0 && ex <= r && kad_sat_add(ex, w) > r) sm.mid = id;
                 }
             } else {
                 // Large M: select by id digits, 4 bits per pass from the top,
-                // with exact 128-bit bin sums.
+                // with exact 128-bit bin sums, over the recorded members when all
+                // were recorded, else over the other side's frontier.
+                const bool from_rec = mc <= mtot;
                 const int nb = 32 - __clz(max(n - 1, 1));
                 const int top = ((nb + 3) / 4) * 4;
                 unsigned int prefix = 0;
@@ -1385,6 +1428,18 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                         sm.bin_hi[tid] = 0;
                     }
                     __syncthreads();
+                    if (from_rec) {
+                        for (int i = tid; i < mc; i += BLOCK) {
+                            const int v = (i < mcap) ? sm.m_id[i] : __ldcg(mext_id + (i - mcap));
+                            if (((unsigned long long)(unsigned)v >> (shift + 4)) !=
+                                ((unsigned long long)prefix >> (shift + 4)))
+                                continue;
+                            const unsigned long long w = (i < mcap) ? sm.m_w[i] : __ldcg(mext_w + (i - mcap));
+                            const int b = ((unsigned)v >> shift) & 15;
+                            const unsigned long long old = atomicAdd(&sm.bin_lo[b], w);
+                            if (old + w < old) atomicAdd(&sm.bin_hi[b], 1ull);
+                        }
+                    } else
                     for (int j = yb + tid; j < ye; j += BLOCK) {
                         const int v = __ldcg(list + phys(Y, j, n));
                         const uint32_t lv = kad_ld_u32(lab_at(label, v));
@@ -1572,8 +1627,16 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 }
             }
             if (D > 0 || sm.abort) {
-                const int Y = 1 - X;
-                for (int j = sm.fb[Y] + tid; j < sm.fe[Y]; j += BLOCK) sigma2[__ldcg(list + phys(Y, j, n))] = 0ull;
+                // every vertex with a nonzero sigma2 was counted into mcount when
+                // it joined M; if all were recorded, clear just those
+                const int mc = sm.mcount;
+                if (mc <= mcap + mext) {
+                    for (int i = tid; i < mc; i += BLOCK)
+                        sigma2[(i < mcap) ? sm.m_id[i] : __ldcg(mext_id + (i - mcap))] = 0ull;
+                } else {
+                    const int Y = 1 - X;
+                    for (int j = sm.fb[Y] + tid; j < sm.fe[Y]; j += BLOCK) sigma2[__ldcg(list + phys(Y, j, n))] = 0ull;
+                }
             }
         }
         __threadfence_block();

@@ -108,7 +108,8 @@ def test_full_run_matches_oracle(kad, name):
 
 @pytest.mark.parametrize("opt", [dict(block_threads=128), dict(block_threads=256), dict(block_threads=1024),
                                  dict(block_threads=512, blocks_per_sm=2), dict(block_threads=256, blocks_per_sm=4), dict(slots=1), dict(slots=7),
-                                 dict(mcap=0), dict(mcap=1), dict(ring_epochs=2), dict(slots=3, ring_epochs=2),
+                                 dict(mcap=0), dict(mcap=1), dict(mcap=0, debug=128), dict(debug=128),
+                                 dict(ring_epochs=2), dict(slots=3, ring_epochs=2),
                                  dict(epoch_size=250), dict(debug=1), dict(debug=2), dict(debug=4),
                                  dict(debug=2, block_threads=512, blocks_per_sm=2), dict(debug=8), dict(debug=16),
                                  dict(debug=16, block_threads=256, blocks_per_sm=4), dict(debug=64),
@@ -175,15 +176,22 @@ def test_trace_methods_agree_on_hub_graph(kad):
 
 
 def test_meeting_selection_paths_agree_on_hub_graph(kad):
-    # Many-member meeting sets: force the general (digit-wise) selection and the
-    # small-set path; both must give the oracle's records.
+    # Many-member meeting sets: the rank selection over up to mcap members, the
+    # digit-wise selection over the recorded members (mcap 0 and 16: all or most
+    # in the global extension) and over the other side's frontier (no extension);
+    # all must give the oracle's records.
     g = gen.rmat(14, 16, seed=2)
     orc = O.samples(g, 5, 0, 800)
     with kad.Graph.from_csr(g) as G:
-        a = G.sample_records(5, 0, 800, mcap=0)
-        b = G.sample_records(5, 0, 800, mcap=256)
-    compare_records(a, orc)
-    compare_records(b, orc)
+        runs = [G.sample_records(5, 0, 800, mcap=0), G.sample_records(5, 0, 800, mcap=16),
+                G.sample_records(5, 0, 800, mcap=256), G.sample_records(5, 0, 800, mcap=0, debug=128),
+                G.sample_records(5, 0, 800, mcap=16, debug=128)]
+        r = G.run(0.02, 0.1, 5, mcap=16)
+    for a in runs:
+        compare_records(a, orc)
+    ref = O.kadabra(g, 0.02, 0.1, 5)
+    assert r["tau"] == ref["tau"]
+    np.testing.assert_array_equal(r["counts"], ref["counts"])
 
 
 @pytest.mark.parametrize("k", [1, 2, 5])
