@@ -341,6 +341,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rmat20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-completion-order", action="store_true", help="skip the completion-order comparison")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--slots", type=int, default=0)
@@ -423,6 +424,27 @@ def main():
     computed = sum(r["samples_computed"] for r in results)  # calibration + adaptive
     total_ms_all, samples_all, computed_all = reduce_ranks(dist, total_ms, samples, computed, dev)
 
+    # ---- the same query in completion order (the non-deterministic epochs of
+    # the local-/shared-frame algorithms): what determinism costs
+    co = None
+    if not args.no_completion_order:
+        for _ in range(2):
+            G.run_device(eps, delta, seed, d_bc=d_bc, flags=kad.KAD_RUN_COMPLETION_ORDER, **opts)
+        co_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        co_res = []
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            co_ev[i][0].record(stream)
+            co_res.append(G.run_device(eps, delta, seed, d_bc=d_bc, flags=kad.KAD_RUN_COMPLETION_ORDER, **opts))
+            co_ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        co_ms = [a.elapsed_time(b) for a, b in co_ev]
+        co_used = sum(r["tau"] + r["calib_samples"] for r in co_res)
+        co = {"value": co_used / (sum(co_ms) / 1000.0), "unit": UNIT, "time_to_stop_ms": statistics.median(co_ms),
+              "tau": [r["tau"] for r in co_res], "samples_computed": statistics.median(r["samples_computed"] for r in co_res),
+              "mode": "KAD_RUN_COMPLETION_ORDER: epoch k = the (kN+1)-th..(k+1)N-th samples to complete "
+                      "(non-deterministic; the headline value above is the deterministic mode)"}
+
     # ---- end to end through the C ABI with host buffers: pinned CSR -> graph
     # create (copy + set-up) -> run -> b~ back to pinned host memory
     h_rp = torch.from_numpy(g.row_ptr).pin_memory()
@@ -504,6 +526,7 @@ def main():
                               f"{r0['slots_used']} slots",
             "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
             "clocks": clk,
+            "completion_order": co,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -115,6 +115,13 @@ typedef struct {
                                   vertices keep the default).  Off by default: the degree rule picks
                                   the fastest on every configured workload, and tuning costs ~10
                                   truncated runs */
+#define KAD_RUN_COMPLETION_ORDER 4u /* the non-deterministic mode of the epoch-based framework
+                                  (Section 3.1; local-/shared-frame of Section 3.2): epoch k holds
+                                  the samples that were the (kN+1)-th to (k+1)N-th to complete,
+                                  instead of samples kN..(k+1)N-1, so no epoch waits for a slow
+                                  sample drawn early.  Each check still sees a consistent state
+                                  (the first (k+1)N completed samples, tau = (k+1)N); which samples
+                                  those are depends on timing.  kad_run_order lists them. */
 #define KAD_DEBUG_TRACE_SCAN 1u    /* trace-back always scans the current vertex's adjacency */
 #define KAD_DEBUG_SMEM_BITMAP 2u /* keep the labelled-vertex bitmap in shared memory when it fits */
 #define KAD_DEBUG_FULL_SCAN 4u   /* the meeting round always scans the expanding side's rows */
@@ -246,6 +253,17 @@ kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row_ptr, const
                                       const int32_t *d_comp, uint64_t seed, uint32_t domain, uint64_t i0,
                                       int64_t count, kad_stream_t stream, int32_t *d_s, int32_t *d_t, int32_t *d_D,
                                       uint64_t *d_sigma_st, uint8_t *d_overflow, int32_t *d_paths, int32_t cap);
+
+/*
+ * kad_run_order -- after a KAD_RUN_COMPLETION_ORDER run on g: idx_out[q] = the
+ * adaptive sample index (phase 0 of the random stream) that took fold position q,
+ * for q < count.  Positions [0, tau) are the samples the run counted, in epochs
+ * of N; later positions completed after the stop was decided.  Valid until the
+ * next run on g; count <= samples_computed - calib_samples (every completed
+ * adaptive sample took a position).  idx_out is host memory.  Errors:
+ * KAD_ERR_INVALID_ARG (no such run, or count out of range), KAD_ERR_CUDA.
+ */
+kad_status kad_run_order(kad_graph *g, uint64_t *idx_out, uint64_t count);
 
 /*
  * kad_eval_fg -- the stop-check kernel's f and g (Appendix B) for n vertices on

@@ -58,6 +58,13 @@ struct Workspace {
     int32_t *paths = nullptr;
     int32_t *plen = nullptr;
     uint8_t *pflag = nullptr;
+    unsigned long long *pidx = nullptr; // completion order: the sample index at each fold position
+    size_t pidx_cap = 0;
+    int32_t *stage = nullptr;           // completion order: one staging path row per slot
+    size_t stage_elems = 0;
+    // the last run on this workspace, for kad_run_order
+    bool last_fast = false;
+    uint64_t last_positions = 0;
     // per-vertex state
     uint32_t *cnt = nullptr, *c0 = nullptr;
     double *bc = nullptr;         // bc output staged here before a copy to host memory
@@ -123,6 +130,8 @@ void ws_free_all(Workspace &w) {
     cudaFree(w.paths);
     cudaFree(w.plen);
     cudaFree(w.pflag);
+    cudaFree(w.pidx);
+    cudaFree(w.stage);
     cudaFree(w.cnt);
     cudaFree(w.c0);
     cudaFree(w.bc);
@@ -268,6 +277,33 @@ kad_status ensure_rows(Workspace &w, size_t rows, int32_t cap, cudaStream_t st) 
     w.rows = nr;
     w.cap = cap;
     w.path_elems = ne;
+    return KAD_OK;
+}
+
+// Completion order: a path row per slot for the trace-back before the sample
+// takes its fold position, and the sample index of every fold position a run
+// can hand out (at most max_epochs * N).
+kad_status ensure_order(Workspace &w, size_t stage_elems, size_t positions, cudaStream_t st) {
+    if (w.stage_elems < stage_elems) {
+        const size_t ne = grow(stage_elems, w.stage_elems);
+        dfree_s(w.stage, st);
+        w.stage_elems = 0;
+        if (dalloc_s(&w.stage, ne, st) != cudaSuccess) {
+            cudaGetLastError();
+            return KAD_ERR_OOM;
+        }
+        w.stage_elems = ne;
+    }
+    if (w.pidx_cap < positions) {
+        const size_t np = grow(positions, w.pidx_cap);
+        dfree_s(w.pidx, st);
+        w.pidx_cap = 0;
+        if (dalloc_s(&w.pidx, np, st) != cudaSuccess) {
+            cudaGetLastError();
+            return KAD_ERR_OOM;
+        }
+        w.pidx_cap = np;
+    }
     return KAD_OK;
 }
 
@@ -672,6 +708,7 @@ void ws_adopt(kad_graph *g) {
         g->ws = g_ws_cache[g->device];
         g_ws_cache[g->device] = Workspace();
         g_ws_cached[g->device] = false;
+        g->ws.last_fast = false; // its last run was on another graph
     }
 }
 
@@ -716,6 +753,9 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
     if ((s = ensure_fixed(g, w, nclass, ring, st)) != KAD_OK) return s;
     if ((s = ensure_slots(g, w, slots, st)) != KAD_OK) return s;
     if ((s = ensure_rows(w, ring * N, cap, st)) != KAD_OK) return s;
+    const bool fast = (o.flags & KAD_RUN_COMPLETION_ORDER) != 0;
+    if (fast && (s = ensure_order(w, (size_t)slots * cap, (size_t)max_epochs * N, st)) != KAD_OK) return s;
+    w.last_fast = false;
 
     Events ev(w, (o.flags & KAD_RUN_TIMING) != 0);
     cudaError_t e;
@@ -749,6 +789,10 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
     a.cap = cap;
     a.plen = w.plen;
     a.pflag = w.pflag;
+    a.fast = fast ? 1 : 0;
+    a.stage = fast ? w.stage : nullptr;
+    a.pidx = fast ? w.pidx : nullptr;
+    a.pidx_cap = fast ? (unsigned long long)max_epochs * N : 0ull;
     a.epoch_done = w.epoch_done;
     a.cnt = w.cnt;
     a.c0 = w.c0;
@@ -821,17 +865,22 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
         if (hc.stop) break;
         if (launches > 4 * max_epochs + 8) return KAD_ERR_INTERNAL; // cannot happen: tau >= omega stops
         const uint64_t closed = hc.closed;
-        uint64_t i1 = (closed + ring < max_epochs ? closed + ring : max_epochs) * N;
+        const uint64_t lim = closed + ring < max_epochs ? closed + ring : max_epochs;
+        uint64_t i1 = lim * N;
+        if (fast) // every issued sample takes one fold position, all inside the ring window
+            i1 = issued + (lim * N > hc.qnext ? lim * N - hc.qnext : 0);
         if (i1 < issued) i1 = issued;
         a.calib_n = 0;
         a.i0 = issued;
         a.i1 = i1;
-        a.k_end = i1 / N;
+        a.k_end = lim;
         if ((s = launch_phase(g, w, a, slots, cfg, 0, st)) != KAD_OK) return s;
         launches++;
         issued = i1;
     }
     const uint64_t tau = hc.tau;
+    w.last_fast = fast;
+    w.last_positions = hc.qnext < (uint64_t)max_epochs * N ? hc.qnext : (uint64_t)max_epochs * N;
     unsigned long long work[KAD_WORK_WORDS];
     if ((e = cudaMemcpyAsync(work, w.work, sizeof(work), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(g, e);
 
@@ -1159,6 +1208,17 @@ kad_status kad_run_device(kad_graph *g, double eps, double delta, uint64_t seed,
     if (!g) return KAD_ERR_INVALID_ARG;
     ws_adopt(g);
     return run_impl(g, g->ws, eps, delta, seed, (cudaStream_t)stream, opt, d_bc, d_counts, out, false);
+}
+
+kad_status kad_run_order(kad_graph *g, uint64_t *idx_out, uint64_t count) {
+    if (!g || (count && !idx_out)) return KAD_ERR_INVALID_ARG;
+    const Workspace &w = g->ws;
+    if (!w.last_fast || count > w.last_positions) return KAD_ERR_INVALID_ARG;
+    if (count == 0) return KAD_OK;
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(g, cudaGetLastError());
+    const cudaError_t e = cudaMemcpy(idx_out, w.pidx, count * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(g, e);
+    return KAD_OK;
 }
 
 kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint64_t i0, int64_t count,

@@ -57,6 +57,7 @@ struct KadCtl {
     // block finished; and the sample indices handed out when the stop was decided
     unsigned long long t_start, t_calib, t_first_close, t_stop, t_end;
     unsigned long long issued_at_stop;
+    unsigned long long qnext; // completion order: fold positions taken so far
 };
 
 // Host-mapped page of a run (pinned host memory the kernel writes through).
@@ -103,6 +104,14 @@ struct SampleArgs {
     // outputs (RING, RECORD)
     int32_t *paths;
     int32_t cap;
+    // completion order (RING): 1 = an adaptive sample takes the next fold
+    // position when its path is complete; its path is traced into the slot's
+    // staging row (cap entries per slot) and then copied to the position's ring
+    // row; pidx[position] = its sample index (positions < pidx_cap)
+    int fast;
+    int32_t *stage;
+    unsigned long long *pidx;
+    unsigned long long pidx_cap;
     int32_t *plen;
     uint8_t *pflag;
     uint32_t epoch; // N

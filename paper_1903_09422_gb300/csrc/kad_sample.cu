@@ -191,6 +191,7 @@ struct Smem {
     int32_t tbuf_v[KAD_TBUF], tbuf_j[KAD_TBUF];
     unsigned long long sst;
     unsigned long long idx;
+    unsigned long long qpos; // completion order: the sample's fold position
     unsigned long long k;
     unsigned long long ovf_acc;
     unsigned long long acc[KAD_WORK_WORDS];
@@ -1489,12 +1490,18 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             sm.tmark = now;
         }
         // ---------------------------------------------------- trace-back + output
+        // In completion order the fold position (and with it the ring row) is
+        // taken once the path is complete; the path is traced into the slot's
+        // staging row meanwhile.
+        const bool by_completion = a.mode == KAD_MODE_RING && a.fast && !calib;
         size_t row = 0;
         if (a.mode == KAD_MODE_RING)
             row = (size_t)((idx / a.epoch) % a.ring) * a.epoch + (size_t)(idx % a.epoch);
         else if (a.mode == KAD_MODE_RECORD)
             row = (size_t)(idx - a.i0);
-        int32_t *const out = calib ? nullptr : a.paths + row * (size_t)a.cap;
+        int32_t *const out = calib ? nullptr
+                                   : (by_completion ? a.stage + (size_t)blockIdx.x * (size_t)a.cap
+                                                    : a.paths + row * (size_t)a.cap);
         // The s side (team 0, the first half of the block) and the t side (team
         // 1) are traced at the same time.  The t side's draws follow the s side's
         // in the stream; team 1 starts where the s side ends if none of its draws
@@ -1581,6 +1588,16 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 }
             }
             __syncthreads();
+        }
+        unsigned long long pos = idx; // the sample's fold position (its index, or its completion rank)
+        if (by_completion) {
+            if (tid == 0) sm.qpos = atomicAdd(&a.ctl->qnext, 1ull);
+            __syncthreads();
+            pos = sm.qpos;
+            row = (size_t)((pos / a.epoch) % a.ring) * a.epoch + (size_t)(pos % a.epoch);
+            const int len = (D > 0) ? min(D - 1, a.cap) : 0;
+            for (int j = tid; j < len; j += BLOCK) a.paths[row * (size_t)a.cap + j] = __ldcg(out + j);
+            if (tid == 0 && pos < a.pidx_cap) a.pidx[pos] = idx;
         }
         if (tid == 0) {
             const int inc = (D > 0) ? D - 1 : 0;
@@ -1674,7 +1691,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 // Publish this sample's path (release); the block completing an
                 // epoch tries the closer role.  Epochs completed before the L table
                 // arrived are closed by the next completion (or the next launch).
-                const unsigned long long e = idx / a.epoch;
+                const unsigned long long e = pos / a.epoch;
                 const unsigned int old = atom_add_release(&a.epoch_done[e % a.ring], 1u);
                 int tc = 0;
                 if (old + 1u == a.epoch) {

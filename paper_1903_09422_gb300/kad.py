@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libkad.so")
 KAD_GRAPH_TRUSTED = 1
 KAD_RUN_TIMING = 1
 KAD_RUN_AUTOTUNE = 2
+KAD_RUN_COMPLETION_ORDER = 4
 WORK_NAMES = ("expanded", "scanned", "labelled", "pred_arcs", "trace_arcs", "increments")
 
 
@@ -60,7 +61,7 @@ class ServerOptions(ctypes.Structure):
 EXPORTS = ("kad_graph_create", "kad_graph_create_device", "kad_graph_free", "kad_graph_info", "kad_options_default",
            "kad_run", "kad_run_device", "kad_sample_records", "kad_sample_records_noalloc", "kad_eval_fg",
            "kad_server_create", "kad_server_add_graph", "kad_submit", "kad_poll", "kad_wait", "kad_server_free",
-           "kad_status_string", "kad_version", "kad_trim")
+           "kad_status_string", "kad_version", "kad_trim", "kad_run_order")
 
 _lib = None
 
@@ -116,6 +117,8 @@ def load():
     lib.kad_version.restype = u32
     lib.kad_trim.argtypes = []
     lib.kad_trim.restype = None
+    lib.kad_run_order.argtypes = [vp, vp, u64]
+    lib.kad_run_order.restype = st
     _lib = lib
     return lib
 
@@ -253,6 +256,13 @@ class Graph:
                                   d_counts.data_ptr() if d_counts is not None else None, ctypes.byref(r)),
                "kad_run_device")
         return _result_scalars(r)
+
+    def run_order(self, count):
+        """kad_run_order: the adaptive sample indices at fold positions [0, count)
+        of the last completion-order run on this graph."""
+        out = np.zeros(count, np.uint64)
+        _check(load().kad_run_order(self._h, out.ctypes.data, count), "kad_run_order")
+        return out
 
     def sample_records(self, seed, i0, count, domain=0, cap=None, stream=None, **opt):
         """Per-sample records of samples [i0, i0+count) (same layout as the oracle's)."""

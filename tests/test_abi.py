@@ -56,4 +56,5 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     # n < 2 and NULL arrays are refused on the host
     assert lib.kad_graph_create(1, None, None, 0, None, ctypes.byref(h)) == 1
     assert lib.kad_run(None, 0.1, 0.1, 1, None, None, None) == 1
+    assert lib.kad_run_order(None, None, 0) == 1
     lib.kad_graph_free(None)
