@@ -555,7 +555,7 @@ int resolve_slots(kad_graph *g, const Workspace &w, const kad_options &o, const 
     if (!fits && cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
         const size_t per = kSlotBytesPerVertex * (size_t)g->gd.n;
         size_t budget = fr / 3 + w.scratch_elems * (kSlotBytesPerVertex - 1) + w.bits_words * 4; // held counts too
-        const size_t maxb = (size_t)64 << 30;
+        const size_t maxb = (size_t)96 << 30;
         if (budget > maxb) budget = maxb;
         const size_t cap = per ? budget / per : (size_t)slots;
         if ((size_t)slots > cap) slots = (int)(cap > 0 ? cap : 1);
