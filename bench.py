@@ -43,10 +43,10 @@ BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=0, 
 
 # DRAM traffic of the sampling kernel measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), bytes per computed sample, for the current kernel source;
-# a workload without an entry reports traffic null.  rmat20: 3.50 GB over a launch
-# of 31,000 samples; rmat18: 1.07 GB over 31,000 (profiles/k_sample_rmat20_dram.md,
+# a workload without an entry reports traffic null.  rmat20: 2.78 GB over a launch
+# of 31,000 samples; rmat18: 0.82 GB over 31,000 (profiles/k_sample_rmat20_dram.md,
 # profiles/k_sample_rmat18_full.md).
-NCU_TRAFFIC_PER_SAMPLE = {"rmat20": 112_879, "rmat18": 34_647}
+NCU_TRAFFIC_PER_SAMPLE = {"rmat20": 89_532, "rmat18": 26_550}
 
 
 def alg_bytes(counters):

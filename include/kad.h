@@ -72,17 +72,20 @@ kad_status kad_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *co
 kad_status kad_graph_create_device(int32_t n, int64_t m, const int32_t *d_row_ptr, const int32_t *d_col,
                                    uint32_t flags, kad_stream_t stream, kad_graph **out);
 
-/* Releases the graph and its device buffers; its run workspace is kept for the
-   next graph on the same device (see kad_trim).  NULL is a no-op. */
+/* Releases the graph.  Waits until the device is idle (as cudaFree does), then
+   returns its arrays to the library's graph memory pool, which keeps them mapped
+   for the next graph; its run workspace is kept for the next graph on the same
+   device (see kad_trim).  NULL is a no-op. */
 void kad_graph_free(kad_graph *g);
 
-/* Frees the workspace kept from freed graphs.  kad_graph_free keeps the last
- * freed graph's workspace (slot scratch, epoch ring, per-vertex arrays: about
- * 24 bytes x n x 304 for the default kernel) for the next graph created on the
- * same device, one per device, so that creating and freeing graphs in a loop
- * does not allocate and clear it every time; it stays allocated until this
- * call or the end of the process.  Not for use while other threads run kad
- * calls. */
+/* Frees the workspace kept from freed graphs and unmaps the free memory of the
+ * graph pool.  kad_graph_free keeps the last freed graph's workspace (slot
+ * scratch, epoch ring, per-vertex arrays: about 29 bytes x n x slots) for the
+ * next graph created on the same device, one per device, and the graph pool
+ * keeps freed CSR arrays and set-up scratch mapped, so that creating and freeing
+ * graphs in a loop neither allocates nor clears them every time; both stay
+ * until this call or the end of the process.  Not for use while other threads
+ * run kad calls. */
 void kad_trim(void);
 
 /* Graph facts computed at creation: vertex and arc counts, VD bound, components. */

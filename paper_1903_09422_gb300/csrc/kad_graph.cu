@@ -339,15 +339,22 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
     int level = 0, qlen = 0;
     unsigned long long arcs = 0;
     int32_t *qa, *qb;
-
-    if (cudaMalloc(&d_flags, 8 * sizeof(int)) != cudaSuccess || cudaMalloc(&parent, (size_t)n * 4) != cudaSuccess ||
-        cudaMalloc(&dist, (size_t)n * 4) != cudaSuccess || cudaMalloc(&q0, (size_t)n * 4) != cudaSuccess ||
-        cudaMalloc(&q1, (size_t)n * 4) != cudaSuccess || cudaMalloc(&best, (size_t)n * 8) != cudaSuccess ||
-        cudaMalloc(&d_arcs, 8) != cudaSuccess) {
+    // one stream-ordered block from the graph pool, cut into the scratch arrays
+    // (each start rounded up to 256 bytes)
+    char *scratch = nullptr;
+    const size_t a4 = (((size_t)n * 4) + 255) & ~(size_t)255, a8 = (((size_t)n * 8) + 255) & ~(size_t)255;
+    if (kad_pool_alloc((void **)&scratch, 256 + 4 * a4 + a8 + 256, st) != cudaSuccess) {
         cudaGetLastError();
         status = KAD_ERR_OOM;
         goto done;
     }
+    d_flags = (int *)scratch;
+    parent = (int32_t *)(scratch + 256);
+    dist = (int32_t *)(scratch + 256 + a4);
+    q0 = (int32_t *)(scratch + 256 + 2 * a4);
+    q1 = (int32_t *)(scratch + 256 + 3 * a4);
+    best = (unsigned long long *)(scratch + 256 + 4 * a4);
+    d_arcs = (unsigned long long *)(scratch + 256 + 4 * a4 + a8);
     GCHK(cudaMemsetAsync(d_flags, 0, 8 * sizeof(int), st));
     k_check_ends<<<1, 32, 0, st>>>(gd.rp, n, gd.m, d_flags);
     k_validate_rows<<<grid_for(((gd.m > n ? gd.m : n) + KAD_ROW_CHUNK - 1) / KAD_ROW_CHUNK + 1, T, 65535), T, 0, st>>>(
@@ -444,12 +451,6 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
     *vd_out = 2 * level + 1;
 
 done:
-    cudaFree(d_flags);
-    cudaFree(parent);
-    cudaFree(dist);
-    cudaFree(q0);
-    cudaFree(q1);
-    cudaFree(best);
-    cudaFree(d_arcs);
+    if (scratch) cudaFreeAsync(scratch, st); // after the set-up's last kernel, in stream order
     return status;
 }

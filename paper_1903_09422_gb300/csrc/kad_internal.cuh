@@ -193,3 +193,8 @@ struct KadGraphDev {
 };
 kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int32_t *vd, int32_t *ncomp, int32_t *maxdeg,
                            cudaError_t *cerr);
+
+// Stream-ordered allocation from the library's graph pool on the current device
+// (freed memory stays mapped for the next graph until kad_trim); free with
+// cudaFreeAsync.
+cudaError_t kad_pool_alloc(void **p, size_t bytes, cudaStream_t st);
