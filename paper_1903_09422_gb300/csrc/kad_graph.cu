@@ -70,15 +70,17 @@ __global__ void k_validate_rows(const int32_t *__restrict__ rp, const int32_t *_
     }
 }
 
-// Symmetry, given sorted duplicate-free rows: every arc (v, w) with w > v has its
-// reverse (v in row w), and there are as many arcs with w > v as with w < v.
-// (The reverse map sends the first kind into the second injectively; equal
-// counts make it a bijection, so every arc of the second kind has its reverse
-// as well.)  Only the upward arcs are searched for: on skewed graphs those are
-// mostly searches in short rows.  Arc-parallel: each thread takes 32 consecutive
-// arcs, finds the row of the first by binary search in row_ptr and walks on, so
-// a hub's row is spread over many threads.  counts[0] += arcs up, counts[1] +=
-// arcs down.  Runs after k_validate_rows has accepted row_ptr.
+// Symmetry, given sorted duplicate-free rows.  Rank the vertices by (degree,
+// id) and call an arc (v, w) "up" when v ranks above w.  The graph is symmetric
+// iff every up arc has its reverse (v in row w) and there are as many up arcs as
+// down arcs: the reverse map sends up arcs into down arcs injectively, and equal
+// counts make it a bijection, so every down arc has its reverse as well.  Only
+// up arcs are searched for, so every search runs in the shorter of the two rows
+// (on skewed graphs most arcs end at a hub, whose row is never searched).
+// Arc-parallel: each thread takes 32 consecutive arcs, finds the row of the
+// first by binary search in row_ptr and walks on, so a hub's row is spread over
+// many threads.  counts[0] += up arcs, counts[1] += down arcs.  Runs after
+// k_validate_rows has accepted row_ptr.
 #define KAD_SYM_CHUNK 32
 __global__ void k_validate_sym(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
                                int64_t m, int *err, unsigned long long *counts) {
@@ -98,27 +100,59 @@ __global__ void k_validate_sym(const int32_t *__restrict__ rp, const int32_t *__
         }
         int v = lo;
         int vend = rp[v + 1];
-        for (int64_t e = e0; e < e1; e++) {
-            while ((int64_t)vend <= e && v < n - 1) {
-                v++;
-                vend = rp[v + 1];
+        // four arcs at a time, their binary searches interleaved, so that each
+        // thread keeps four independent loads in flight
+        for (int64_t e = e0; e < e1; e += 4) {
+            int wk[4], vk[4], a[4], b[4], bend[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                wk[k] = -1;
+                vk[k] = v;
+                a[k] = b[k] = bend[k] = 0;
+                if (e + k >= e1) continue;
+                while ((int64_t)vend <= e + k && v < n - 1) {
+                    v++;
+                    vend = rp[v + 1];
+                }
+                vk[k] = v;
+                const int w = col[e + k];
+                if (w < 0 || w >= n) continue;
+                wk[k] = w;
+                a[k] = rp[w];
+                b[k] = bend[k] = rp[w + 1];
             }
-            const int w = col[e];
-            if (w < 0 || w >= n) continue;
-            if (w < v) {
-                down++;
-                continue;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (wk[k] < 0) continue;
+                // the arc is "up" when its tail ranks above its head by (degree,
+                // id); only up arcs are searched, in the head's (shorter) row
+                const int dv = rp[vk[k] + 1] - rp[vk[k]], dw = bend[k] - a[k];
+                const bool upward = dv > dw || (dv == dw && vk[k] > wk[k]);
+                if (upward) {
+                    up++;
+                } else {
+                    down++;
+                    wk[k] = -1;
+                    a[k] = b[k] = 0;
+                }
             }
-            up++;
-            int a = rp[w], b = rp[w + 1];
-            while (a < b) {
-                const int mid = (a + b) >> 1;
-                if (col[mid] < v)
-                    a = mid + 1;
-                else
-                    b = mid;
+            for (;;) {
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (a[k] >= b[k]) continue;
+                    any = true;
+                    const int mid = (a[k] + b[k]) >> 1;
+                    if (col[mid] < vk[k])
+                        a[k] = mid + 1;
+                    else
+                        b[k] = mid;
+                }
+                if (!any) break;
             }
-            if (a >= rp[w + 1] || col[a] != v) atomicOr(err, GERR_SYM);
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (wk[k] >= 0 && (a[k] >= bend[k] || col[a[k]] != vk[k])) atomicOr(err, GERR_SYM);
         }
     }
 #pragma unroll

@@ -283,6 +283,33 @@ def test_bad_csr_is_rejected(kad):
         kad.Graph(np.array([0, 1], np.int32), np.array([0], np.int32))  # n = 1
 
 
+def test_single_arc_asymmetry_is_found_anywhere(kad):
+    # one arc moved to another target inside its sorted row (hub rows and short
+    # rows, every position within a thread's group of arcs): the moved arc has no
+    # reverse, so the graph is rejected
+    g = gen.rmat(13, 8, seed=2)
+    rp, col = g.row_ptr, g.col
+    rng = np.random.default_rng(5)
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(rp))
+    done = 0
+    for e in rng.permutation(g.m):
+        u, lo, hi = rows[e], rp[rows[e]], rp[rows[e] + 1]
+        left = col[e - 1] if e > lo else -1
+        right = col[e + 1] if e + 1 < hi else g.n
+        cand = [x for x in range(left + 1, right) if x != col[e] and x != u]
+        if not cand:
+            continue
+        bad = col.copy()
+        bad[e] = cand[len(cand) // 2]
+        with pytest.raises(kad.KadError) as ex:
+            kad.Graph(rp, bad)
+        assert ex.value.status == 2
+        done += 1
+        if done == 12:
+            break
+    assert done == 12
+
+
 def test_invalid_run_arguments(kad):
     g = gen.path_graph(10)
     with kad.Graph.from_csr(g) as G:
