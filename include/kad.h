@@ -96,8 +96,11 @@ typedef struct {
     uint32_t calib_div;  /* calibration length tau0 = N ceil(max(1, ceil(omega/calib_div))/N); default 100 */
     uint32_t ring_epochs;/* epochs of sample frames in flight at once (0 = automatic) */
     int32_t slots;       /* concurrent samples = resident sampling blocks (0 = automatic) */
-    int32_t mcap;        /* meeting-set size handled by the fast selection path (-1 = default;
-                            0 forces the general path; results do not depend on it) */
+    int32_t mcap;        /* meeting-set members kept in shared memory and ranked directly
+                            (-1 = default 256, at most 256); larger sets are selected digit by
+                            digit over the recorded members (up to mcap + 3840, the rest of
+                            them in a per-slot global row), beyond that over the other side's
+                            frontier.  0 forces the digit-wise path; results do not depend on it */
     int32_t block_threads; /* threads per sampling block: 128, 256, 512 or 1024 (0 = 512) */
     int32_t blocks_per_sm; /* resident sampling blocks per SM the kernel is built for: 128 threads 4|8,
                               256: 2|4, 512: 1|2, 1024: 1 (0 = 4, 2, 2, 1 respectively).  When both

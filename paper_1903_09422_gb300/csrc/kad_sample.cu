@@ -13,7 +13,8 @@
 //      degree sum (s on ties); the round that reaches the other side's frontier
 //      collects the meeting set M and the expanding side's counts at M;
 //   4. meeting draw: w in M with probability sigma_X(w) sigma_Y(w) / sigma_st,
-//      M walked in ascending vertex id;
+//      M walked in ascending vertex id (M is recorded during the search: a
+//      rank selection for up to 256 members, else digit-wise selection);
 //   5. trace-back from w to s, then to t, rebuilt from G and the per-vertex
 //      level labels (no predecessor graph, Appendix C.1); the two sides are
 //      traced at once by the two halves of the block, the t side's draws taken
@@ -31,6 +32,9 @@
 // epochs strictly in index order into the counts (the associative operation of
 // Algorithm 1 is integer addition) and evaluates the stop rule of Appendix B on
 // the state after each epoch, so every check sees an integral prefix of samples.
+// In completion order (the non-deterministic local-/shared-frame behaviour of
+// Section 3.2) epoch k holds the (kN+1)-th to (k+1)N-th samples to complete
+// instead: a sample takes its fold position once its path is complete.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
