@@ -32,12 +32,14 @@ def oracle_counts(recs, idx, n):
 
 
 def rule_holds(counts, c0, L, tau, omega, eps):
-    # Appendix B: stop iff f <= eps and g <= eps for every vertex (or tau >= omega)
+    # Appendix B: stop iff f <= eps and g <= eps for every vertex (or tau >= omega);
+    # f and g depend on a vertex only through (count, calibration count)
     if tau >= omega:
         return True
-    for v in range(len(counts)):
-        Lv = L[c0[v]]
-        if not (O.f(int(counts[v]), Lv, tau, omega) <= eps and O.g(int(counts[v]), Lv, tau, omega) <= eps):
+    pairs = np.unique(np.stack([np.asarray(counts, np.int64), np.asarray(c0, np.int64)]), axis=1)
+    for c, k in pairs.T:
+        Lv = L[k]
+        if not (O.f(int(c), Lv, tau, omega) <= eps and O.g(int(c), Lv, tau, omega) <= eps):
             return False
     return True
 
@@ -107,3 +109,25 @@ def test_completion_order_list_needs_such_a_run(kad):
         G.run(0.05, 0.1, 1)
         with pytest.raises(RuntimeError):
             G.run_order(1)
+
+
+def test_completion_order_at_full_size(kad):
+    # the benchmarked query (R-MAT scale 20, eps = 0.01) in completion order:
+    # every count against the oracle's increments of the listed samples
+    name = "rmat20"
+    g = gen.workload_graph(name)
+    w = gen.WORKLOADS[name]
+    ref = O.kadabra(g, w["eps"], w["delta"], w["seed"], max_epochs=1)  # calibration and L
+    with kad.Graph.from_csr(g) as G:
+        r = G.run(w["eps"], w["delta"], w["seed"], c0=True, flags=kad.KAD_RUN_COMPLETION_ORDER)
+        order = G.run_order(r["tau"]).astype(np.int64)
+    tau, N = r["tau"], 1000
+    np.testing.assert_array_equal(r["c0"], ref["c0"])
+    assert len(np.unique(order)) == tau
+    recs = O.samples(g, w["seed"], 0, int(order.max()) + 1)
+    counts = oracle_counts(recs, order, g.n)
+    np.testing.assert_array_equal(r["counts"].astype(np.int64), counts)
+    assert r["overflow_samples"] == int(recs["overflow"][order].sum())
+    assert rule_holds(counts, ref["c0"], ref["L"], tau, ref["omega"], w["eps"])
+    prev = oracle_counts(recs, order[: tau - N], g.n)
+    assert not rule_holds(prev, ref["c0"], ref["L"], tau - N, ref["omega"], w["eps"])
