@@ -44,9 +44,10 @@ BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=0, 
 # DRAM traffic of the sampling kernel measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), bytes per computed sample, for the current kernel source;
 # a workload without an entry reports traffic null.  rmat20: 2.78 GB over a launch
-# of 31,000 samples; rmat18: 0.82 GB over 31,000 (profiles/k_sample_rmat20_dram.md,
-# profiles/k_sample_rmat18_full.md).
-NCU_TRAFFIC_PER_SAMPLE = {"rmat20": 89_532, "rmat18": 26_550}
+# of 31,000 samples; rmat18: 0.82 GB over 31,000; hyp4m: 57.8 GB over 142,000;
+# grid2048: 697 GB over 56,000 (profiles/k_sample_rmat20_dram.md,
+# profiles/k_sample_rmat18_full.md, profiles/k_sample_hyp4m_grid2048_dram.md).
+NCU_TRAFFIC_PER_SAMPLE = {"rmat20": 89_532, "rmat18": 26_550, "hyp4m": 406_867, "grid2048": 12_449_158}
 
 
 def alg_bytes(counters):
@@ -505,8 +506,10 @@ def main():
                        "step": "one full KADABRA query (calibration + adaptive sampling to stop + b~)",
                        "l2": f"flushed between steps ({args.flush_mb} MB write)", "parallelism": f"replicas x{world}"},
             "time_to_stop_ms": statistics.median(step_ms),
+            "step_ms": [round(x, 3) for x in step_ms],
             "time_to_stop_ads_ms": statistics.median(r["t_ads_ms"] for r in results),
             "samples_computed_per_s": computed_all / (total_ms_all / 1000.0),
+            "samples_computed": int(statistics.median(r["samples_computed"] for r in results)),
             "tau": r0["tau"], "calib_samples": r0["calib_samples"], "epochs": r0["epochs"], "omega": r0["omega"],
             "vd_bound": r0["vd_bound"], "stopped_by_omega": r0["stopped_by_omega"],
             "algorithmic_teps": scanned / (sum(kt) / 1000.0),
