@@ -32,6 +32,44 @@ def diamond_chain(k, width=2):
     return gen.from_edges(prev + 1, edges)
 
 
+def rejection_ladder(la=200, lb=150, lc=200, k2=61):
+    """A graph on which the s side's trace-back draws from a count in (2^63, 2^64)
+    that is not a power of two, so Lemire's rule rejects a quarter of those draws.
+
+    Hub A (la leaves) starts a ladder of k2 width-2 diamonds and one width-3
+    diamond that ends at hub B (lc leaves); B reaches hub B' (lb leaves) through
+    one more width-2 diamond (q1, q2).  For s a leaf of A and t a leaf of B', the
+    balanced search takes t to B first (B' has the smaller degree sum), then s
+    walks the ladder and meets t's side at B: sigma_s(B) = 3 * 2^61, sigma_t(B) = 2,
+    sigma_st = 3 * 2^62.  The s side's first trace draw is U(3 * 2^61); the t side's
+    first is U(2), a real choice between q1 and q2.
+    Returns (graph, leaves of A, leaves of B')."""
+    ed, nid = [], [0]
+
+    def new():
+        nid[0] += 1
+        return nid[0] - 1
+
+    A = new()
+    aleaves = [new() for _ in range(la)]
+    ed += [(A, x) for x in aleaves]
+    prev = A
+    for _ in range(k2):
+        m1, m2, j = new(), new(), new()
+        ed += [(prev, m1), (prev, m2), (m1, j), (m2, j)]
+        prev = j
+    xs = [new() for _ in range(3)]
+    B = new()
+    for x in xs:
+        ed += [(prev, x), (x, B)]
+    q1, q2, Bp = new(), new(), new()
+    ed += [(B, q1), (B, q2), (q1, Bp), (q2, Bp)]
+    ed += [(B, new()) for _ in range(lc)]
+    bleaves = [new() for _ in range(lb)]
+    ed += [(Bp, x) for x in bleaves]
+    return gen.from_edges(nid[0], ed, name="rejection_ladder"), set(aleaves), set(bleaves)
+
+
 def mixed_components(seed=9):
     # a large R-MAT component, a grid, small random pieces and isolated vertices,
     # with the vertex ids shuffled so that no component is a contiguous id range
@@ -62,6 +100,7 @@ GRAPHS = {
     "two_comp": lambda: gen.from_edges(12, [(0, 1), (1, 2), (2, 3), (3, 0), (4, 5), (5, 6), (6, 7), (7, 8), (8, 9),
                                             (9, 10), (10, 11)]),
     "isolated": lambda: gen.from_edges(6, [(0, 1), (1, 2)]),
+    "ladder": lambda: rejection_ladder()[0],
 }
 
 
@@ -349,3 +388,46 @@ def test_default_variant_follows_average_degree(kad):
             r = G.run(0.05, 0.1, 3)
         assert (r["block_threads_used"], r["blocks_per_sm_used"]) == want
         np.testing.assert_array_equal(r["counts"], ref["counts"])
+
+
+def test_trace_draw_rejections_match_oracle(kad):
+    # Samples whose s-side trace-back draw is rejected by Lemire's rule (the
+    # count is 3 * 2^61): every later draw of the sample, including the t side's,
+    # comes from a later stream position.  The oracle shows that the range below
+    # holds such samples; the CUDA path must give the same records.
+    g, aleaves, bleaves = rejection_ladder()
+    seed, count = 7, 3000
+    orc = O.samples(g, seed, 0, count)
+    rejected = 0
+    for i in range(count):
+        s, t = int(orc["s"][i]), int(orc["t"][i])
+        if s in aleaves and t in bleaves:
+            assert int(orc["sigma_st"][i]) == 3 * 2**62
+            # stream words used by the pair, meeting and first s-side trace draws
+            # against those used without the trace draw: more than one word apart
+            # means the trace draw was rejected at least once
+            _, u3 = O.stream_draws(seed, i, 0, [g.n, g.n - 1, 3 * 2**62])
+            _, u4 = O.stream_draws(seed, i, 0, [g.n, g.n - 1, 3 * 2**62, 3 * 2**61])
+            rejected += (u4 - u3) > 1
+    assert rejected >= 10, rejected
+    assert not orc["overflow"].any()
+    with kad.Graph.from_csr(g) as G:
+        for opt in (dict(), dict(block_threads=256, blocks_per_sm=4), dict(block_threads=1024)):
+            compare_records(G.sample_records(seed, 0, count, **opt), orc)
+
+
+def test_smallest_workload_exact_triple(kad):
+    # R-MAT scale 12, eps = 0.05, delta = 0.1, seed 1: the smallest configured
+    # workload, end to end, at its own seed.
+    w = gen.WORKLOADS["rmat12"]
+    g = gen.workload_graph("rmat12")
+    ref = O.kadabra(g, w["eps"], w["delta"], w["seed"])
+    with kad.Graph.from_csr(g) as G:
+        r = G.run(w["eps"], w["delta"], w["seed"], c0=True, ltab=True)
+    assert (r["tau"], r["epochs"], r["omega"], r["calib_samples"], r["vd_bound"]) == \
+        (ref["tau"], ref["epochs"], ref["omega"], ref["calib_samples"], ref["vd"])
+    np.testing.assert_array_equal(r["c0"], ref["c0"])
+    np.testing.assert_array_equal(r["L"], ref["L"])
+    np.testing.assert_array_equal(r["counts"], ref["counts"])
+    np.testing.assert_array_equal(r["bc"], ref["bc"])
+    assert r["overflow_samples"] == ref["overflow_samples"]

@@ -2,7 +2,7 @@
 allocate device memory (they own every device buffer through their own pool, so
 the library must not call cudaMalloc/cudaFree; its scratch is a fixed device
 array instead).  Its output must equal the allocating entry point's,
-kad_sample_records, record for record, on consecutive calls.
+kad_sample_records, record for record, on consecutive calls, and the oracle's.
 
 This file is named to be collected last, so a run that stops at the first
 failure has already run every other test.
@@ -68,6 +68,35 @@ def test_noalloc_without_component_labels_on_a_disconnected_graph(kad):
         cap = G.path_cap
     _same(_noalloc(kad, g, 3, 0, 400, cap), ref1)
     _same(_noalloc(kad, g, 3, 400, 400, cap), ref2)
+
+
+def _slots_for(n):
+    """Sampling slots the fixed scratch holds for n vertices (same sizing as the
+    entry point: 48 MiB minus a 4 KiB head and 4 MiB of path lengths; per slot a
+    16-byte record, sigma2 and a list entry per vertex, and a bitmap word per 32
+    vertices; a shared component array; every part 256-byte aligned)."""
+    a = lambda x: (x + 255) & ~255
+    area = (48 << 20) - 4096 - (1 << 20) * 4
+    for slots in range(64, 0, -1):
+        need = a(n * 4) + a(slots * n * 16) + a(slots * n * 8) + a(slots * n * 4) + a(slots * ((n + 31) // 32) * 4)
+        if need <= area:
+            return slots
+    return 0
+
+
+def test_noalloc_with_fewer_slots_matches_the_oracle(kad):
+    # R-MAT scale 18 (n = 173,790) leaves room for only a few sampling slots in
+    # the fixed scratch, so the entry point runs with fewer than its 64 slots.
+    import oracle as O
+    from paper_1903_09422_gb300 import gen
+    g = gen.rmat(18, 16, seed=1)
+    assert 1 < _slots_for(g.n) < 64
+    cap = O.path_cap(g)
+    for i0, count in ((0, 240), (240, 160)):  # two calls in a row share the scratch
+        got = _noalloc(kad, g, 9, i0, count, cap)
+        ref = O.samples(g, 9, i0, count)
+        ref["overflow"] = ref["overflow"].astype(np.int32)
+        _same(got, ref)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(kad):
