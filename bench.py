@@ -42,12 +42,36 @@ UNIT = "samples/s"
 BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=0, increments=4)
 
 # DRAM traffic of the sampling kernel measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum), bytes per computed sample, for the current kernel source;
-# a workload without an entry reports traffic null.  rmat20: 2.78 GB over a launch
-# of 31,000 samples; rmat18: 0.82 GB over 31,000; hyp4m: 57.8 GB over 142,000;
-# grid2048: 697 GB over 56,000 (profiles/k_sample_rmat20_dram.md,
+# dram__bytes_write.sum), bytes per computed sample, with the SHA-256 prefix of
+# the kernel source file it was measured on.  A workload without an entry, or
+# whose kernel source has changed since, reports traffic null.  rmat20: 2.78 GB
+# over a launch of 31,000 samples; rmat18: 0.82 GB over 31,000; hyp4m: 57.8 GB
+# over 142,000; grid2048: 697 GB over 56,000 (profiles/k_sample_rmat20_dram.md,
 # profiles/k_sample_rmat18_full.md, profiles/k_sample_hyp4m_grid2048_dram.md).
-NCU_TRAFFIC_PER_SAMPLE = {"rmat20": 89_532, "rmat18": 26_550, "hyp4m": 406_867, "grid2048": 12_449_158}
+NCU_TRAFFIC_PER_SAMPLE = {
+    ("k_sample", "rmat20"): (89_532, "6fbca8b18533ff3c"),
+    ("k_sample", "rmat18"): (26_550, "6fbca8b18533ff3c"),
+    ("k_sample", "hyp4m"): (406_867, "6fbca8b18533ff3c"),
+    ("k_sample", "grid2048"): (12_449_158, "6fbca8b18533ff3c"),
+}
+KERNEL_SOURCE = {"k_sample": "kad_sample.cu"}
+
+
+def source_hash(kernel):
+    import hashlib
+    path = os.path.join(ROOT, "paper_1903_09422_gb300", "csrc", KERNEL_SOURCE[kernel])
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic_per_sample(kernel, workload):
+    """(bytes per computed sample, note): None when unmeasured or stale."""
+    ent = NCU_TRAFFIC_PER_SAMPLE.get((kernel, workload))
+    if ent is None:
+        return None, "no ncu capture of this kernel on this workload"
+    if ent[1] != source_hash(kernel):
+        return None, "stale: the kernel source changed since its ncu capture"
+    return ent[0], "ncu dram__bytes_read.sum + dram__bytes_write.sum per computed sample x samples computed"
 
 
 def alg_bytes(counters):
@@ -485,9 +509,12 @@ def main():
     achieved = sum(ab) / (sum(kt) / 1000.0) / 1e9
     per_sample = sum(ab) / max(1, sum(r["samples_computed"] for r in results))
     traffic = None
-    tps = NCU_TRAFFIC_PER_SAMPLE.get(args.workload)
+    tps, traffic_note = ncu_traffic_per_sample("k_sample", args.workload)
     if tps is not None:
         traffic = tps * statistics.mean(r["samples_computed"] for r in results)
+    # DRAM bytes actually moved per second, from the ncu traffic (a separate
+    # figure: the headline fraction is the algorithmic bytes' rate)
+    dram_gbs = traffic / (statistics.mean(kt) / 1000.0) / 1e9 if traffic is not None else None
     r0 = results[-1]
     scanned = sum(r["counters"]["scanned"] for r in results)
 
@@ -515,7 +542,8 @@ def main():
             "algorithmic_teps": scanned / (sum(kt) / 1000.0),
             "graph_setup_ms": setup_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
+                         "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
+                         "dram_gbs": dram_gbs, "dram_frac": (dram_gbs / peak) if dram_gbs is not None else None,
                          "kernel": "k_sample (adaptive phase, one persistent launch)",
                          "alg_bytes_per_sample": per_sample, "peak_kind": f"{peak_kind} (hbm_gbs burst)",
                          "kernel_ms": statistics.median(kt)},

@@ -248,9 +248,8 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
  * get up to 64 slots), count <= 1,048,576 per call; larger values return
  * KAD_ERR_INVALID_ARG before any device work.  A path longer than cap returns
  * KAD_ERR_INVALID_ARG.
- * The first call on a device looks up the array's device address for that
- * device (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  Every call shares the one array and leaves it as
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, a host-side query).  Every call shares the one array and leaves it as
  * it was at its end: the call clears what must start at zero, but calls whose
  * work overlaps on the GPU (different streams or host threads) race on it --
  * serialise them.  Returns after synchronising `stream`.

@@ -16,8 +16,6 @@
 #include <stdint.h>
 #include <string.h>
 
-#include <mutex>
-
 #include "kad_internal.cuh"
 
 namespace {
@@ -31,14 +29,8 @@ constexpr size_t kSlotAreaOffset = kHeadBytes + kPlenBytes;
 constexpr size_t kSlotArea = kNoallocBytes - kSlotAreaOffset;
 constexpr int kMaxSlots = 64;
 constexpr int kThreads = 512;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
-
-// Host-side copies of the array's device address, one per device.  In host code
-// the name g_noalloc_scratch is only a host stand-in, never a device address.
-unsigned char *g_scratch_addr[kMaxDevices];
-std::mutex g_scratch_mu;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -53,20 +45,18 @@ size_t slot_area_bytes(int64_t n, int64_t slots) {
            align256((size_t)(slots * n) * 4) + align256((size_t)slots * nwords(n) * 4);
 }
 
-kad_status scratch_for_device(int dev, unsigned char **out) {
-    if (dev < 0 || dev >= kMaxDevices) return KAD_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        // the device is current here: cudaGetSymbolAddress resolves this device's copy
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return KAD_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = (unsigned char *)p;
+// The array's device address on the current device.  In host code the name
+// g_noalloc_scratch is only a host stand-in, never a device address, so every
+// call looks the address up (a host-side query with no stream work) rather than
+// keeping it: a cached address could outlive the context it belongs to.
+kad_status scratch_for_device(unsigned char **out) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return KAD_ERR_CUDA;
     }
-    *out = g_scratch_addr[dev];
+    *out = (unsigned char *)p;
     return KAD_OK;
 }
 
@@ -100,13 +90,8 @@ extern "C" kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row
     if (count == 0) return KAD_OK;
     if ((uint64_t)count * (uint64_t)cap > (uint64_t)1 << 40) return KAD_ERR_INVALID_ARG;
     const cudaStream_t st = (cudaStream_t)stream;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return KAD_ERR_CUDA;
-    }
     unsigned char *base = nullptr;
-    kad_status s = scratch_for_device(dev, &base);
+    kad_status s = scratch_for_device(&base);
     if (s != KAD_OK) return s;
 
     int64_t slots = kMaxSlots;
