@@ -111,7 +111,11 @@ typedef struct {
     uint32_t debug;      /* KAD_DEBUG_* (tests only; results do not depend on it) */
     uint32_t max_epochs; /* > 0: stop after this many epochs even if the stop rule does not hold
                             (a truncated run, for comparisons on large graphs); 0 = no limit */
-    uint32_t reserved;
+    int32_t samples_per_block; /* > 0: the warp-per-sample kernel -- one block of 1024 threads per SM,
+                                  this many of its 32 warps (at most 32) each computing its own
+                                  samples, all of them expanding large rounds for each other through
+                                  a job board in shared memory; 0 = the library's choice of kernel.
+                                  block_threads / blocks_per_sm then do not apply */
 } kad_options;
 
 #define KAD_RUN_TIMING 1u      /* fill kad_result.t_* with CUDA-event times of each phase */
@@ -137,6 +141,8 @@ typedef struct {
 #define KAD_DEBUG_BITMAP 32u      /* filter label reads through the bitmap whatever the degree */
 #define KAD_DEBUG_COARSE_BITMAP 64u /* one bitmap bit per 8 vertices (the default only when the slots'
                                        exact bitmaps would exceed 32 MB) */
+#define KAD_DEBUG_NO_PROBE 256u  /* claim new vertices from a large round's first scan (no probe scan for
+                                    the meeting first); results do not depend on it */
 #define KAD_DEBUG_NO_MEXT 128u   /* record at most mcap meeting-set members (in shared memory);
                                     larger sets are re-collected from the other side's frontier */
 
@@ -189,6 +195,12 @@ typedef struct {
        (calibration + adaptive) handed out when the stop was decided */
     double t_dev_calib_ms, t_dev_first_close_ms, t_dev_stop_ms, t_dev_end_ms;
     uint64_t issued_at_stop;
+    /* the warp-per-sample kernel's sampling contexts per block (0: the block-per-sample kernel ran) */
+    int32_t samples_per_block_used;
+    int32_t reserved_;
+    /* of phase_cycles' BFS stage: cycles in expansion passes, and in round closes
+       (the rest is pairwise tests and loading frontiers) */
+    uint64_t bfs_split_cycles[2];
 } kad_result;
 
 /*

@@ -547,12 +547,22 @@ struct LaunchCfg {
     int threads;
     int per_sm;      // resident blocks per SM the kernel variant is compiled for
     size_t dyn_smem; // bytes of dynamic shared memory (the slot bitmap) or 0
+    int warp = 0;    // 1: the warp-per-sample kernel (1024 threads, one block per SM)
+    int nctx = 0;    // its sampling contexts (owner warps) per block
 };
 
 // Threads per block and blocks per SM.  Unknown combinations fall back to the
 // variant with the same block size and the default occupancy.
 LaunchCfg resolve_cfg(const kad_options &o) {
     LaunchCfg c;
+    if (o.samples_per_block > 0) {
+        c.threads = 1024;
+        c.per_sm = 1;
+        c.dyn_smem = 0;
+        c.warp = 1;
+        c.nctx = o.samples_per_block < 32 ? o.samples_per_block : 32;
+        return c;
+    }
     c.threads = (o.block_threads == 128 || o.block_threads == 256 || o.block_threads == 1024) ? o.block_threads : 512;
     const int def = (c.threads == 128) ? 4 : (c.threads == 256) ? 2 : (c.threads == 512) ? 2 : 1;
     c.per_sm = (o.blocks_per_sm > 0 && kad_sample_variant_exists(c.threads, o.blocks_per_sm)) ? o.blocks_per_sm : def;
@@ -565,7 +575,7 @@ LaunchCfg resolve_cfg(const kad_options &o) {
 // are short: C3 grid 68 ms, C4 hyperbolic 29.6 against 31.7 ms), else 512 x 2
 // (R-MAT's dense hub rows want wide blocks: C2 3.2 ms against 4.9 ms).
 LaunchCfg default_cfg(const kad_graph *g, const kad_options &o) {
-    if (o.block_threads != 0 || o.blocks_per_sm != 0) return resolve_cfg(o);
+    if (o.block_threads != 0 || o.blocks_per_sm != 0 || o.samples_per_block > 0) return resolve_cfg(o);
     const bool sparse = g->gd.m <= 32 * (int64_t)g->gd.n;
     kad_options d = o;
     d.block_threads = sparse ? 256 : 512;
@@ -589,6 +599,7 @@ void choose_bitmap_home(LaunchCfg &c, int32_t n, int dev) {
 // Number of sampling slots: all resident blocks, capped by a share of free memory.
 int resolve_slots(kad_graph *g, const Workspace &w, const kad_options &o, const LaunchCfg &cfg) {
     int slots = o.slots;
+    if (slots <= 0 && cfg.warp) slots = device_sms(g->device) * cfg.nctx;
     if (slots <= 0) {
         const int per_sm = blocks_per_sm_cached(g->device, cfg.threads, cfg.per_sm, cfg.dyn_smem);
         slots = device_sms(g->device) * (per_sm > 0 ? per_sm : 1);
@@ -618,6 +629,7 @@ void fill_defaults(kad_options *o) {
     o->block_threads = 0;
     o->blocks_per_sm = 0;
     o->flags = 0;
+    o->samples_per_block = 0;
 }
 
 __global__ void k_set_ctl(KadCtl *c, unsigned long long next) { c->next = next; }
@@ -632,6 +644,20 @@ double now_ms() {
     struct timespec t;
     clock_gettime(CLOCK_MONOTONIC, &t);
     return (double)t.tv_sec * 1e3 + (double)t.tv_nsec * 1e-6;
+}
+
+// The warp-per-sample kernel's shape for `slots` sampling slots: K contexts in
+// each of nb blocks (at most one per SM), nb * K <= slots; fewer contexts per
+// block rather than fewer blocks when slots are scarce.
+void warp_geometry(const kad_graph *g, const LaunchCfg &cfg, int slots, int *K_out, int *nb_out) {
+    const int sms = device_sms(g->device);
+    int K = cfg.nctx > 0 ? cfg.nctx : 1;
+    if (K > slots / sms) K = slots / sms > 0 ? slots / sms : 1;
+    int nb = slots / K;
+    if (nb > sms) nb = sms;
+    if (nb < 1) nb = 1;
+    *K_out = K;
+    *nb_out = nb;
 }
 
 kad_status launch_phase(kad_graph *g, Workspace &w, const SampleArgs &a, int blocks, const LaunchCfg &cfg,
@@ -660,7 +686,35 @@ kad_status launch_phase(kad_graph *g, Workspace &w, const SampleArgs &a, int blo
     b.mext_id = ext ? w.mext_id : nullptr;
     b.mext_w = ext ? w.mext_w : nullptr;
     b.mext = ext ? kMext : 0;
-    e = kad_launch_sample(b, blocks, cfg.threads, cfg.per_sm, cfg.dyn_smem, st);
+    if (cfg.warp) {
+        // `blocks` is the number of sampling slots: nctx contexts in each of up to
+        // one block per SM (fewer contexts per block when slots are scarce)
+        int K = 0, nb = 0;
+        warp_geometry(g, cfg, blocks, &K, &nb);
+        b.nctx = K;
+        // every context's bitmap of labelled vertices in shared memory, one bit
+        // per 2^shift consecutive vertices, as fine as the space allows
+        int per_block_max = 0;
+        cudaDeviceGetAttribute(&per_block_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
+        const size_t stat = kad_wsample_static_smem();
+        const size_t avail = (size_t)per_block_max > stat + 1024 ? (size_t)per_block_max - stat - 1024 : 0;
+        const size_t per_ctx = avail / 4 / (size_t)K;
+        const int n = g->gd.n;
+        int shift = 0;
+        while (shift < 30 && (size_t)((((n - 1) >> shift) >> 5) + 1) > per_ctx) shift++;
+        b.bits_shift = shift;
+        b.nw = (int32_t)((((n - 1) >> shift) >> 5) + 1);
+        if ((a.debug & KAD_DEBUG_COARSE_BITMAP) && shift < 3) {
+            b.bits_shift = 3;
+            b.nw = (int32_t)((((n - 1) >> 3) >> 5) + 1);
+        }
+        b.bits_smem = 1;
+        const size_t dyn = b.no_bits ? 0 : (size_t)K * (size_t)b.nw * 4;
+        if ((size_t)nb * K > (size_t)blocks) return KAD_ERR_INTERNAL; // cannot happen
+        e = kad_launch_wsample(b, nb, dyn, st);
+    } else {
+        e = kad_launch_sample(b, blocks, cfg.threads, cfg.per_sm, cfg.dyn_smem, st);
+    }
     if (e == cudaSuccess && w.ev_launch) e = cudaEventRecord(w.ev_launch, st);
     if (e != cudaSuccess) return fail(g, e);
     return KAD_OK;
@@ -694,7 +748,7 @@ kad_status read_ctl(kad_graph *g, Workspace &w, KadCtl *h, cudaStream_t st) {
     if (e != cudaSuccess) return fail(g, e);
     if (h->err) {
         w.dirty = true;
-        return KAD_ERR_INTERNAL;
+        return (h->err == KAD_DERR_WAIT) ? KAD_ERR_TIMEOUT : KAD_ERR_INTERNAL;
     }
     return KAD_OK;
 }
@@ -960,10 +1014,19 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
     out->tau_star = ts;
     for (int i = 0; i < 6; i++) out->work[i] = work[i];
     for (int i = 0; i < 6; i++) out->phase_cycles[i] = work[8 + i];
+    out->bfs_split_cycles[0] = work[14];
+    out->bfs_split_cycles[1] = work[15];
     out->ads_launches = launches;
     out->slots_used = slots;
     out->block_threads_used = cfg.threads;
     out->blocks_per_sm_used = cfg.per_sm;
+    out->samples_per_block_used = 0;
+    if (cfg.warp) {
+        int K = 0, nb = 0;
+        warp_geometry(g, cfg, slots, &K, &nb);
+        out->samples_per_block_used = K;
+        out->slots_used = K * nb;
+    }
     // k_hist_init, then k_set_ctl + k_sample per launch, and k_finalize if b~ was wanted
     out->kernel_launches = 1u + 2u * launches + (bc_dst ? 1u : 0u);
     if (ev.on) {

@@ -38,6 +38,7 @@
 #define KAD_DERR_SELECT 4    // meeting draw found no vertex
 #define KAD_DERR_LEVEL 5     // level overflow
 #define KAD_DERR_FRONTIER 6  // list overflow
+#define KAD_DERR_WAIT 7      // a bounded wait of the warp-per-sample kernel ran out
 
 // Control block of one adaptive run (device memory).
 struct KadCtl {
@@ -100,6 +101,7 @@ struct SampleArgs {
     unsigned long long i0, i1;
     int mode;
     int mcap;
+    int nctx; // warp-per-sample kernel: sampling contexts (owner warps) per block
     uint32_t debug; // KAD_DEBUG_*
     // outputs (RING, RECORD)
     int32_t *paths;
@@ -135,7 +137,8 @@ struct SampleArgs {
     unsigned long long omega;
     unsigned long long k_end; // epochs of this launch end before k_end
     unsigned long long max_epochs; // forced stop after this many epochs (truncated runs); 0 = none
-    // work counters [0..5], samples [6], SM cycles per phase [8..13] (KAD_WORK_WORDS)
+    // work counters [0..5], samples [6], SM cycles per phase [8..13], and of the BFS
+    // phase: expansion passes [14] and round closes [15] (KAD_WORK_WORDS)
     unsigned long long *work;
 };
 
@@ -159,10 +162,11 @@ __device__ __forceinline__ void kad_set_err(KadCtl *ctl, int code) {
 }
 
 // f and g of Appendix B with a fixed operation order and correctly rounded
-// operations only (no contraction), so that host and device agree bit for bit:
+// operations only (no contraction), so that host and device agree bit for bit
+// (out of line: one copy of its divisions and square root per kernel):
 //   T = tau, W = omega, b = c/T, q = W/T, a = 1/3 -+ q, x = ((2b) W)/L,
 //   f|g = (L/T) (a + sqrt(a*a + x)).
-__device__ __forceinline__ double kad_fg_dev(unsigned long long c, double L, unsigned long long tau,
+static __device__ __noinline__ double kad_fg_dev(unsigned long long c, double L, unsigned long long tau,
                                              unsigned long long omega, bool upper) {
     double T = (double)tau, W = (double)omega;
     double b = __ddiv_rn((double)c, T);
@@ -179,6 +183,11 @@ cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, int 
 bool kad_sample_variant_exists(int threads, int per_sm);
 size_t kad_sample_static_smem(int threads, int per_sm);
 int kad_sample_max_blocks_per_sm(int threads, int per_sm, size_t dyn_smem);
+// the warp-per-sample kernel (kad_wsample.cu): 1024 threads, one block per SM,
+// a.nctx contexts per block, dyn_smem = a.nctx x a.nw words of bitmap
+cudaError_t kad_launch_wsample(const SampleArgs &a, int blocks, size_t dyn_smem, cudaStream_t st);
+size_t kad_wsample_static_smem();
+int kad_wsample_max_blocks_per_sm(size_t dyn_smem);
 cudaError_t kad_launch_finalize(const uint32_t *cnt, int32_t n, unsigned long long tau, double *bc, cudaStream_t st);
 cudaError_t kad_launch_fg(const uint32_t *counts, const uint32_t *c0, const double *ltab, int32_t n,
                           unsigned long long tau, unsigned long long omega, double *f, double *g, cudaStream_t st);

@@ -39,12 +39,11 @@
 #include <stdint.h>
 #include <string.h>
 
-#include "kad_internal.cuh"
+#include "kad_device.cuh"
 
-#define FULL_MASK 0xffffffffu
 #define KAD_MCAP_MAX 256
 #define KAD_ITEMS 4     // arcs per thread per expansion pass
-#define KAD_MAXLV 62    // levels whose list ranges are kept for the trace-back
+#define KAD_PITEMS 8    // arcs per thread per probe pass
 #define KAD_LCAP 64     // largest predecessor level searched from its list
 #define KAD_DEG_SCAN 64 // adjacency lists up to this length are always scanned
 #define KAD_PAIR_MIN_ARCS 1024 // rounds with fewer arcs always expand by scanning
@@ -55,89 +54,6 @@
 
 namespace {
 
-// atomic add with release semantics at GPU scope: every write of this thread
-// before it is visible to whoever observes the new value
-__device__ __forceinline__ unsigned int atom_add_release(unsigned int *p, unsigned int v) {
-    unsigned int old;
-    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-// ---------------------------------------------------------------- Philox
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011).
-__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; r++) {
-        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
-        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
-        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-        c[0] = n0;
-        c[1] = lo1;
-        c[2] = n2;
-        c[3] = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-}
-
-// The random stream of one sample; used by a single thread.
-struct Stream {
-    uint32_t k0, k1, dom, blk;
-    unsigned long long idx, w0, w1;
-    int pos;
-
-    __device__ void init(uint32_t key0, uint32_t key1, unsigned long long index, uint32_t domain) {
-        k0 = key0;
-        k1 = key1;
-        idx = index;
-        dom = domain;
-        blk = 0;
-        pos = 2;
-    }
-    __device__ unsigned long long next() {
-        if (pos == 2) {
-            uint32_t c[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), blk, dom};
-            philox10(c, k0, k1);
-            w0 = (unsigned long long)c[0] | ((unsigned long long)c[1] << 32);
-            w1 = (unsigned long long)c[2] | ((unsigned long long)c[3] << 32);
-            blk++;
-            pos = 0;
-        }
-        return (pos++ == 0) ? w0 : w1;
-    }
-    // Uniform in [0, m), m >= 1: Lemire's multiply-and-reject.  The rejection
-    // loop is bounded; 64 rejections in a row have probability below 2^-64.
-    __device__ unsigned long long uniform(unsigned long long m, KadCtl *ctl) {
-        unsigned long long x = next();
-        unsigned long long lo = x * m, hi = __umul64hi(x, m);
-        if (lo < m) {
-            const unsigned long long th = (0ull - m) % m;
-            int guard = 0;
-            while (lo < th) {
-                if (++guard > 64) {
-                    kad_set_err(ctl, KAD_DERR_REJECT);
-                    break;
-                }
-                x = next();
-                lo = x * m;
-                hi = __umul64hi(x, m);
-            }
-        }
-        return hi;
-    }
-};
 
 // ---------------------------------------------------------------- block helpers
 template <int BLOCK>
@@ -242,21 +158,6 @@ __device__ __forceinline__ unsigned long long block_sat_sum(unsigned long long v
     return r;
 }
 
-__device__ __forceinline__ unsigned long long warp_incl_sat_scan(unsigned long long x) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(FULL_MASK, x, o);
-        if (lane >= o) x = kad_sat_add(y, x);
-    }
-    return x;
-}
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL_MASK, x, o);
-    return x;
-}
 
 // The labelled-vertex bitmap of a slot lives in the block's dynamic shared
 // memory when it fits (every check then costs a shared-memory read), else in
@@ -281,47 +182,6 @@ __device__ __forceinline__ void bits_clear_word(bool sh, uint32_t *g, int w) {
         g[w] = 0u;
 }
 
-// Per vertex and slot one 16-byte record: the label (word 0), an unused word,
-// and the path count sigma (words 2-3), so that a label and its count come in
-// one load and one 32-byte sector.
-__device__ __forceinline__ uint32_t *lab_at(uint32_t *vs, int v) { return vs + 4 * (size_t)v; }
-__device__ __forceinline__ const uint32_t *lab_at(const uint32_t *vs, int v) { return vs + 4 * (size_t)v; }
-__device__ __forceinline__ unsigned long long *sig_at(uint32_t *vs, int v) {
-    return (unsigned long long *)(vs + 4 * (size_t)v + 2);
-}
-__device__ __forceinline__ const unsigned long long *sig_at(const uint32_t *vs, int v) {
-    return (const unsigned long long *)(vs + 4 * (size_t)v + 2);
-}
-// label and sigma of v, read through L2 in one 16-byte load
-__device__ __forceinline__ void ld_vs(const uint32_t *vs, int v, uint32_t &lab, unsigned long long &sig) {
-    const uint4 x = __ldcg((const uint4 *)(vs + 4 * (size_t)v));
-    lab = x.x;
-    sig = (unsigned long long)x.z | ((unsigned long long)x.w << 32);
-}
-// the path count to use: saturated when the label says it wrapped
-__device__ __forceinline__ unsigned long long sig_val(uint32_t lab, unsigned long long sig) {
-    return (lab & KAD_OVF) ? KAD_U64MAX : sig;
-}
-
-// Physical list position of the j-th vertex labelled on side z: the s side
-// fills the slot's list from the front, the t side from the back.
-__device__ __forceinline__ int phys(int z, int j, int n) { return z ? (n - 1 - j) : j; }
-
-// Write one interior vertex (at distance j from s, 1 <= j <= D-1).  A null row
-// means a calibration sample: count v and move it one histogram bin up.
-__device__ __forceinline__ void emit(const SampleArgs &a, int32_t *row, int D, int j, int v) {
-    if (j < 1 || j > D - 1) return;
-    if (!row) {
-        const unsigned int c = atomicAdd(a.c0w + v, 1u);
-        atomicSub(a.hist + c, 1u);
-        atomicAdd(a.hist + c + 1, 1u);
-    } else {
-        if (j - 1 < a.cap)
-            row[j - 1] = v;
-        else
-            kad_set_err(a.ctl, KAD_DERR_CAP);
-    }
-}
 
 // ---------------------------------------------------------------- trace-back
 // One trace-back step at `cur` (on side z, distance d): among the neighbours p
@@ -372,17 +232,28 @@ __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *
                 ek[k] = __ldg(a.rp + pp[k] + 1);
             }
         }
-#pragma unroll
+        // the running sums item by item (a loop, so that the scan exists once)
+#pragma unroll 1
         for (int k = 0; k < 4; k++) {
-            const unsigned long long incl = warp_incl_sat_scan(wk[k]);
+            unsigned long long wkk = wk[0];
+            int ppk = pp[0], rkk = rk[0], ekk = ek[0];
+#pragma unroll
+            for (int q = 1; q < 4; q++)
+                if (k == q) {
+                    wkk = wk[q];
+                    ppk = pp[q];
+                    rkk = rk[q];
+                    ekk = ek[q];
+                }
+            const unsigned long long incl = warp_incl_sat_scan(wkk);
             const unsigned long long cum = kad_sat_add(carry, incl);
-            const unsigned hit = __ballot_sync(FULL_MASK, pp[k] >= 0 && cum > r);
+            const unsigned hit = __ballot_sync(FULL_MASK, ppk >= 0 && cum > r);
             if (hit) {
                 const int fl = __ffs(hit) - 1;
-                p_sel = __shfl_sync(FULL_MASK, pp[k], fl);
-                s_sel = __shfl_sync(FULL_MASK, wk[k], fl);
-                rs_sel = __shfl_sync(FULL_MASK, rk[k], fl);
-                re_sel = __shfl_sync(FULL_MASK, ek[k], fl);
+                p_sel = __shfl_sync(FULL_MASK, ppk, fl);
+                s_sel = __shfl_sync(FULL_MASK, wkk, fl);
+                rs_sel = __shfl_sync(FULL_MASK, rkk, fl);
+                re_sel = __shfl_sync(FULL_MASK, ekk, fl);
                 if (lane == 0) w_trace += (unsigned long long)(base + 32 * k + fl - rsC + 1);
                 return;
             }
@@ -500,6 +371,7 @@ __device__ __forceinline__ void team_from_level(const SampleArgs &a, Smem<BLOCK>
         unsigned long long ex[2] = {0ull, 0ull};
 #pragma unroll
         for (int slot = 0; slot < 2; slot++) {
+#pragma unroll 4
             for (int qq = 0; qq < 32; qq++) {
                 const int pq = __shfl_sync(FULL_MASK, pc[slot], qq);
                 const unsigned long long wq = __shfl_sync(FULL_MASK, wc[slot], qq);
@@ -716,6 +588,7 @@ struct ExpandCtx {
     bool bsh, watch;
     bool nobits; // no labelled-vertex bitmap: labels are read directly
     int gs;      // bitmap group shift: one bit per 2^gs vertices
+    bool probe;  // look for arcs into the other side's frontier only (no claims)
 };
 
 // Expand the arcs first + k*stride (k < KAD_ITEMS) below `total` of the chunk.
@@ -798,7 +671,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
         prev[k] = 0;
         const int v = vv[k];
         if (fresh[k]) {
-            if (meeting_seen) continue;
+            if (meeting_seen || c.probe) continue;
             old[k] = atomicCAS(lab_at(c.label, v), 0u, c.keyNext);
             kind[k] = 1;
             prev[k] = atomicAdd(sig_at(c.label, v), sm.sig[ix[k]]);
@@ -808,17 +681,39 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
                 kind[k] = 1;
                 prev[k] = atomicAdd(sig_at(c.label, v), sm.sig[ix[k]]);
             } else if ((lv & KAD_SIDE) != c.sideX) {
-                // v is on the other side's frontier: the searches meet.  The arc
-                // that first marks v records it in M.
-                kind[k] = 2;
-                if (!(lv & KAD_INM) && !(atomicOr(lab_at(c.label, v), KAD_INM) & KAD_INM)) {
-                    const int slot = atomicAdd(&sm.mcount, 1);
-                    if (slot < c.mcap) sm.m_id[slot] = v;
-                    else if (slot - c.mcap < c.mext) c.mext_id[slot - c.mcap] = v;
-                }
-                prev[k] = atomicAdd(c.sigma2 + v, sm.sig[ix[k]]);
+                kind[k] = 2; // handled below
             }
         }
+    }
+    // Arcs into the other side's frontier: the searches meet.  The arc that
+    // first marks its head records it in M.  One at a time (a few per sample),
+    // so that this code exists once.
+    unsigned m2 = 0;
+#pragma unroll
+    for (int k = 0; k < KAD_ITEMS; k++)
+        if (kind[k] == 2) m2 |= 1u << k;
+    const bool any_m = m2 != 0;
+    pred_m += (unsigned long long)__popc(m2);
+    while (m2) {
+        const int k = __ffs(m2) - 1;
+        m2 &= m2 - 1;
+        int v = vv[0], ixk = ix[0];
+        uint32_t lv = ll[0];
+#pragma unroll
+        for (int q = 1; q < KAD_ITEMS; q++)
+            if (k == q) {
+                v = vv[q];
+                ixk = ix[q];
+                lv = ll[q];
+            }
+        if (!(lv & KAD_INM) && !(atomicOr(lab_at(c.label, v), KAD_INM) & KAD_INM)) {
+            const int slot = atomicAdd(&sm.mcount, 1);
+            if (slot < c.mcap) sm.m_id[slot] = v;
+            else if (slot - c.mcap < c.mext) c.mext_id[slot - c.mcap] = v;
+        }
+        const unsigned long long add = sm.sig[ixk];
+        const unsigned long long pv = atomicAdd(c.sigma2 + v, add);
+        if (pv + add < pv) atomicOr(lab_at(c.label, v), KAD_OVF2);
     }
     int rs0[KAD_ITEMS], rs1[KAD_ITEMS];
 #pragma unroll
@@ -830,7 +725,6 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
         }
     }
     bool claimed[KAD_ITEMS];
-    bool any_m = false;
 #pragma unroll
     for (int k = 0; k < KAD_ITEMS; k++) {
         claimed[k] = fresh[k] && kind[k] == 1 && old[k] == 0u;
@@ -840,10 +734,6 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
         if (kind[k] == 1) {
             pred_next++;
             if (prev[k] + sm.sig[ix[k]] < prev[k]) atomicOr(lab_at(c.label, vv[k]), KAD_OVF);
-        } else if (kind[k] == 2) {
-            pred_m++;
-            any_m = true;
-            if (prev[k] + sm.sig[ix[k]] < prev[k]) atomicOr(lab_at(c.label, vv[k]), KAD_OVF2);
         }
     }
     if (any_m) sm.met[c.rb] = 1;
@@ -878,11 +768,256 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
     return false;
 }
 
+// The probe scan of a large round: arcs first + k*stride (k < KAD_PITEMS) below
+// `total`.  Only an arc into the other side's frontier matters here (it marks
+// its head as a member of M, recording it on first mark, and pushes sigma_X
+// into sigma2); nothing is claimed, so a pass carries twice the arcs of a
+// claiming one.  Returns true (for the whole warp) when the run has stopped.
+template <int BLOCK>
+__device__ __forceinline__ bool probe_items(const SampleArgs &a, Smem<BLOCK> &sm, const ExpandCtx &c, int first,
+                                            int stride, int total, unsigned long long &pred_m) {
+    const int lane = threadIdx.x & 31;
+    int stop_now = 0;
+    if (lane == 0 && c.watch) stop_now = *(volatile int *)&a.ctl->stop;
+    int vv[KAD_PITEMS], ix[KAD_PITEMS];
+#pragma unroll
+    for (int k = 0; k < KAD_PITEMS; k++) {
+        const int e = first + k * stride;
+        vv[k] = -1;
+        ix[k] = 0;
+        if (e < total) {
+            int lo = 0, hi = c.cnt - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sm.off[mid] <= e)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            vv[k] = __ldg(a.col + sm.rs[lo] + (e - sm.off[lo]));
+            ix[k] = lo;
+        }
+    }
+    uint32_t ll[KAD_PITEMS];
+    if (c.nobits) {
+#pragma unroll
+        for (int k = 0; k < KAD_PITEMS; k++) ll[k] = (vv[k] >= 0) ? kad_ld_u32(lab_at(c.label, vv[k])) : 0u;
+    } else {
+#pragma unroll
+        for (int k = 0; k < KAD_PITEMS; k++) ll[k] = (vv[k] >= 0) ? bits_ld(c.bsh, c.bits, (vv[k] >> c.gs) >> 5) : 0u;
+#pragma unroll
+        for (int k = 0; k < KAD_PITEMS; k++)
+            ll[k] = (vv[k] >= 0 && ((ll[k] >> ((vv[k] >> c.gs) & 31)) & 1u)) ? kad_ld_u32(lab_at(c.label, vv[k])) : 0u;
+    }
+    if (__shfl_sync(FULL_MASK, stop_now, 0)) return true;
+    // arcs into the other side's frontier (a few per sample), handled one at a
+    // time so that the code below exists once
+    unsigned mk = 0;
+#pragma unroll
+    for (int k = 0; k < KAD_PITEMS; k++)
+        if (ll[k] != 0u && (ll[k] & KAD_SIDE) != c.sideX) mk |= 1u << k;
+    const bool any_m = mk != 0;
+    while (mk) {
+        const int k = __ffs(mk) - 1;
+        mk &= mk - 1;
+        int v = vv[0], ixk = ix[0];
+        uint32_t lv = ll[0];
+#pragma unroll
+        for (int q = 1; q < KAD_PITEMS; q++)
+            if (k == q) {
+                v = vv[q];
+                ixk = ix[q];
+                lv = ll[q];
+            }
+        if (!(lv & KAD_INM) && !(atomicOr(lab_at(c.label, v), KAD_INM) & KAD_INM)) {
+            const int slot = atomicAdd(&sm.mcount, 1);
+            if (slot < c.mcap)
+                sm.m_id[slot] = v;
+            else if (slot - c.mcap < c.mext)
+                c.mext_id[slot - c.mcap] = v;
+        }
+        const unsigned long long add = sm.sig[ixk];
+        const unsigned long long prev = atomicAdd(c.sigma2 + v, add);
+        if (prev + add < prev) atomicOr(lab_at(c.label, v), KAD_OVF2);
+        pred_m++;
+    }
+    if (any_m) sm.met[c.rb] = 1;
+    return false;
+}
+
+// Meeting draw for a large M (out of line: a minority of samples): select by id
+// digits, 4 bits per pass from the top, with exact 128-bit bin sums, over the
+// recorded members when all were recorded, else over the other side's
+// frontier.  Sets sm.mid.  Called by every thread of the block.
+template <int BLOCK>
+__device__ __noinline__ void select_by_digits(const SampleArgs &a, Smem<BLOCK> &sm, bool from_rec, int mc, int mcap,
+                                              const int32_t *mext_id, const unsigned long long *mext_w,
+                                              const int32_t *list, const uint32_t *label,
+                                              const unsigned long long *sigma2, int n, int Y, int yb, int ye,
+                                              unsigned long long r) {
+    const int tid = threadIdx.x;
+    const int nb = 32 - __clz(max(n - 1, 1));
+    const int top = ((nb + 3) / 4) * 4;
+    unsigned int prefix = 0;
+    unsigned long long P = 0;
+    for (int shift = top - 4; shift >= 0; shift -= 4) {
+        if (tid < 16) {
+            sm.bin_lo[tid] = 0;
+            sm.bin_hi[tid] = 0;
+        }
+        __syncthreads();
+        if (from_rec) {
+            for (int i = tid; i < mc; i += BLOCK) {
+                const int v = (i < mcap) ? sm.m_id[i] : __ldcg(mext_id + (i - mcap));
+                if (((unsigned long long)(unsigned)v >> (shift + 4)) !=
+                    ((unsigned long long)prefix >> (shift + 4)))
+                    continue;
+                const unsigned long long w = (i < mcap) ? sm.m_w[i] : __ldcg(mext_w + (i - mcap));
+                const int b = ((unsigned)v >> shift) & 15;
+                const unsigned long long old = atomicAdd(&sm.bin_lo[b], w);
+                if (old + w < old) atomicAdd(&sm.bin_hi[b], 1ull);
+            }
+        } else
+        for (int j = yb + tid; j < ye; j += BLOCK) {
+            const int v = __ldcg(list + phys(Y, j, n));
+            const uint32_t lv = kad_ld_u32(lab_at(label, v));
+            if (!(lv & KAD_INM)) continue;
+            if (((unsigned long long)(unsigned)v >> (shift + 4)) !=
+                ((unsigned long long)prefix >> (shift + 4)))
+                continue;
+            const unsigned long long sx = (lv & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + v);
+            const unsigned long long sy = (lv & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sig_at(label, v));
+            const unsigned long long w = kad_sat_mul(sx, sy);
+            const int b = ((unsigned)v >> shift) & 15;
+            const unsigned long long old = atomicAdd(&sm.bin_lo[b], w);
+            if (old + w < old) atomicAdd(&sm.bin_hi[b], 1ull);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long cum = P;
+            int chosen = -1;
+            for (int b = 0; b < 16; b++) {
+                const unsigned long long bw = sm.bin_hi[b] ? KAD_U64MAX : sm.bin_lo[b];
+                const unsigned long long nc = kad_sat_add(cum, bw);
+                if (nc > r) {
+                    chosen = b;
+                    break;
+                }
+                cum = nc;
+            }
+            if (chosen < 0) {
+                kad_set_err(a.ctl, KAD_DERR_SELECT);
+                chosen = 0;
+            }
+            sm.P = cum;
+            sm.prefix = prefix | ((unsigned)chosen << shift);
+        }
+        __syncthreads();
+        P = sm.P;
+        prefix = sm.prefix;
+    }
+    if (tid == 0) sm.mid = (int)prefix;
+}
+
+// The block finishing the last calibration sample copies the histogram of c0
+// to the mapped host page and raises the flag the host waits for (out of line:
+// once per run).
+template <int BLOCK>
+__device__ __noinline__ void publish_histogram(const SampleArgs &a) {
+    const int tid = threadIdx.x;
+    for (int c = tid; c < a.nclass; c += BLOCK) a.hpage->hist[c] = __ldcg(a.hist + c);
+    __threadfence_system();
+    __syncthreads();
+    if (tid == 0) {
+        a.ctl->t_calib = global_ns();
+        *(volatile int *)&a.hpage->calib_flag = 1;
+        __threadfence_system();
+    }
+}
+
+// The pairwise test when there are more pairs than half the block's threads (out
+// of line: rare): four pairs per thread and step, their binary searches
+// interleaved.  Called by every thread of the block.
+template <int BLOCK>
+__device__ __noinline__ void pairs_many(const SampleArgs &a, Smem<BLOCK> &sm, const int32_t *list, uint32_t *label,
+                                        unsigned long long *sigma2, int32_t *mext_id, int mcap, int mext, int Y,
+                                        int yb, int fx, long long np, int n, int rb, unsigned long long &pred_m) {
+    const int tid = threadIdx.x;
+    // four pairs per thread and step, their binary searches interleaved
+    for (long long p0 = tid; p0 < np; p0 += 4ll * BLOCK) {
+        int pi[4], pw[4], lo[4], hi[4], key[4];
+        bool hit[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const long long p = p0 + (long long)k * BLOCK;
+            pi[k] = -1;
+            pw[k] = -1;
+            hit[k] = false;
+            lo[k] = hi[k] = key[k] = 0;
+            if (p < np) {
+                pi[k] = (int)(p % fx);
+                pw[k] = __ldcg(list + phys(Y, yb + (int)(p / fx), n));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (pw[k] < 0) continue;
+            const int rsW = __ldg(a.rp + pw[k]), reW = __ldg(a.rp + pw[k] + 1);
+            const int rsU = sm.rs[pi[k]], reU = sm.off[pi[k]];
+            if (reU - rsU <= reW - rsW) { // search w in the row of u
+                lo[k] = rsU;
+                hi[k] = reU;
+                key[k] = pw[k];
+            } else { // search u in the row of w
+                lo[k] = rsW;
+                hi[k] = reW;
+                key[k] = sm.uid[pi[k]];
+            }
+        }
+        for (int step = 0; step < 32; step++) {
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (hit[k] || lo[k] >= hi[k]) continue;
+                any = true;
+                const int mid = (lo[k] + hi[k]) >> 1;
+                const int v = __ldg(a.col + mid);
+                if (v < key[k])
+                    lo[k] = mid + 1;
+                else if (v > key[k])
+                    hi[k] = mid;
+                else
+                    hit[k] = true;
+            }
+            if (!any) break;
+        }
+        unsigned long long prev[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            prev[k] = 0;
+            if (!hit[k]) continue;
+            if (!(atomicOr(lab_at(label, pw[k]), KAD_INM) & KAD_INM)) {
+                const int slot = atomicAdd(&sm.mcount, 1);
+                if (slot < mcap) sm.m_id[slot] = pw[k];
+                else if (slot - mcap < mext) mext_id[slot - mcap] = pw[k];
+            }
+            prev[k] = atomicAdd(sigma2 + pw[k], sm.sig[pi[k]]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (!hit[k]) continue;
+            pred_m++;
+            sm.met[rb] = 1;
+            if (prev[k] + sm.sig[pi[k]] < prev[k]) atomicOr(lab_at(label, pw[k]), KAD_OVF2);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- closer
 // Fold epoch k (sample rows of ring slot k mod R) into the counts, then
 // evaluate the stop rule on the consistent state after k+1 epochs.
 template <int BLOCK>
-__device__ void close_epoch(const SampleArgs &a, Smem<BLOCK> &sm, unsigned long long k) {
+__device__ __noinline__ void close_epoch(const SampleArgs &a, Smem<BLOCK> &sm, unsigned long long k) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const size_t rb = (size_t)(k % a.ring) * a.epoch;
     if (tid == 0) sm.ovf_acc = 0;
@@ -940,18 +1075,12 @@ __device__ void close_epoch(const SampleArgs &a, Smem<BLOCK> &sm, unsigned long 
     __syncthreads();
 }
 
-// Epoch k can be closed once all its samples are written, no stop has been
-// decided, and the host has uploaded the L table (calibration's result).
-__device__ __forceinline__ bool epoch_ready(const SampleArgs &a, unsigned long long k) {
-    return k < a.k_end && *(volatile int *)&a.ctl->stop == 0 && *(volatile int *)&a.ctl->ltab_ready != 0 &&
-           *(volatile uint32_t *)&a.epoch_done[k % a.ring] == a.epoch;
-}
 
 // The closer role: at most one block holds it.  After releasing it the holder
 // looks once more for a complete epoch, so a completion that raced with the
 // release is never lost.  No thread ever waits for another block.
 template <int BLOCK>
-__device__ void run_closer(const SampleArgs &a, Smem<BLOCK> &sm) {
+__device__ __noinline__ void run_closer(const SampleArgs &a, Smem<BLOCK> &sm) {
     bool holding = false;
     if (threadIdx.x == 0) holding = (atomicCAS(&a.ctl->closer, 0, 1) == 0);
     for (;;) {
@@ -1150,78 +1279,98 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 }
                 __syncthreads();
                 const long long np = (long long)fx * (long long)fy;
-                // four pairs per thread and step, their binary searches interleaved
-                for (long long p0 = tid; p0 < np; p0 += 4ll * BLOCK) {
-                    int pi[4], pw[4], lo[4], hi[4], key[4];
-                    bool hit[4];
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        const long long p = p0 + (long long)k * BLOCK;
-                        pi[k] = -1;
-                        pw[k] = -1;
-                        hit[k] = false;
-                        lo[k] = hi[k] = key[k] = 0;
-                        if (p < np) {
-                            pi[k] = (int)(p % fx);
-                            pw[k] = __ldcg(list + phys(Y, yb + (int)(p / fx), n));
+                if (np <= BLOCK / 2) {
+                    // G threads per pair (G * np <= BLOCK): probes at G-1 points split
+                    // the searched row into G parts per step; once at most 4G entries
+                    // are left, the group reads all of them at once
+                    int G = 1;
+                    while (G < 32 && 2 * G * np <= BLOCK) G *= 2;
+                    const int sub = tid & (G - 1);
+                    const long long p = tid / G;
+                    int pi = -1, pw = -1, lo = 0, hi = 0, key = 0;
+                    if (p < np) {
+                        pi = (int)(p % fx);
+                        pw = __ldcg(list + phys(Y, yb + (int)(p / fx), n));
+                        const int rsW = __ldg(a.rp + pw), reW = __ldg(a.rp + pw + 1);
+                        const int rsU = sm.rs[pi], reU = sm.off[pi];
+                        if (reU - rsU <= reW - rsW) {
+                            lo = rsU;
+                            hi = reU;
+                            key = pw;
+                        } else {
+                            lo = rsW;
+                            hi = reW;
+                            key = sm.uid[pi];
                         }
                     }
+                    const int P = (G > 1) ? G - 1 : 1;
+                    const int lgP1 = (G > 1) ? __ffs(G) - 1 : 1; // P + 1 = 2^lgP1
+                    bool done = p >= np || lo >= hi, found = false;
+                    while (__any_sync(FULL_MASK, !done)) {
+                        const int len = hi - lo;
+                        if (!done && len <= 4 * G) {
+                            // every position left, four per thread
 #pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        if (pw[k] < 0) continue;
-                        const int rsW = __ldg(a.rp + pw[k]), reW = __ldg(a.rp + pw[k] + 1);
-                        const int rsU = sm.rs[pi[k]], reU = sm.off[pi[k]];
-                        if (reU - rsU <= reW - rsW) { // search w in the row of u
-                            lo[k] = rsU;
-                            hi[k] = reU;
-                            key[k] = pw[k];
-                        } else { // search u in the row of w
-                            lo[k] = rsW;
-                            hi[k] = reW;
-                            key[k] = sm.uid[pi[k]];
+                            for (int k = 0; k < 4; k++) {
+                                const int q = lo + sub + k * G;
+                                if (q < hi && __ldg(a.col + q) == key) found = true;
+                            }
+                            done = true;
+                        }
+                        int v = 0, q = 0;
+                        const bool probe = !done && sub < P;
+                        if (probe) {
+                            q = lo + (int)(((long long)len * (sub + 1)) >> lgP1);
+                            v = __ldg(a.col + q);
+                        }
+                        int nlo = (probe && v < key) ? q + 1 : -0x7fffffff;
+                        int nhi = (probe && v > key) ? q : 0x7fffffff;
+                        int eq = (probe && v == key) ? 1 : 0;
+                        for (int o = 1; o < G; o <<= 1) {
+                            nlo = max(nlo, __shfl_xor_sync(FULL_MASK, nlo, o));
+                            nhi = min(nhi, __shfl_xor_sync(FULL_MASK, nhi, o));
+                            eq |= __shfl_xor_sync(FULL_MASK, eq, o);
+                        }
+                        if (!done) {
+                            if (eq) {
+                                found = true;
+                                done = true;
+                            } else {
+                                lo = max(lo, nlo);
+                                hi = min(hi, nhi);
+                                if (lo >= hi) done = true;
+                            }
                         }
                     }
-                    for (int step = 0; step < 32; step++) {
-                        bool any = false;
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            if (hit[k] || lo[k] >= hi[k]) continue;
-                            any = true;
-                            const int mid = (lo[k] + hi[k]) >> 1;
-                            const int v = __ldg(a.col + mid);
-                            if (v < key[k])
-                                lo[k] = mid + 1;
-                            else if (v > key[k])
-                                hi[k] = mid;
-                            else
-                                hit[k] = true;
-                        }
-                        if (!any) break;
-                    }
-                    unsigned long long prev[4];
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        prev[k] = 0;
-                        if (!hit[k]) continue;
-                        if (!(atomicOr(lab_at(label, pw[k]), KAD_INM) & KAD_INM)) {
+                    int f = found ? 1 : 0;
+                    for (int o = 1; o < G; o <<= 1) f |= __shfl_xor_sync(FULL_MASK, f, o);
+                    if (f && sub == 0) {
+                        if (!(atomicOr(lab_at(label, pw), KAD_INM) & KAD_INM)) {
                             const int slot = atomicAdd(&sm.mcount, 1);
-                            if (slot < mcap) sm.m_id[slot] = pw[k];
-                            else if (slot - mcap < mext) mext_id[slot - mcap] = pw[k];
+                            if (slot < mcap) sm.m_id[slot] = pw;
+                            else if (slot - mcap < mext) mext_id[slot - mcap] = pw;
                         }
-                        prev[k] = atomicAdd(sigma2 + pw[k], sm.sig[pi[k]]);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        if (!hit[k]) continue;
+                        const unsigned long long prev = atomicAdd(sigma2 + pw, sm.sig[pi]);
                         pred_m++;
                         sm.met[rb] = 1;
-                        if (prev[k] + sm.sig[pi[k]] < prev[k]) atomicOr(lab_at(label, pw[k]), KAD_OVF2);
+                        if (prev + sm.sig[pi] < prev) atomicOr(lab_at(label, pw), KAD_OVF2);
                     }
+                } else {
+                    pairs_many<BLOCK>(a, sm, list, label, sigma2, mext_id, mcap, mext, Y, yb, fx, np, n, rb, pred_m);
                 }
                 __syncthreads();
             }
-            // a meeting found by the pairwise test completes the round
-            const int expand_end = (pairs && sm.met[rb]) ? fb : fe;
+            // A large round is probed first: one scan that only looks for arcs
+            // into the other side's frontier (collecting M and sigma_X on M), and
+            // claims new vertices only if it found none.  Almost all of a large
+            // round's arcs are scanned in the meeting round, where claims are
+            // wasted work; an ordinary large round is scanned twice.
+            const bool probe_first = !(a.debug & KAD_DEBUG_NO_PROBE) && sm.dsum[X] > (unsigned long long)(BLOCK * KAD_ITEMS);
+            // (probe passes carry KAD_PITEMS arcs per thread)
+            for (int ph = probe_first ? 0 : 1; ph < 2; ph++) {
+            // a meeting found by the pairwise test or the probe completes the round
+            if (sm.met[rb] || sm.abort) break;
+            const int expand_end = fe;
             for (int cb = fb; cb < expand_end; cb += BLOCK) {
                 const int cnt = min(BLOCK, fe - cb);
                 int d = 0;
@@ -1275,18 +1424,34 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 ec.nobits = nobits;
                 ec.gs = gs;
                 ec.watch = watch_stop;
-                for (int base = 0; base < total; base += BLOCK * KAD_ITEMS) {
-                    if (expand_items<BLOCK>(a, sm, ec, base + tid, BLOCK, total, pred_next, pred_m)) {
-                        if (lane == 0) sm.abort = 1;
-                        break;
+                ec.probe = ph == 0;
+                long long tp = 0;
+                if (tid == 0) tp = clock64();
+                if (ec.probe) {
+                    for (int base = 0; base < total; base += BLOCK * KAD_PITEMS) {
+                        if (probe_items<BLOCK>(a, sm, ec, base + tid, BLOCK, total, pred_m)) {
+                            if (lane == 0) sm.abort = 1;
+                            break;
+                        }
+                    }
+                } else {
+                    for (int base = 0; base < total; base += BLOCK * KAD_ITEMS) {
+                        if (expand_items<BLOCK>(a, sm, ec, base + tid, BLOCK, total, pred_next, pred_m)) {
+                            if (lane == 0) sm.abort = 1;
+                            break;
+                        }
                     }
                 }
                 __syncthreads();
+                if (tid == 0) sm.acc[14] += (unsigned long long)(clock64() - tp);
                 if (sm.abort) break;
+            }
             }
             // every warp's passes ended at the chunk's barrier: this round's flag is final
             const int met = sm.met[rb];
             w_pred += met ? pred_m : pred_next;
+            long long tc = 0;
+            if (tid == 0) tc = clock64();
             if (tid == 0) {
                 if (sm.abort) {
                     // An expansion pass saw the run's stop: this sample lies beyond
@@ -1313,6 +1478,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 }
             }
             __syncthreads();
+            if (tid == 0) sm.acc[15] += (unsigned long long)(clock64() - tc);
             rnd++;
         }
 
@@ -1419,71 +1585,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     if (i < mc && p == 0 && ex <= r && kad_sat_add(ex, w) > r) sm.mid = id;
                 }
             } else {
-                // Large M: select by id digits, 4 bits per pass from the top,
-                // with exact 128-bit bin sums, over the recorded members when all
-                // were recorded, else over the other side's frontier.
-                const bool from_rec = mc <= mtot;
-                const int nb = 32 - __clz(max(n - 1, 1));
-                const int top = ((nb + 3) / 4) * 4;
-                unsigned int prefix = 0;
-                unsigned long long P = 0;
-                for (int shift = top - 4; shift >= 0; shift -= 4) {
-                    if (tid < 16) {
-                        sm.bin_lo[tid] = 0;
-                        sm.bin_hi[tid] = 0;
-                    }
-                    __syncthreads();
-                    if (from_rec) {
-                        for (int i = tid; i < mc; i += BLOCK) {
-                            const int v = (i < mcap) ? sm.m_id[i] : __ldcg(mext_id + (i - mcap));
-                            if (((unsigned long long)(unsigned)v >> (shift + 4)) !=
-                                ((unsigned long long)prefix >> (shift + 4)))
-                                continue;
-                            const unsigned long long w = (i < mcap) ? sm.m_w[i] : __ldcg(mext_w + (i - mcap));
-                            const int b = ((unsigned)v >> shift) & 15;
-                            const unsigned long long old = atomicAdd(&sm.bin_lo[b], w);
-                            if (old + w < old) atomicAdd(&sm.bin_hi[b], 1ull);
-                        }
-                    } else
-                    for (int j = yb + tid; j < ye; j += BLOCK) {
-                        const int v = __ldcg(list + phys(Y, j, n));
-                        const uint32_t lv = kad_ld_u32(lab_at(label, v));
-                        if (!(lv & KAD_INM)) continue;
-                        if (((unsigned long long)(unsigned)v >> (shift + 4)) !=
-                            ((unsigned long long)prefix >> (shift + 4)))
-                            continue;
-                        const unsigned long long sx = (lv & KAD_OVF2) ? KAD_U64MAX : kad_ld_u64(sigma2 + v);
-                        const unsigned long long sy = (lv & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sig_at(label, v));
-                        const unsigned long long w = kad_sat_mul(sx, sy);
-                        const int b = ((unsigned)v >> shift) & 15;
-                        const unsigned long long old = atomicAdd(&sm.bin_lo[b], w);
-                        if (old + w < old) atomicAdd(&sm.bin_hi[b], 1ull);
-                    }
-                    __syncthreads();
-                    if (tid == 0) {
-                        unsigned long long cum = P;
-                        int chosen = -1;
-                        for (int b = 0; b < 16; b++) {
-                            const unsigned long long bw = sm.bin_hi[b] ? KAD_U64MAX : sm.bin_lo[b];
-                            const unsigned long long nc = kad_sat_add(cum, bw);
-                            if (nc > r) {
-                                chosen = b;
-                                break;
-                            }
-                            cum = nc;
-                        }
-                        if (chosen < 0) {
-                            kad_set_err(a.ctl, KAD_DERR_SELECT);
-                            chosen = 0;
-                        }
-                        sm.P = cum;
-                        sm.prefix = prefix | ((unsigned)chosen << shift);
-                    }
-                    __syncthreads();
-                    P = sm.P;
-                    prefix = sm.prefix;
-                }
-                if (tid == 0) sm.mid = (int)prefix;
+                select_by_digits<BLOCK>(a, sm, mc <= mtot, mc, mcap, mext_id, mext_w, list, label, sigma2, n, Y, yb,
+                                        ye, r);
             }
             __syncthreads();
         }
@@ -1680,16 +1783,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 sm.publish = (done == a.calib_n) ? 1 : 0;
             }
             __syncthreads();
-            if (sm.publish) {
-                for (int c = tid; c < a.nclass; c += BLOCK) a.hpage->hist[c] = __ldcg(a.hist + c);
-                __threadfence_system();
-                __syncthreads();
-                if (tid == 0) {
-                    a.ctl->t_calib = global_ns();
-                    *(volatile int *)&a.hpage->calib_flag = 1;
-                    __threadfence_system();
-                }
-            }
+            if (sm.publish) publish_histogram<BLOCK>(a);
         } else if (a.mode == KAD_MODE_RING) {
             if (tid == 0) {
                 // Publish this sample's path (release); the block completing an

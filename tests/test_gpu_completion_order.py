@@ -49,6 +49,9 @@ CASES = {
     "rmat12_128x8": (lambda: gen.rmat(12, 8, seed=1), 0.03, 12, dict(block_threads=128, blocks_per_sm=8)),
     "rmat12_N250": (lambda: gen.rmat(12, 8, seed=1), 0.04, 5, dict(epoch_size=250)),
     "grid40": (lambda: gen.grid(40, seed=3), 0.05, 3, {}),
+    "rmat12_warp": (lambda: gen.rmat(12, 8, seed=1), 0.03, 11, dict(samples_per_block=32)),
+    "rmat12_warp5": (lambda: gen.rmat(12, 8, seed=1), 0.03, 12, dict(samples_per_block=5)),
+    "grid40_warp": (lambda: gen.grid(40, seed=3), 0.05, 3, dict(samples_per_block=32)),
 }
 
 
@@ -83,14 +86,15 @@ def test_completion_order_counts_exactly_the_listed_samples(kad, name):
         assert not rule_holds(prev, ref["c0"], ref["L"], tau - N, ref["omega"], eps)
 
 
-def test_completion_order_across_launches(kad):
+@pytest.mark.parametrize("opt", [{}, dict(samples_per_block=8)])
+def test_completion_order_across_launches(kad, opt):
     # a two-epoch ring and few slots: the run needs several launches, each
     # issuing only as many samples as the ring has free fold positions
     g = gen.rmat(12, 8, seed=1)
     eps, delta, seed = 0.03, 0.1, 7
     ref = O.kadabra(g, eps, delta, seed)
     with kad.Graph.from_csr(g) as G:
-        r = G.run(eps, delta, seed, flags=kad.KAD_RUN_COMPLETION_ORDER, ring_epochs=2, slots=40)
+        r = G.run(eps, delta, seed, flags=kad.KAD_RUN_COMPLETION_ORDER, ring_epochs=2, slots=40, **opt)
         order = G.run_order(r["tau"]).astype(np.int64)
     tau = r["tau"]
     assert tau % 1000 == 0

@@ -64,25 +64,34 @@ def compare_records(rec, orc):
         assert rec["counters"][k] == orc["counters"][k], k
 
 
+# the two sampling kernels: block per sample, warp per sample
+KERNELS = {"block": {}, "warp": dict(samples_per_block=32)}
+_rmat20_ref = {}
+
+
 @pytest.mark.parametrize("name,count", [("rmat20", 2000), ("grid2048", 400), ("hyp4m", 400)])
-def test_records_at_full_size(kad, oracle_runs, name, count):
+@pytest.mark.parametrize("kernel", sorted(KERNELS))
+def test_records_at_full_size(kad, oracle_runs, name, count, kernel):
     g = workload(name)
     w = gen.WORKLOADS[name]
     with kad.Graph.from_csr(g) as G:
         assert G.vd_bound == O.vd_bound(g)
-        rec = G.sample_records(w["seed"], 5000, count)
-        cal = G.sample_records(w["seed"], 0, count // 2, domain=1)
+        rec = G.sample_records(w["seed"], 5000, count, **KERNELS[kernel])
+        cal = G.sample_records(w["seed"], 0, count // 2, domain=1, **KERNELS[kernel])
     compare_records(rec, O.samples(g, w["seed"], 5000, count))
     compare_records(cal, O.samples(g, w["seed"], 0, count // 2, domain=1))
 
 
-def test_benchmarked_query_end_to_end(kad):
+@pytest.mark.parametrize("kernel", sorted(KERNELS))
+def test_benchmarked_query_end_to_end(kad, kernel):
     name = "rmat20"
     g = workload(name)
     w = gen.WORKLOADS[name]
-    ref = O.kadabra(g, w["eps"], w["delta"], w["seed"])
+    if name not in _rmat20_ref:
+        _rmat20_ref[name] = O.kadabra(g, w["eps"], w["delta"], w["seed"])
+    ref = _rmat20_ref[name]
     with kad.Graph.from_csr(g) as G:
-        r = G.run(w["eps"], w["delta"], w["seed"], c0=True, ltab=True)
+        r = G.run(w["eps"], w["delta"], w["seed"], c0=True, ltab=True, **KERNELS[kernel])
     assert (r["tau"], r["epochs"], r["omega"], r["calib_samples"]) == \
         (ref["tau"], ref["epochs"], ref["omega"], ref["calib_samples"])
     np.testing.assert_array_equal(r["c0"], ref["c0"])
@@ -108,11 +117,12 @@ def test_truncated_run_at_full_size(kad, name):
 
 
 @pytest.mark.parametrize("name", ["grid2048", "hyp4m"])
-def test_run_to_stop_at_full_size(kad, oracle_runs, name):
+@pytest.mark.parametrize("kernel", sorted(KERNELS))
+def test_run_to_stop_at_full_size(kad, oracle_runs, name, kernel):
     g = workload(name)
     w = gen.WORKLOADS[name]
     with kad.Graph.from_csr(g) as G:
-        r = G.run(w["eps"], w["delta"], w["seed"], c0=True, ltab=True)
+        r = G.run(w["eps"], w["delta"], w["seed"], c0=True, ltab=True, **KERNELS[kernel])
     ref = oracle_runs[name].result(timeout=900)
     assert (r["tau"], r["epochs"], r["omega"], r["calib_samples"]) == \
         (ref["tau"], ref["epochs"], ref["omega"], ref["calib_samples"])
