@@ -104,7 +104,7 @@ typedef struct {
     int32_t block_threads; /* threads per sampling block: 128, 256, 512 or 1024 (0 = 512) */
     int32_t blocks_per_sm; /* resident sampling blocks per SM the kernel is built for: 128 threads 4|8,
                               256: 2|4, 512: 1|2, 1024: 1 (0 = 4, 2, 2, 1 respectively).  When both
-                              are 0 the kernel is 256x4 on graphs of average degree at most 32
+                              are 0 the kernel is 256x4 on graphs of average degree at most 8
                               and 512x2 otherwise, or with KAD_RUN_AUTOTUNE the fastest of
                               512x2, 256x4, 256x2, 1024x1 and 128x8 on this graph */
     uint32_t flags;      /* KAD_RUN_* */

@@ -571,12 +571,13 @@ LaunchCfg resolve_cfg(const kad_options &o) {
 }
 
 // The kernel variant when the caller names none: 256 threads x 4 blocks per SM
-// on graphs of average degree up to 32 (more samples in flight pay off when rows
-// are short: C3 grid 68 ms, C4 hyperbolic 29.6 against 31.7 ms), else 512 x 2
-// (R-MAT's dense hub rows want wide blocks: C2 3.2 ms against 4.9 ms).
+// on graphs of average degree up to 8 (more samples in flight pay off when rows
+// are short and searches deep: the 2048^2 grid 69 ms against 105 ms), else
+// 512 x 2 (hub rows want wide blocks: R-MAT scale 20 2.8 ms against 4.1 ms, the
+// 4M-vertex hyperbolic graph 24.9 against 26.2 ms).
 LaunchCfg default_cfg(const kad_graph *g, const kad_options &o) {
     if (o.block_threads != 0 || o.blocks_per_sm != 0 || o.samples_per_block > 0) return resolve_cfg(o);
-    const bool sparse = g->gd.m <= 32 * (int64_t)g->gd.n;
+    const bool sparse = g->gd.m <= 8 * (int64_t)g->gd.n;
     kad_options d = o;
     d.block_threads = sparse ? 256 : 512;
     d.blocks_per_sm = sparse ? 4 : 2;

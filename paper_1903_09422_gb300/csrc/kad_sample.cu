@@ -76,6 +76,9 @@ struct Smem {
     unsigned long long next_dsum[2];
     volatile int met[2];
     int abort; // the run stopped while this (adaptive) sample was in its BFS
+    // probe-first policy of this block: > 0 while probed rounds usually met;
+    // large rounds counted, so that every 16th is probed whatever the score
+    int probe_score, probe_rounds;
     int chunk_total; // arcs of a one-vertex chunk
     int mcount;    // members of M recorded (the first m_cap ids are in m_id)
     int mid;
@@ -1146,6 +1149,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     // into the next level or meeting set.
     unsigned long long w_pred = 0;
     if (tid < KAD_WORK_WORDS) sm.acc[tid] = 0;
+    if (tid == 0) {
+        sm.probe_score = 4;
+        sm.probe_rounds = 0;
+    }
     if (tid == 0 && a.mode == KAD_MODE_RING) atomicCAS(&a.ctl->t_start, 0ull, global_ns());
     Stream st;
 
@@ -1365,8 +1372,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             // claims new vertices only if it found none.  Almost all of a large
             // round's arcs are scanned in the meeting round, where claims are
             // wasted work; an ordinary large round is scanned twice.
-            const bool probe_first = !(a.debug & KAD_DEBUG_NO_PROBE) && sm.dsum[X] > (unsigned long long)(BLOCK * KAD_ITEMS);
-            // (probe passes carry KAD_PITEMS arcs per thread)
+            // Whether a large round is the meeting round depends on the graph:
+            // on low-diameter graphs it usually is, on deep ones (grids) almost
+            // never.  The block keeps a score of how its probes fared and probes
+            // while it is positive, and every 16th large round regardless.
+            const bool large = sm.dsum[X] > (unsigned long long)(BLOCK * KAD_ITEMS);
+            const bool probe_first = !(a.debug & KAD_DEBUG_NO_PROBE) && large &&
+                                     (sm.probe_score > 0 || (sm.probe_rounds & 15) == 0);
             for (int ph = probe_first ? 0 : 1; ph < 2; ph++) {
             // a meeting found by the pairwise test or the probe completes the round
             if (sm.met[rb] || sm.abort) break;
@@ -1452,6 +1464,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             w_pred += met ? pred_m : pred_next;
             long long tc = 0;
             if (tid == 0) tc = clock64();
+            if (tid == 0 && large) {
+                sm.probe_rounds++;
+                if (probe_first) sm.probe_score = met ? min(sm.probe_score + 1, 8) : sm.probe_score - 1;
+            }
             if (tid == 0) {
                 if (sm.abort) {
                     // An expansion pass saw the run's stop: this sample lies beyond

@@ -100,6 +100,7 @@ struct WCtx {
     int fb[2], fe[2], lev[2], tail[2], root_rs[2];
     int met;    // the round reached the other side's frontier
     int probe;  // this scan of the round only looks for the other side's frontier (no claims)
+    int probe_score, probe_rounds; // probe-first policy (as the block kernel's)
     int mcount; // meeting-set members recorded (atomic)
     int predm;  // pred counts arcs into M (1) or into the next level (0)
     uint32_t sideX, keyNext;
@@ -719,7 +720,9 @@ __device__ __noinline__ void w_search(const SampleArgs &a, WShared &S, int c) {
         // A large round is probed first: one scan that only looks for arcs into
         // the other side's frontier, and claims new vertices only if it found
         // none (the meeting round holds almost all of a sample's arcs).
-        const bool probe_first = !(a.debug & KAD_DEBUG_NO_PROBE) && dX > W_PROBE_MIN_ARCS;
+        const bool large = dX > W_PROBE_MIN_ARCS;
+        const bool probe_first = !(a.debug & KAD_DEBUG_NO_PROBE) && large &&
+                                 (C.probe_score > 0 || (C.probe_rounds & 15) == 0);
         long long tp = 0;
         if (lane == 0) tp = clock64();
         for (int ph = probe_first ? 0 : 1; ph < 2; ph++) {
@@ -740,6 +743,10 @@ __device__ __noinline__ void w_search(const SampleArgs &a, WShared &S, int c) {
             const long long tc = clock64();
             C.acc[14] += (unsigned long long)(tc - tp);
             const int met = C.met;
+            if (large) {
+                C.probe_rounds++;
+                if (probe_first) C.probe_score = met ? min(C.probe_score + 1, 8) : C.probe_score - 1;
+            }
             const unsigned long long pr = C.pred;
             C.acc[3] += met ? (pr >> 40) : (pr & ((1ull << 40) - 1));
             if (C.abort) {
@@ -1507,6 +1514,10 @@ __global__ void __launch_bounds__(W_THREADS, 1) k_wsample(const SampleArgs a) {
         S.c[wid].jend = 0;
     }
     if (lane < KAD_WORK_WORDS) S.c[wid].acc[lane] = 0;
+    if (lane == 0) {
+        S.c[wid].probe_score = 4;
+        S.c[wid].probe_rounds = 0;
+    }
     if (tid == 0 && a.mode == KAD_MODE_RING) atomicCAS(&a.ctl->t_start, 0ull, global_ns());
     __syncthreads();
     // a launch that continues a run first closes what an earlier launch completed
