@@ -419,6 +419,13 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
     const bool leader = tl == 0;
     int nb = 0, par = 0;
     while (d >= 1) {
+        if (d == 1) {
+            // The only vertex at distance 0 is the root.  Its draw, U(1), takes
+            // exactly one word of the stream and cannot be rejected: the leader
+            // just consumes the word, and the team needs no barrier.
+            if (leader) st.next();
+            break;
+        }
         if (leader) sm.t_r[t] = st.uniform(sc, a.ctl);
         team_bar(t, TT);
         const unsigned long long r = sm.t_r[t];
@@ -426,11 +433,7 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
         unsigned long long s_sel = 0;
         const int ls = (d <= KAD_MAXLV) ? sm.lvs[z][d - 1] : 0;
         const int lcnt = (d <= KAD_MAXLV) ? sm.lvs[z][d] - ls : KAD_LCAP + 1;
-        if (d == 1) {
-            // the only vertex at distance 0 is the root
-            p_sel = z ? sm.t : sm.s;
-            s_sel = 1ull;
-        } else if (!(a.debug & KAD_DEBUG_TRACE_SCAN) && reC - rsC > KAD_DEG_SCAN && lcnt <= KAD_LCAP) {
+        if (!(a.debug & KAD_DEBUG_TRACE_SCAN) && reC - rsC > KAD_DEG_SCAN && lcnt <= KAD_LCAP) {
             // few vertices at distance d-1: the team tests each of them for
             // adjacency to cur
             team_from_level<BLOCK>(a, sm, t, label, list, n, z, ls, lcnt, cur, rsC, reC, r, p_sel, s_sel);
@@ -1160,6 +1163,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     // completed while the L table was not yet available.
     if (a.mode == KAD_MODE_RING && blockIdx.x == 0) run_closer<BLOCK>(a, sm);
 
+    unsigned long long g_pre = ~0ull; // thread 0: an index fetched ahead (~0: none)
     for (;;) {
         // ---------------------------------------------------- next sample index
         if (tid == 0) {
@@ -1168,7 +1172,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             uint32_t dom = a.domain;
             const bool stopped = (a.mode == KAD_MODE_RING) && (*(volatile int *)&a.ctl->stop != 0);
             if (!stopped) {
-                const unsigned long long g = atomicAdd(&a.ctl->next, 1ull);
+                const unsigned long long g = (g_pre != ~0ull) ? g_pre : atomicAdd(&a.ctl->next, 1ull);
+                g_pre = ~0ull;
                 if (a.mode == KAD_MODE_RECORD) {
                     if (g < a.i1) idx = g;
                 } else if (g < a.calib_n) {
@@ -1412,6 +1417,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     }
                     __syncthreads();
                     total = sm.chunk_total;
+                } else if (cnt <= 32) {
+                    // every entry is in warp 0: a warp scan, one barrier
+                    if (tid < 32) {
+                        int x = d;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int y = __shfl_up_sync(FULL_MASK, x, o);
+                            if (lane >= o) x += y;
+                        }
+                        if (tid < cnt) sm.off[tid] = x - d;
+                        if (tid == 31) sm.chunk_total = x;
+                    }
+                    __syncthreads();
+                    total = sm.chunk_total;
                 } else {
                     const int excl = block_excl_scan<BLOCK>(d, sm.wtmp, total);
                     if (tid < cnt) sm.off[tid] = excl;
@@ -1502,6 +1521,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             const long long now = clock64();
             sm.acc[9] += (unsigned long long)(now - sm.tmark);
             sm.tmark = now;
+            // the next sample's index, fetched while this one is finished (an
+            // index taken after the run stopped is simply not computed: its
+            // epoch lies beyond the stop epoch)
+            g_pre = atomicAdd(&a.ctl->next, 1ull);
         }
         const int D = sm.D;
         unsigned long long sst = 0;
@@ -1512,7 +1535,49 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             // members recorded during the search: the first mcap in shared
             // memory, the next mext in the slot's extension
             const int mtot = mcap + mext;
-            const bool recorded = sm.mcount <= mtot;
+            const int mc0 = sm.mcount; // final: the round ended at a barrier
+            if (mc0 <= 32 && mc0 <= mtot) {
+                // A small recorded M (most samples): warp 0 alone, one member per
+                // lane -- weights, their saturating sum, the draw, and each
+                // member's exclusive prefix in id order by shuffles.
+                if (tid < 32) {
+                    int id = 0x7fffffff;
+                    unsigned long long w = 0;
+                    if (lane < mc0) {
+                        id = (lane < mcap) ? sm.m_id[lane] : __ldcg(mext_id + (lane - mcap));
+                        uint32_t lv;
+                        unsigned long long s1;
+                        const unsigned long long s2 = kad_ld_u64(sigma2 + id);
+                        ld_vs(label, id, lv, s1);
+                        w = kad_sat_mul((lv & KAD_OVF2) ? KAD_U64MAX : s2, sig_val(lv, s1));
+                    }
+                    unsigned long long tot = w;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) tot = kad_sat_add(tot, __shfl_xor_sync(FULL_MASK, tot, o));
+                    unsigned long long r = 0;
+                    if (tid == 0) {
+                        r = st.uniform(tot ? tot : 1ull, a.ctl);
+                        sm.sst = tot;
+                        sm.st_w0 = st.w0;
+                        sm.st_w1 = st.w1;
+                        sm.st_blk = st.blk;
+                        sm.st_pos = st.pos;
+                    }
+                    r = __shfl_sync(FULL_MASK, r, 0);
+                    unsigned long long ex = 0;
+                    for (int q = 0; q < mc0; q++) {
+                        const int iq = __shfl_sync(FULL_MASK, id, q);
+                        const unsigned long long wq = __shfl_sync(FULL_MASK, w, q);
+                        if (iq < id) ex = kad_sat_add(ex, wq);
+                    }
+                    const unsigned hit = __ballot_sync(FULL_MASK, lane < mc0 && ex <= r && kad_sat_add(ex, w) > r);
+                    const int chosen = __shfl_sync(FULL_MASK, id, hit ? __ffs(hit) - 1 : 0);
+                    if (tid == 0) sm.mid = hit ? chosen : -1;
+                }
+                __syncthreads();
+                sst = sm.sst;
+            } else {
+            const bool recorded = mc0 <= mtot;
             __syncthreads();
             if (tid == 0 && !recorded) sm.mcount = 0;
             __syncthreads();
@@ -1605,6 +1670,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                                         ye, r);
             }
             __syncthreads();
+            }
         }
 
         if (tid == 0) {

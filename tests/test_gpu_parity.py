@@ -253,7 +253,7 @@ def test_autotuner_keeps_results_and_choice(kad):
         r3 = G.run(0.05, 0.1, 8)  # without the flag: the average-degree rule
     assert (r1["block_threads_used"], r1["blocks_per_sm_used"]) in {(512, 2), (256, 4), (256, 2), (1024, 1), (128, 8)}
     assert (r1["block_threads_used"], r1["blocks_per_sm_used"]) == (r2["block_threads_used"], r2["blocks_per_sm_used"])
-    assert (r3["block_threads_used"], r3["blocks_per_sm_used"]) == ((256, 4) if g.m <= 32 * g.n else (512, 2))
+    assert (r3["block_threads_used"], r3["blocks_per_sm_used"]) == ((256, 4) if g.m <= 8 * g.n else (512, 2))
     for r in (r1, r2, r3):
         assert r["tau"] == ref["tau"]
         np.testing.assert_array_equal(r["counts"], ref["counts"])
@@ -378,11 +378,11 @@ def test_workspace_kept_across_graphs(kad):
 
 
 def test_default_variant_follows_average_degree(kad):
-    # without a named variant: 256x4 on graphs of average degree up to 32,
+    # without a named variant: 256x4 on graphs of average degree up to 8,
     # 512x2 on denser ones; the results are those of the oracle either way
-    for g, want in ((gen.grid(48, seed=7), (256, 4)), (gen.rmat(12, 8, seed=1), (256, 4)),
+    for g, want in ((gen.grid(48, seed=7), (256, 4)), (gen.rmat(12, 8, seed=1), (512, 2)),
                     (gen.er(300, 0.25, seed=2), (512, 2))):
-        assert (g.m <= 32 * g.n) == (want == (256, 4))
+        assert (g.m <= 8 * g.n) == (want == (256, 4))
         ref = O.kadabra(g, 0.05, 0.1, 3)
         with kad.Graph.from_csr(g) as G:
             r = G.run(0.05, 0.1, 3)
