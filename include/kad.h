@@ -119,12 +119,13 @@ typedef struct {
 } kad_options;
 
 #define KAD_RUN_TIMING 1u      /* fill kad_result.t_* with CUDA-event times of each phase */
-#define KAD_RUN_AUTOTUNE 2u    /* the graph's first run (block_threads and blocks_per_sm both 0) times the
-                                  same query, truncated after 4 epochs, twice under each candidate variant
-                                  and keeps the fastest for the graph's later runs (graphs under 16384
-                                  vertices keep the default).  Off by default: the degree rule picks
-                                  the fastest on every configured workload, and tuning costs ~10
-                                  truncated runs */
+#define KAD_RUN_AUTOTUNE 2u    /* the graph's first run (block_threads, blocks_per_sm and samples_per_block
+                                  all 0) times the same query, truncated after 4 epochs, twice under each
+                                  candidate -- block per sample 512x2, 256x4, 256x2, 1024x1, 128x8, and
+                                  warp per sample with 8 or 24 samples per block -- and keeps the fastest
+                                  for the graph's later runs (graphs under 16384 vertices keep the
+                                  default).  Off by default: the degree rule picks the fastest on every
+                                  configured workload, and tuning costs 14 truncated runs */
 #define KAD_RUN_COMPLETION_ORDER 4u /* the non-deterministic mode of the epoch-based framework
                                   (Section 3.1; local-/shared-frame of Section 3.2): epoch k holds
                                   the samples that were the (kN+1)-th to (k+1)N-th to complete,
@@ -270,6 +271,39 @@ kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row_ptr, const
                                       const int32_t *d_comp, uint64_t seed, uint32_t domain, uint64_t i0,
                                       int64_t count, kad_stream_t stream, int32_t *d_s, int32_t *d_t, int32_t *d_D,
                                       uint64_t *d_sigma_st, uint8_t *d_overflow, int32_t *d_paths, int32_t cap);
+
+/* ------------------------------------------------------------------ sharding
+ * A KADABRA run whose samples are split among `world` ranks, one GPU each: the
+ * distributed reduction of sampling states that Section 6 (conclusions and
+ * future work) names as the next step, with the fixed sample-to-epoch
+ * assignment of the indexed-frame algorithm (Appendix D.2).
+ *
+ * The calibration range [0, tau0) and every epoch's range [kN, (k+1)N) are
+ * split into `world` contiguous chunks in rank order (kad_shard_range); rank r
+ * computes the samples of its chunks.  After each phase every rank contributes
+ * its chunk's path rows and receives all ranks' rows through `allgather`, then
+ * folds all of them into its own counts on the device (integer addition, so the
+ * order does not matter) and evaluates the stop rule (Appendix B) on the same
+ * state as every other rank: all ranks stop at the same epoch, with the same
+ * counts, tau and L table as kad_run on one GPU, bit for bit.
+ *
+ * allgather(user, send, bytes, recv): a collective the caller provides (NCCL,
+ * MPI, gloo, ...).  send: host, `bytes` bytes; recv: host, world * bytes,
+ * receiving rank q's send at offset q * bytes.  Every rank calls it the same
+ * number of times with the same `bytes`.  Return 0 on success; anything else
+ * ends the run with KAD_ERR_CANCELLED.
+ * Outputs as kad_run (host pointers in *out); work counters and samples_computed
+ * are this rank's own.  KAD_RUN_COMPLETION_ORDER is rejected
+ * (KAD_ERR_INVALID_ARG).  Blocking; device work on `stream`.
+ */
+typedef int (*kad_allgather_fn)(void *user, const void *send, size_t bytes, void *recv);
+kad_status kad_run_sharded(kad_graph *g, double eps, double delta, uint64_t seed, int32_t rank, int32_t world,
+                           kad_allgather_fn allgather, void *user, kad_stream_t stream, const kad_options *opt,
+                           kad_result *out);
+
+/* The chunk [*lo, *hi) of `count` items that rank `rank` of `world` takes:
+ * contiguous, in rank order, sizes differing by at most one.  Host only. */
+void kad_shard_range(int64_t count, int32_t rank, int32_t world, int64_t *lo, int64_t *hi);
 
 /*
  * kad_run_order -- after a KAD_RUN_COMPLETION_ORDER run on g: idx_out[q] = the

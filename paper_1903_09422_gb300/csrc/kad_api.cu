@@ -769,12 +769,15 @@ kad_status autotune(kad_graph *g, Workspace &w, double eps, double delta, const 
         g->tuned_per_sm = best.per_sm;
     }
     if (!g->tuned_threads) {
-        static const int cand[5][2] = {{512, 2}, {256, 4}, {256, 2}, {1024, 1}, {128, 8}};
+        // block per sample (threads, blocks per SM), then warp per sample
+        // (0, samples per block): one block of 1024 threads per SM
+        static const int cand[7][2] = {{512, 2}, {256, 4}, {256, 2}, {1024, 1}, {128, 8}, {0, 8}, {0, 24}};
         double best_ms = 0.0;
-        for (int c = 0; c < 5; c++) {
+        for (int c = 0; c < 7; c++) {
             kad_options o2 = o;
             o2.block_threads = cand[c][0];
-            o2.blocks_per_sm = cand[c][1];
+            o2.blocks_per_sm = cand[c][0] ? cand[c][1] : 0;
+            o2.samples_per_block = cand[c][0] ? 0 : cand[c][1];
             o2.max_epochs = kTuneEpochs;
             o2.flags = (o2.flags | KAD_RUN_TIMING) & ~KAD_RUN_AUTOTUNE;
             // twice, keeping the faster: the first launch of a variant also pays
@@ -789,14 +792,22 @@ kad_status autotune(kad_graph *g, Workspace &w, double eps, double delta, const 
             }
             if (c == 0 || ms < best_ms) {
                 best_ms = ms;
-                g->tuned_threads = cand[c][0];
+                g->tuned_threads = cand[c][0] ? cand[c][0] : -1; // -1: warp per sample
                 g->tuned_per_sm = cand[c][1];
             }
         }
     }
-    best.threads = g->tuned_threads;
-    best.per_sm = g->tuned_per_sm;
-    best.dyn_smem = 0;
+    if (g->tuned_threads > 0) {
+        best.threads = g->tuned_threads;
+        best.per_sm = g->tuned_per_sm;
+        best.dyn_smem = 0;
+        best.warp = 0;
+        best.nctx = 0;
+    } else {
+        kad_options o3 = o;
+        o3.samples_per_block = g->tuned_per_sm;
+        best = resolve_cfg(o3);
+    }
     return KAD_OK;
 }
 
@@ -836,7 +847,7 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
     if (nclass > (size_t)0x7fffffff || omega > ((uint64_t)1 << 40)) return KAD_ERR_INVALID_ARG;
     kad_status s;
     LaunchCfg cfg = default_cfg(g, o);
-    if (o.block_threads == 0 && o.blocks_per_sm == 0 && (o.flags & KAD_RUN_AUTOTUNE))
+    if (o.block_threads == 0 && o.blocks_per_sm == 0 && o.samples_per_block == 0 && (o.flags & KAD_RUN_AUTOTUNE))
         if ((s = autotune(g, w, eps, delta, o, st, cfg)) != KAD_OK) return s;
     if (o.debug & KAD_DEBUG_SMEM_BITMAP) choose_bitmap_home(cfg, g->gd.n, g->device);
     const int slots = resolve_slots(g, w, o, cfg);
@@ -1321,6 +1332,250 @@ kad_status kad_run_device(kad_graph *g, double eps, double delta, uint64_t seed,
     if (!g) return KAD_ERR_INVALID_ARG;
     ws_adopt(g);
     return run_impl(g, g->ws, eps, delta, seed, (cudaStream_t)stream, opt, d_bc, d_counts, out, false);
+}
+
+void kad_shard_range(int64_t count, int32_t rank, int32_t world, int64_t *lo, int64_t *hi) {
+    if (!lo || !hi) return;
+    if (count < 0 || world < 1 || rank < 0 || rank >= world) {
+        *lo = *hi = 0;
+        return;
+    }
+    // contiguous chunks whose sizes differ by at most one, in rank order
+    *lo = (int64_t)(((__int128)count * rank) / world);
+    *hi = (int64_t)(((__int128)count * (rank + 1)) / world);
+}
+
+kad_status kad_run_sharded(kad_graph *g, double eps, double delta, uint64_t seed, int32_t rank, int32_t world,
+                           kad_allgather_fn allgather, void *user, kad_stream_t stream, const kad_options *opt_in,
+                           kad_result *out) {
+    if (!g || !out || !allgather || world < 1 || rank < 0 || rank >= world) return KAD_ERR_INVALID_ARG;
+    if (g->poisoned) return KAD_ERR_CUDA;
+    if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0)) return KAD_ERR_INVALID_ARG;
+    const double t_entry = now_ms();
+    kad_options o;
+    if (opt_in)
+        o = *opt_in;
+    else
+        fill_defaults(&o);
+    if (o.epoch_size == 0 || o.calib_div == 0 || (o.flags & KAD_RUN_COMPLETION_ORDER)) return KAD_ERR_INVALID_ARG;
+    if (cudaSetDevice(g->device) != cudaSuccess) return fail(g, cudaGetLastError());
+    ws_adopt(g);
+    Workspace &w = g->ws;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int32_t n = g->gd.n;
+    const uint32_t N = o.epoch_size;
+    const uint64_t omega = run_omega(g->vd, eps, delta);
+    const uint64_t tau0 = run_calib(omega, N, o.calib_div);
+    uint64_t max_epochs = (omega + N - 1) / N;
+    if (o.max_epochs && o.max_epochs < max_epochs) max_epochs = o.max_epochs;
+    const size_t nclass = (size_t)tau0 + 1;
+    if (nclass > (size_t)0x7fffffff || omega > ((uint64_t)1 << 40)) return KAD_ERR_INVALID_ARG;
+    const int32_t cap = path_cap(g);
+    // every rank pads its chunk to maxc rows: the largest chunk of either phase
+    const int64_t maxc = (int64_t)(((tau0 > N ? tau0 : N) + (uint64_t)world - 1) / (uint64_t)world);
+    const size_t blk_ints = (size_t)maxc * (size_t)(2 + cap);
+    if ((double)blk_ints * (double)world * 4.0 > (double)((size_t)1 << 34)) return KAD_ERR_INVALID_ARG;
+    LaunchCfg cfg = default_cfg(g, o);
+    int slots = resolve_slots(g, w, o, cfg);
+    kad_status s;
+    if ((s = ensure_fixed(g, w, nclass, 2, st)) != KAD_OK) return s;
+    if ((s = ensure_slots(g, w, slots, st)) != KAD_OK) return s;
+    if ((s = ensure_rows(w, (size_t)maxc, cap, st)) != KAD_OK) return s;
+
+    int32_t *d_blocks = nullptr, *d_s = nullptr, *d_t = nullptr, *d_D = nullptr;
+    unsigned long long *d_sst = nullptr, *d_ovf = nullptr;
+    int *d_fail = nullptr;
+    int32_t *h_send = nullptr, *h_recv = nullptr;
+    uint8_t *h_flag = nullptr;
+    uint32_t *h_hist = nullptr;
+    cudaError_t e = cudaSuccess;
+    uint64_t tau = 0, epochs = 0, ovf = 0;
+    int stopped_by = 0;
+    double ts = 0.0;
+    unsigned long long work[KAD_WORK_WORDS];
+    if (dalloc(&d_blocks, blk_ints * (size_t)world) != cudaSuccess || dalloc(&d_s, (size_t)maxc) != cudaSuccess ||
+        dalloc(&d_t, (size_t)maxc) != cudaSuccess || dalloc(&d_D, (size_t)maxc) != cudaSuccess ||
+        dalloc(&d_sst, (size_t)maxc) != cudaSuccess || dalloc(&d_ovf, 1) != cudaSuccess ||
+        dalloc(&d_fail, 1) != cudaSuccess) {
+        cudaGetLastError();
+        s = KAD_ERR_OOM;
+        goto done;
+    }
+    h_send = (int32_t *)malloc(blk_ints * 4);
+    h_recv = (int32_t *)malloc(blk_ints * 4 * (size_t)world);
+    h_flag = (uint8_t *)malloc((size_t)maxc);
+    h_hist = (uint32_t *)malloc(nclass * 4);
+    if (!h_send || !h_recv || !h_flag || !h_hist) {
+        s = KAD_ERR_OOM;
+        goto done;
+    }
+    if ((e = cudaMemsetAsync(w.c0, 0, (size_t)n * 4, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(w.cnt, 0, (size_t)n * 4, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(w.hist, 0, nclass * 4, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(w.ctl, 0, sizeof(KadCtl), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d_ovf, 0, 8, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(w.work, 0, KAD_WORK_WORDS * sizeof(unsigned long long), st)) != cudaSuccess) {
+        s = fail(g, e);
+        goto done;
+    }
+    k_hist_init<<<1, 32, 0, st>>>(w.hist, (uint32_t)n);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        s = fail(g, e);
+        goto done;
+    }
+    // phase 0: calibration (domain 1, indices [0, tau0)); phase k >= 1: adaptive
+    // epoch k-1 (domain 0, indices [(k-1)N, kN))
+    for (uint64_t ph = 0; ph <= max_epochs; ph++) {
+        const bool calib = ph == 0;
+        const uint64_t base = calib ? 0 : (ph - 1) * (uint64_t)N;
+        const int64_t count = calib ? (int64_t)tau0 : (int64_t)N;
+        int64_t lo = 0, hi = 0;
+        kad_shard_range(count, rank, world, &lo, &hi);
+        const int64_t c = hi - lo;
+        // this rank's chunk, in record mode: one path row per sample
+        if (c > 0) {
+            SampleArgs a = base_args(g, w, seed);
+            a.mcap = (o.mcap < 0) ? kDefaultMcap : o.mcap;
+            a.debug = o.debug;
+            a.domain = calib ? 1 : 0;
+            a.i0 = base + (uint64_t)lo;
+            a.i1 = base + (uint64_t)hi;
+            a.mode = KAD_MODE_RECORD;
+            a.paths = w.paths;
+            a.cap = cap;
+            a.plen = w.plen;
+            a.pflag = w.pflag;
+            a.rec_s = d_s;
+            a.rec_t = d_t;
+            a.rec_D = d_D;
+            a.rec_sst = d_sst;
+            a.epoch = 1;
+            a.ring = 1;
+            if ((s = launch_phase(g, w, a, (int)(c < slots ? c : slots), cfg, a.i0, st)) != KAD_OK) goto done;
+        }
+        // pack [lengths][flags][paths] of maxc rows; absent rows have length -1
+        for (int64_t j = 0; j < maxc; j++) h_send[j] = -1;
+        if (c > 0) {
+            e = cudaMemcpyAsync(h_send, w.plen, (size_t)c * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h_flag, w.pflag, (size_t)c, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_send + 2 * maxc, w.paths, (size_t)c * (size_t)cap * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                s = fail(g, e);
+                goto done;
+            }
+            KadCtl hc;
+            if ((s = read_ctl(g, w, &hc, st)) != KAD_OK) goto done;
+        }
+        for (int64_t j = 0; j < maxc; j++) h_send[maxc + j] = (j < c) ? (int32_t)h_flag[j] : 0;
+        if (allgather(user, h_send, blk_ints * 4, h_recv) != 0) {
+            s = KAD_ERR_CANCELLED;
+            goto done;
+        }
+        if ((e = cudaMemcpyAsync(d_blocks, h_recv, blk_ints * 4 * (size_t)world, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = kad_launch_fold_rows(d_blocks, world, (int)maxc, cap, calib ? 1 : 0, w.c0, w.hist, w.cnt, w.classmax,
+                                      w.c0, d_ovf, st)) != cudaSuccess) {
+            s = fail(g, e);
+            goto done;
+        }
+        if (calib) {
+            // every rank now holds the same c0: the histogram, tau* and the L
+            // table on the host, as in kad_run
+            if ((e = cudaMemcpyAsync(h_hist, w.hist, nclass * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+                s = fail(g, e);
+                goto done;
+            }
+            ts = run_tau_star(h_hist, tau0, eps, delta, omega);
+            for (size_t q = 0; q < nclass; q++) {
+                w.h_ltab[q] = run_L((double)q / (double)tau0, ts, eps, omega);
+                w.h_cmax[q] = h_hist[q] ? 0 : -1;
+            }
+            if ((e = cudaMemcpyAsync(w.ltab, w.h_ltab, nclass * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(w.classmax, w.h_cmax, nclass * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+                s = fail(g, e);
+                goto done;
+            }
+            continue;
+        }
+        // the stop rule on the state after epochs 0..ph-1 (Appendix B)
+        tau = ph * (uint64_t)N;
+        epochs = ph;
+        if (tau >= omega) {
+            stopped_by = 1;
+            break;
+        }
+        int failed = 1;
+        if ((e = cudaMemsetAsync(d_fail, 0, sizeof(int), st)) != cudaSuccess ||
+            (e = kad_launch_check_classes(w.classmax, w.ltab, (int)nclass, tau, omega, eps, d_fail, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&failed, d_fail, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            s = fail(g, e);
+            goto done;
+        }
+        if (!failed) {
+            stopped_by = 0;
+            break;
+        }
+        if (o.max_epochs && ph >= o.max_epochs) {
+            stopped_by = 2;
+            break;
+        }
+    }
+    if (epochs == 0) { // cannot happen: the loop runs at least one adaptive epoch
+        s = KAD_ERR_INTERNAL;
+        goto done;
+    }
+    // outputs, as kad_run's host outputs
+    e = cudaMemcpyAsync(work, w.work, sizeof(work), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ovf, d_ovf, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && out->bc) {
+        e = kad_launch_finalize(w.cnt, n, tau, w.bc, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out->bc, w.bc, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess && out->counts) e = cudaMemcpyAsync(out->counts, w.cnt, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && out->c0) e = cudaMemcpyAsync(out->c0, w.c0, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && out->ltab && out->ltab_cap >= (int64_t)nclass)
+        e = cudaMemcpyAsync(out->ltab, w.ltab, nclass * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        s = fail(g, e);
+        goto done;
+    }
+    out->tau = tau;
+    out->omega = omega;
+    out->calib_samples = tau0;
+    out->samples_computed = work[6];
+    out->overflow_samples = ovf;
+    out->epochs = (uint32_t)epochs;
+    out->vd_bound = g->vd;
+    out->sigma_overflow = ovf ? 1 : 0;
+    out->stopped_by_omega = stopped_by;
+    out->tau_star = ts;
+    for (int i = 0; i < 6; i++) out->work[i] = work[i];
+    for (int i = 0; i < 6; i++) out->phase_cycles[i] = work[8 + i];
+    out->slots_used = slots;
+    out->block_threads_used = cfg.threads;
+    out->blocks_per_sm_used = cfg.per_sm;
+    out->samples_per_block_used = cfg.warp ? cfg.nctx : 0;
+    out->t_host_ms = now_ms() - t_entry;
+    out->t_total_ms = out->t_host_ms;
+    s = KAD_OK;
+done:
+    cudaFree(d_blocks);
+    cudaFree(d_s);
+    cudaFree(d_t);
+    cudaFree(d_D);
+    cudaFree(d_sst);
+    cudaFree(d_ovf);
+    cudaFree(d_fail);
+    free(h_send);
+    free(h_recv);
+    free(h_flag);
+    free(h_hist);
+    return s;
 }
 
 kad_status kad_run_order(kad_graph *g, uint64_t *idx_out, uint64_t count) {

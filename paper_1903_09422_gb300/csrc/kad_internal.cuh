@@ -188,6 +188,12 @@ int kad_sample_max_blocks_per_sm(int threads, int per_sm, size_t dyn_smem);
 cudaError_t kad_launch_wsample(const SampleArgs &a, int blocks, size_t dyn_smem, cudaStream_t st);
 size_t kad_wsample_static_smem();
 int kad_wsample_max_blocks_per_sm(size_t dyn_smem);
+// the sharded run's fold of all ranks' path rows and its stop check (kad_shard.cu)
+cudaError_t kad_launch_fold_rows(const int32_t *blocks, int world, int maxc, int cap, int calib, uint32_t *c0w,
+                                 uint32_t *hist, uint32_t *cnt, int32_t *classmax, const uint32_t *c0,
+                                 unsigned long long *ovf, cudaStream_t st);
+cudaError_t kad_launch_check_classes(const int32_t *classmax, const double *ltab, int nclass, unsigned long long tau,
+                                     unsigned long long omega, double eps, int *fail, cudaStream_t st);
 cudaError_t kad_launch_finalize(const uint32_t *cnt, int32_t n, unsigned long long tau, double *bc, cudaStream_t st);
 cudaError_t kad_launch_fg(const uint32_t *counts, const uint32_t *c0, const double *ltab, int32_t n,
                           unsigned long long tau, unsigned long long omega, double *f, double *g, cudaStream_t st);

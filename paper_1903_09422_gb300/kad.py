@@ -63,7 +63,7 @@ class ServerOptions(ctypes.Structure):
 EXPORTS = ("kad_graph_create", "kad_graph_create_device", "kad_graph_free", "kad_graph_info", "kad_options_default",
            "kad_run", "kad_run_device", "kad_sample_records", "kad_sample_records_noalloc", "kad_eval_fg",
            "kad_server_create", "kad_server_add_graph", "kad_submit", "kad_poll", "kad_wait", "kad_server_free",
-           "kad_status_string", "kad_version", "kad_trim", "kad_run_order")
+           "kad_status_string", "kad_version", "kad_trim", "kad_run_order", "kad_run_sharded", "kad_shard_range")
 
 _lib = None
 
@@ -121,8 +121,54 @@ def load():
     lib.kad_trim.restype = None
     lib.kad_run_order.argtypes = [vp, vp, u64]
     lib.kad_run_order.restype = st
+    lib.kad_run_sharded.argtypes = [vp, dbl, dbl, u64, i32, i32, ALLGATHER_FN, vp, vp, ctypes.POINTER(Options),
+                                    ctypes.POINTER(Result)]
+    lib.kad_run_sharded.restype = st
+    lib.kad_shard_range.argtypes = [i64, i32, i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.kad_shard_range.restype = None
     _lib = lib
     return lib
+
+
+# int allgather(void *user, const void *send, size_t bytes, void *recv)
+ALLGATHER_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+def shard_range(count, rank, world):
+    """kad_shard_range: the chunk [lo, hi) of `count` items that `rank` of `world` takes."""
+    lo, hi = ctypes.c_int64(0), ctypes.c_int64(0)
+    load().kad_shard_range(count, rank, world, ctypes.byref(lo), ctypes.byref(hi))
+    return lo.value, hi.value
+
+
+def make_allgather(fn):
+    """Wrap fn(send: bytes) -> bytes (all ranks' sends concatenated in rank order)
+    as the C callback of kad_run_sharded.  Keep the returned object alive for the
+    duration of the call."""
+    def cb(user, send, nbytes, recv):
+        try:
+            out = fn(ctypes.string_at(send, nbytes))
+            ctypes.memmove(recv, out, len(out))
+            return 0
+        except Exception:
+            return 1
+    return ALLGATHER_FN(cb)
+
+
+def torch_allgather(group=None):
+    """An allgather over a torch.distributed process group (host bytes in, host
+    bytes out; device tensors when the group's backend is NCCL)."""
+    import torch
+    import torch.distributed as dist
+
+    def fn(payload):
+        world = dist.get_world_size(group)
+        dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+        src = torch.frombuffer(bytearray(payload), dtype=torch.uint8).to(dev)
+        dst = torch.empty(world * src.numel(), dtype=torch.uint8, device=dev)
+        dist.all_gather_into_tensor(dst, src, group=group)
+        return dst.cpu().numpy().tobytes()
+    return fn
 
 
 def status_string(s):
@@ -258,6 +304,35 @@ class Graph:
                                   d_counts.data_ptr() if d_counts is not None else None, ctypes.byref(r)),
                "kad_run_device")
         return _result_scalars(r)
+
+    def run_sharded(self, eps, delta, seed, rank, world, allgather, stream=None, counts=True, c0=False, ltab=False,
+                    **opt):
+        """kad_run_sharded: this rank's part of a run split among `world` ranks.
+        allgather: fn(send: bytes) -> bytes, all ranks' sends in rank order."""
+        lib = load()
+        o = options(**opt)
+        r = Result()
+        out = {}
+        bc = np.zeros(self.n, dtype=np.float64)
+        r.bc = bc.ctypes.data
+        if counts:
+            out["counts"] = np.zeros(self.n, dtype=np.uint32)
+            r.counts = out["counts"].ctypes.data
+        if c0:
+            out["c0"] = np.zeros(self.n, dtype=np.uint32)
+            r.c0 = out["c0"].ctypes.data
+        if ltab:
+            out["L"] = np.zeros(1 << 22, dtype=np.float64)
+            r.ltab = out["L"].ctypes.data
+            r.ltab_cap = out["L"].size
+        cb = make_allgather(allgather)
+        _check(lib.kad_run_sharded(self._h, eps, delta, seed, rank, world, cb, None, _stream_handle(stream),
+                                   ctypes.byref(o), ctypes.byref(r)), "kad_run_sharded")
+        out["bc"] = bc
+        out.update(_result_scalars(r))
+        if ltab:
+            out["L"] = out["L"][: r.calib_samples + 1].copy()
+        return out
 
     def run_order(self, count):
         """kad_run_order: the adaptive sample indices at fold positions [0, count)
