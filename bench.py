@@ -44,17 +44,19 @@ BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=0, 
 # DRAM traffic of the sampling kernel measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), bytes per computed sample, with the SHA-256 prefix of
 # the kernel source file it was measured on.  A workload without an entry, or
-# whose kernel source has changed since, reports traffic null.  rmat20: 2.78 GB
-# over a launch of 31,000 samples; rmat18: 0.82 GB over 31,000; hyp4m: 57.8 GB
-# over 142,000; grid2048: 697 GB over 56,000 (profiles/k_sample_rmat20_dram.md,
-# profiles/k_sample_rmat18_full.md, profiles/k_sample_hyp4m_grid2048_dram.md).
+# whose kernel source has changed since, reports traffic null.  Each figure is a
+# query's first sampling launch, which under ncu computes every sample its ring
+# admits: rmat20 2.685 GB over 31,000 samples; rmat18 0.768 GB over 31,000;
+# hyp4m 28.66 GB over 142,000; grid2048 715.4 GB over 56,000
+# (profiles/k_sample_rmat20_dram.md, profiles/k_sample_rmat18_full.md,
+# profiles/k_sample_hyp4m_grid2048_dram.md).
 NCU_TRAFFIC_PER_SAMPLE = {
-    ("k_sample", "rmat20"): (89_532, "6fbca8b18533ff3c"),
-    ("k_sample", "rmat18"): (26_550, "6fbca8b18533ff3c"),
-    ("k_sample", "hyp4m"): (406_867, "6fbca8b18533ff3c"),
-    ("k_sample", "grid2048"): (12_449_158, "6fbca8b18533ff3c"),
+    ("k_sample", "rmat20"): (86_613, "839ec422ce812ac4"),
+    ("k_sample", "rmat18"): (24_781, "839ec422ce812ac4"),
+    ("k_sample", "hyp4m"): (201_862, "839ec422ce812ac4"),
+    ("k_sample", "grid2048"): (12_775_125, "839ec422ce812ac4"),
 }
-KERNEL_SOURCE = {"k_sample": "kad_sample.cu"}
+KERNEL_SOURCE = {"k_sample": "kad_sample.cu", "k_wsample": "kad_wsample.cu"}
 
 
 def source_hash(kernel):
@@ -241,23 +243,28 @@ def run_reference(args):
     return 0
 
 
-def serve_graphs(count, seed=20261203):
-    """count graphs: generator = idx mod 3 (R-MAT, grid + shortcuts, hyperbolic),
-    target size n = round(10^(4 + 2u)), u uniform in [0, 1) (log-uniform 1e4..1e6)."""
+def _serve_graph(spec):
     from paper_1903_09422_gb300 import gen
+    i, kind, n_t = spec
+    if kind == 0:
+        return gen.rmat(max(4, int(round(np.log2(n_t)))), 16, seed=i + 1)
+    if kind == 1:
+        return gen.grid(max(8, int(round(np.sqrt(n_t)))), seed=i + 1)
+    return gen.hyperbolic(n_t, seed=i + 1)
+
+
+def serve_graphs(count, seed=20261203, workers=8):
+    """count graphs: generator = idx mod 3 (R-MAT, grid + shortcuts, hyperbolic),
+    target size n = round(10^(4 + 2u)), u uniform in [0, 1) (log-uniform 1e4..1e6).
+    Each graph depends only on its index; they are generated by a pool of spawned
+    processes (no CUDA state is inherited)."""
+    import multiprocessing as mpx
     rng = np.random.default_rng(seed)
-    out = []
-    for i in range(count):
-        n_t = int(round(10 ** (4 + 2 * rng.random())))
-        kind = i % 3
-        if kind == 0:
-            g = gen.rmat(max(4, int(round(np.log2(n_t)))), 16, seed=i + 1)
-        elif kind == 1:
-            g = gen.grid(max(8, int(round(np.sqrt(n_t)))), seed=i + 1)
-        else:
-            g = gen.hyperbolic(n_t, seed=i + 1)
-        out.append(g)
-    return out
+    specs = [(i, i % 3, int(round(10 ** (4 + 2 * rng.random())))) for i in range(count)]
+    if workers <= 1:
+        return [_serve_graph(s) for s in specs]
+    with mpx.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_serve_graph, specs, chunksize=1)
 
 
 def open_loop(kad, graphs, workers, qg, qe, qseed, arrivals, policy=0):
@@ -358,6 +365,51 @@ def run_serve(args):
     return 0
 
 
+def serve_specs(count, seed=20261203):
+    rng = np.random.default_rng(seed)
+    return [(i, i % 3, int(round(10 ** (4 + 2 * rng.random())))) for i in range(count)]
+
+
+def serving_record(kad, graphs, queries=300, plain_n=150, load=4.0, workers=4):
+    """A bounded sample of the serving stream for the default bench line: the
+    plain arm's back-to-back capacity (one query at a time with every sampling
+    slot) and its device-busy fraction (the sum of the queries' CUDA-event device
+    time over the wall time: overlapping queries can raise throughput by at most
+    1 / busy), then the same Poisson arrivals at `load` x that capacity, plain
+    (arrival order) against served (several workers, highest response ratio)."""
+    rng = np.random.default_rng(7)
+    qg = rng.integers(0, len(graphs), queries)
+    qe = np.array([0.05, 0.02, 0.01])[rng.integers(0, 3, queries)]
+    qseed = np.arange(1, queries + 1)
+    with kad.Server(workers=1, policy=1) as P:
+        gids = [P.add_graph(g, trusted=True) for g in graphs]
+        for q in range(min(5, queries)):
+            P.wait(P.submit(gids[qg[q]], qe[q], 0.1, int(qseed[q]), want_bc=False))
+        dev_ms = 0.0
+        t0 = time.perf_counter()
+        for q in range(plain_n):
+            r = P.wait(P.submit(gids[qg[q]], qe[q], 0.1, int(qseed[q]), want_bc=False))
+            dev_ms += r["t_total_ms"]
+        plain_s = time.perf_counter() - t0
+    cap_qps = plain_n / plain_s
+    busy = dev_ms / (1000.0 * plain_s)
+    arrivals = np.cumsum(np.random.default_rng(11).exponential(1.0 / (load * cap_qps), queries))
+
+    def summary(makespan, lat, samples):
+        return {"queries_per_s": queries / makespan, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "samples_per_s": samples / makespan}
+
+    plain = summary(*open_loop(kad, graphs, 1, qg, qe, qseed, arrivals, policy=1))
+    served = summary(*open_loop(kad, graphs, workers, qg, qe, qseed, arrivals, policy=0))
+    return {"workload": f"{len(graphs)} resident graphs (R-MAT / grid+shortcuts / hyperbolic, n log-uniform "
+                        f"1e4..1e6), {queries} queries per arm, Poisson arrivals at {load} x plain capacity, "
+                        f"eps in {{.05,.02,.01}}, delta .1 (a bounded sample of the 10,000-query stream)",
+            "plain_capacity_qps": cap_qps, "plain_device_busy": busy,
+            "overlap_bound": (1.0 / busy) if busy > 0 else None,
+            "plain": plain, "served": served, "served_over_plain": served["queries_per_s"] / plain["queries_per_s"],
+            "workers": workers}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,6 +423,7 @@ def main():
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--samples-per-block", type=int, default=0, help="> 0: the warp-per-sample kernel")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
     ap.add_argument("--eps", type=float, default=None, help="override the workload's eps (experiments)")
     ap.add_argument("--serve-graphs", type=int, default=64)
@@ -378,12 +431,21 @@ def main():
     ap.add_argument("--serve-plain", type=int, default=400, help="queries timed for the one-at-a-time baseline")
     ap.add_argument("--serve-load", default="0.5,1,2,4", help="arrival rates, as multiples of plain queries/s")
     ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving record of the default line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+
+    # the serving record's graphs are generated by spawned processes while the
+    # main measurement runs (single GPU only)
+    serve_pool = serve_async = None
+    if not args.no_serving and args.gpus == 1 and int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        import multiprocessing as mpx
+        serve_pool = mpx.get_context("spawn").Pool(8)
+        serve_async = serve_pool.map_async(_serve_graph, serve_specs(args.serve_graphs), chunksize=1)
 
     import torch
     rank, world, dist = dist_setup(args.gpus)
@@ -403,7 +465,7 @@ def main():
     if args.eps:
         eps = args.eps
     opts = dict(block_threads=args.block_threads or None, slots=args.slots or None,
-                blocks_per_sm=args.blocks_per_sm or None)
+                blocks_per_sm=args.blocks_per_sm or None, samples_per_block=args.samples_per_block or None)
     stream = torch.cuda.current_stream()
 
     # inputs resident in HBM before timing
@@ -509,7 +571,7 @@ def main():
     achieved = sum(ab) / (sum(kt) / 1000.0) / 1e9
     per_sample = sum(ab) / max(1, sum(r["samples_computed"] for r in results))
     traffic = None
-    tps, traffic_note = ncu_traffic_per_sample("k_sample", args.workload)
+    tps, traffic_note = ncu_traffic_per_sample("k_wsample" if args.samples_per_block else "k_sample", args.workload)
     if tps is not None:
         traffic = tps * statistics.mean(r["samples_computed"] for r in results)
     # DRAM bytes actually moved per second, from the ncu traffic (a separate
@@ -544,7 +606,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
                          "dram_gbs": dram_gbs, "dram_frac": (dram_gbs / peak) if dram_gbs is not None else None,
-                         "kernel": "k_sample (adaptive phase, one persistent launch)",
+                         "kernel": ("k_wsample" if r0.get("samples_per_block_used") else "k_sample") +
+                                   " (calibration + adaptive phase, one persistent launch)",
                          "alg_bytes_per_sample": per_sample, "peak_kind": f"{peak_kind} (hbm_gbs burst)",
                          "kernel_ms": statistics.median(kt)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.m),
@@ -553,13 +616,23 @@ def main():
             "phase_share": phase_share(results),
             "phase_cycles_per_sample": {k: round(v / max(1, sum(r["samples_computed"] for r in results)))
                                         for k, v in phase_total(results).items()},
-            "kernel_variant": f"{r0['block_threads_used']} threads x {r0['blocks_per_sm_used']} blocks/SM, "
-                              f"{r0['slots_used']} slots",
+            "kernel_variant": (f"warp per sample: {r0['samples_per_block_used']} samples per block of 1024 threads, "
+                               f"{r0['slots_used']} slots") if r0.get("samples_per_block_used") else
+                              (f"{r0['block_threads_used']} threads x {r0['blocks_per_sm_used']} blocks/SM, "
+                               f"{r0['slots_used']} slots"),
             "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
             "clocks": clk,
             "completion_order": co,
             "cpu_baseline": cpu,
         }
+        if serve_async is not None:
+            try:
+                graphs = serve_async.get(timeout=900)
+                line["serving"] = serving_record(kad, graphs, workers=args.serve_workers)
+            except Exception as ex:  # the record must not sink the bench line
+                line["serving"] = {"error": str(ex)}
+            finally:
+                serve_pool.close()
         print(json.dumps(line), flush=True)
     G.close()
     if dist:

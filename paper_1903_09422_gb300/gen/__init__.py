@@ -161,6 +161,7 @@ def grid_plain(rows: int, cols: int) -> CSR:
 # Named workloads: graph recipe plus the (eps, delta, seed) each is run at.
 WORKLOADS = {
     "rmat12": dict(kind="rmat", scale=12, edge_factor=8, eps=0.05, delta=0.1, seed=1),
+    "rmat15": dict(kind="rmat", scale=15, edge_factor=16, eps=0.01, delta=0.1, seed=1),
     "rmat18": dict(kind="rmat", scale=18, edge_factor=16, eps=0.01, delta=0.1, seed=1),
     "rmat20": dict(kind="rmat", scale=20, edge_factor=16, eps=0.01, delta=0.1, seed=1),
     "grid2048": dict(kind="grid", side=2048, eps=0.01, delta=0.1, seed=1),
