@@ -57,9 +57,13 @@ def _load():
             lib.orc_stream_draws.restype = None
             lib.orc_stream_words.argtypes = [u64, u64, u32, i64, vp]
             lib.orc_stream_words.restype = None
-            lib.orc_components.argtypes = [i32, vp, vp, vp]
+            lib.orc_transpose.argtypes = [i32, vp, vp, vp, vp]
+            lib.orc_transpose.restype = None
+            lib.orc_components.argtypes = [i32, vp, vp, vp, vp, vp]
             lib.orc_components.restype = i32
-            lib.orc_vd_bound.argtypes = [i32, vp, vp]
+            lib.orc_scc.argtypes = [i32, vp, vp, vp, vp, vp]
+            lib.orc_scc.restype = i32
+            lib.orc_vd_bound.argtypes = [i32, vp, vp, vp, vp]
             lib.orc_vd_bound.restype = i32
             lib.orc_omega.argtypes = [i32, dbl, dbl]
             lib.orc_omega.restype = u64
@@ -72,23 +76,52 @@ def _load():
             lib.orc_L.restype = dbl
             lib.orc_tau_star.argtypes = [vp, u64, dbl, dbl, u64]
             lib.orc_tau_star.restype = dbl
-            lib.orc_samples.argtypes = [i32, vp, vp, u64, u32, u64, i64, vp, vp, vp, vp, vp, vp, i32, vp]
+            lib.orc_samples.argtypes = [i32, vp, vp, vp, vp, u64, u32, u64, i64, vp, vp, vp, vp, vp, vp, i32, vp]
             lib.orc_samples.restype = ctypes.c_int
-            lib.orc_pair_paths.argtypes = [i32, vp, vp, i32, i32, u64, u32, i64, vp, i32, vp]
+            lib.orc_pair_paths.argtypes = [i32, vp, vp, vp, vp, i32, i32, u64, u32, i64, vp, i32, vp]
             lib.orc_pair_paths.restype = ctypes.c_int
-            lib.orc_kadabra.argtypes = [i32, vp, vp, dbl, dbl, u64, u32, u32, u64, vp, vp, vp, vp, i64,
+            lib.orc_kadabra.argtypes = [i32, vp, vp, vp, vp, dbl, dbl, u64, u32, u32, u64, vp, vp, vp, vp, i64,
                                         ctypes.POINTER(_Result)]
             lib.orc_kadabra.restype = ctypes.c_int
             _lib = lib
     return _lib
 
 
-def _csr(g):
-    rp = np.ascontiguousarray(g.row_ptr, dtype=np.int32)
-    col = np.ascontiguousarray(g.col, dtype=np.int32)
-    if col.size == 0:
-        col = np.zeros(1, dtype=np.int32)
-    return rp, col
+def _arr(x):
+    a = np.ascontiguousarray(x, dtype=np.int32)
+    return a if a.size else np.zeros(1, dtype=np.int32)
+
+
+class _Rows:
+    """A graph's CSR arrays as the C functions take them: the out-arc rows, and
+    for a directed graph (``g.directed``) the in-arc rows too (else NULL).  The
+    arrays stay referenced by this object for the duration of a call."""
+
+    def __init__(self, g, force_directed=False):
+        self.n = g.n
+        self.rp = _arr(g.row_ptr)
+        self.col = _arr(g.col)
+        self.rpT = self.colT = None
+        if getattr(g, "directed", False):
+            rpT, colT = transpose(g)
+            self.rpT, self.colT = _arr(rpT), _arr(colT)
+        elif force_directed:
+            self.rpT, self.colT = self.rp, self.col
+
+    def args(self):
+        rpT = self.rpT.ctypes.data if self.rpT is not None else None
+        colT = self.colT.ctypes.data if self.colT is not None else None
+        return (self.n, self.rp.ctypes.data, self.col.ctypes.data, rpT, colT)
+
+
+def transpose(g):
+    """The in-arc CSR (row_ptr, col) of a directed graph, rows ascending."""
+    rp, col = _arr(g.row_ptr), _arr(g.col)
+    m = int(np.asarray(g.col).size)
+    rpT = np.zeros(g.n + 1, np.int32)
+    colT = np.zeros(max(m, 1), np.int32)
+    _load().orc_transpose(g.n, rp.ctypes.data, col.ctypes.data, rpT.ctypes.data, colT.ctypes.data)
+    return rpT, colT[:m]
 
 
 def philox4x32_10(ctr, key):
@@ -114,15 +147,26 @@ def stream_draws(seed, index, domain, ms):
 
 
 def components(g):
-    rp, col = _csr(g)
+    """(count, labels): connected components, the weak ones of a directed graph."""
+    r = _Rows(g)
     comp = np.zeros(g.n, dtype=np.int32)
-    nc = _load().orc_components(g.n, rp.ctypes.data, col.ctypes.data, comp.ctypes.data)
+    nc = _load().orc_components(*r.args(), comp.ctypes.data)
     return int(nc), comp
 
 
-def vd_bound(g):
-    rp, col = _csr(g)
-    return int(_load().orc_vd_bound(g.n, rp.ctypes.data, col.ctypes.data))
+def scc(g):
+    """(count, labels): strongly connected components (labels in the order found)."""
+    r = _Rows(g, force_directed=True)
+    out = np.zeros(g.n, dtype=np.int32)
+    ns = _load().orc_scc(*r.args(), out.ctypes.data)
+    return int(ns), out
+
+
+def vd_bound(g, directed=None):
+    """The vertex-diameter bound: the undirected rule, or the directed one for
+    a directed graph (or for any graph with directed=True)."""
+    r = _Rows(g, force_directed=bool(directed))
+    return int(_load().orc_vd_bound(*r.args()))
 
 
 def omega(vd, eps, delta):
@@ -156,7 +200,7 @@ def path_cap(g):
 
 def samples(g, seed, i0, count, domain=0, cap=None):
     """Per-sample records of samples [i0, i0+count): dict of arrays."""
-    rp, col = _csr(g)
+    r = _Rows(g)
     cap = path_cap(g) if cap is None else cap
     s = np.zeros(count, np.int32)
     t = np.zeros(count, np.int32)
@@ -165,7 +209,7 @@ def samples(g, seed, i0, count, domain=0, cap=None):
     ovf = np.zeros(count, np.int32)
     paths = np.full((count, cap), -1, np.int32)
     ctr = np.zeros(6, np.uint64)
-    rc = _load().orc_samples(g.n, rp.ctypes.data, col.ctypes.data, seed, domain, i0, count, s.ctypes.data,
+    rc = _load().orc_samples(*r.args(), seed, domain, i0, count, s.ctypes.data,
                              t.ctypes.data, D.ctypes.data, sst.ctypes.data, ovf.ctypes.data, paths.ctypes.data, cap,
                              ctr.ctypes.data)
     if rc != 0:
@@ -176,12 +220,11 @@ def samples(g, seed, i0, count, domain=0, cap=None):
 
 def pair_paths(g, s, t, count, seed=1, domain=0, cap=None):
     """`count` uniform shortest s-t path draws; returns (paths[count, cap], sigma_st)."""
-    rp, col = _csr(g)
+    r = _Rows(g)
     cap = path_cap(g) if cap is None else cap
     paths = np.full((count, cap), -1, np.int32)
     sst = ctypes.c_uint64(0)
-    rc = _load().orc_pair_paths(g.n, rp.ctypes.data, col.ctypes.data, s, t, seed, domain, count, paths.ctypes.data,
-                                cap, ctypes.byref(sst))
+    rc = _load().orc_pair_paths(*r.args(), s, t, seed, domain, count, paths.ctypes.data, cap, ctypes.byref(sst))
     if rc != 0:
         raise RuntimeError(f"oracle pair_paths failed: {rc}")
     return paths, int(sst.value)
@@ -189,9 +232,9 @@ def pair_paths(g, s, t, count, seed=1, domain=0, cap=None):
 
 def kadabra(g, eps, delta, seed, epoch=1000, calib_div=100, max_epochs=0):
     """Full KADABRA run.  max_epochs > 0 truncates the adaptive phase (timing samples)."""
-    rp, col = _csr(g)
+    r = _Rows(g)
     lib = _load()
-    vd = lib.orc_vd_bound(g.n, rp.ctypes.data, col.ctypes.data)
+    vd = lib.orc_vd_bound(*r.args())
     om = lib.orc_omega(vd, eps, delta)
     t0 = lib.orc_calib_samples(om, epoch, calib_div)
     counts = np.zeros(g.n, np.uint32)
@@ -199,7 +242,7 @@ def kadabra(g, eps, delta, seed, epoch=1000, calib_div=100, max_epochs=0):
     c0 = np.zeros(g.n, np.uint32)
     Ltab = np.zeros(t0 + 1, np.float64)
     res = _Result()
-    rc = lib.orc_kadabra(g.n, rp.ctypes.data, col.ctypes.data, eps, delta, seed, epoch, calib_div, max_epochs,
+    rc = lib.orc_kadabra(*r.args(), eps, delta, seed, epoch, calib_div, max_epochs,
                          counts.ctypes.data, bc.ctypes.data, c0.ctypes.data, Ltab.ctypes.data, Ltab.size,
                          ctypes.byref(res))
     if rc != 0:

@@ -14,6 +14,10 @@
  *     g <= eps for every vertex.
  *   - Appendix C.1: same-component check before searching; the path is rebuilt
  *     from G and the distance vectors, not from a predecessor graph.
+ *   - Section 5: KADABRA also covers directed graphs.  A directed graph is given
+ *     with its in-arc rows as well; the s side searches along out-arcs, the t
+ *     side along in-arcs, components are the weak ones, and the vertex-diameter
+ *     bound goes through the strongly connected components (a READING below).
  *   - Appendix D.2 (indexed frames): random numbers depend on a sample index,
  *     not on a thread, and a stop check sees a fixed prefix of samples, which
  *     makes the result deterministic.
@@ -151,18 +155,51 @@ static uint64_t sat_mul(uint64_t a, uint64_t b) {
 }
 
 /* ------------------------------------------------------------------ graph */
+/* A graph is given by the rows each BFS side expands along: rp[0]/col[0] are
+ * the out-arcs (the s side searches forward from s), rp[1]/col[1] the in-arcs
+ * (the t side searches backward from t).  An undirected graph passes its one
+ * symmetric CSR for both.  The trace-back of side z walks the rows of the other
+ * side, 1 - z: from a vertex toward s over its in-arcs, toward t over its
+ * out-arcs. */
 typedef struct {
     int32_t n;
-    const int32_t *rp;
-    const int32_t *col;
+    const int32_t *rp[2];
+    const int32_t *col[2];
 } orc_graph;
 
-static int32_t deg(const orc_graph *g, int32_t v) { return g->rp[v + 1] - g->rp[v]; }
+static int32_t deg(const orc_graph *g, int z, int32_t v) { return g->rp[z][v + 1] - g->rp[z][v]; }
+
+static void graph_init(orc_graph *g, int32_t n, const int32_t *rp, const int32_t *col, const int32_t *rpT,
+                       const int32_t *colT) {
+    g->n = n;
+    g->rp[0] = rp;
+    g->col[0] = col;
+    g->rp[1] = rpT ? rpT : rp;
+    g->col[1] = rpT ? colT : col;
+}
+
+/* The in-arc CSR of a directed graph: row v lists every u with an arc u->v, in
+ * ascending u (a counting sort of the arcs by head, taken in tail order). */
+void orc_transpose(int32_t n, const int32_t *rp, const int32_t *col, int32_t *rpT, int32_t *colT) {
+    int32_t *fill = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    if (!fill) return;
+    for (int32_t v = 0; v <= n; v++) rpT[v] = 0;
+    for (int32_t e = 0; e < rp[n]; e++) rpT[col[e] + 1]++;
+    for (int32_t v = 0; v < n; v++) rpT[v + 1] += rpT[v];
+    for (int32_t v = 0; v <= n; v++) fill[v] = rpT[v];
+    for (int32_t u = 0; u < n; u++)
+        for (int32_t e = rp[u]; e < rp[u + 1]; e++) colT[fill[col[e]]++] = u;
+    free(fill);
+}
 
 /* Connected components by BFS in ascending id order (Appendix C.1 footnote:
- * components are computed during preprocessing).  comp[v] = index of v's
- * component, numbered by smallest member.  Returns the component count. */
-int32_t orc_components(int32_t n, const int32_t *rp, const int32_t *col, int32_t *comp) {
+ * components are computed during preprocessing); for a directed graph the weak
+ * components (arcs followed both ways), since no path joins two of them.
+ * comp[v] = index of v's component, numbered by smallest member.  Returns the
+ * component count. */
+static int32_t components(const orc_graph *g, int32_t *comp) {
+    const int32_t n = g->n;
+    const int sides = (g->rp[1] != g->rp[0]) ? 2 : 1;
     int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     if (!queue) return -1;
     for (int32_t v = 0; v < n; v++) comp[v] = -1;
@@ -174,13 +211,14 @@ int32_t orc_components(int32_t n, const int32_t *rp, const int32_t *col, int32_t
         comp[r] = nc;
         while (head < tail) {
             int32_t u = queue[head++];
-            for (int32_t e = rp[u]; e < rp[u + 1]; e++) {
-                int32_t w = col[e];
-                if (comp[w] < 0) {
-                    comp[w] = nc;
-                    queue[tail++] = w;
+            for (int z = 0; z < sides; z++)
+                for (int32_t e = g->rp[z][u]; e < g->rp[z][u + 1]; e++) {
+                    int32_t w = g->col[z][e];
+                    if (comp[w] < 0) {
+                        comp[w] = nc;
+                        queue[tail++] = w;
+                    }
                 }
-            }
         }
         nc++;
     }
@@ -188,12 +226,88 @@ int32_t orc_components(int32_t n, const int32_t *rp, const int32_t *col, int32_t
     return nc;
 }
 
+int32_t orc_components(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *rpT, const int32_t *colT,
+                       int32_t *comp) {
+    orc_graph g;
+    graph_init(&g, n, rp, col, rpT, colT);
+    return components(&g, comp);
+}
+
+/* Strongly connected components of a directed graph (Kosaraju: a depth-first
+ * search along the out-arcs lists the vertices by finishing time; searches
+ * along the in-arcs, started in decreasing finishing time, then each collect
+ * one component).  scc[v] = index of v's component in the order found.
+ * Returns the component count. */
+int32_t orc_scc(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *rpT, const int32_t *colT,
+                int32_t *scc) {
+    int32_t *order = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *stk = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *pos = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    uint8_t *seen = (uint8_t *)calloc((size_t)n, 1);
+    if (!order || !stk || !pos || !seen) {
+        free(order);
+        free(stk);
+        free(pos);
+        free(seen);
+        return -1;
+    }
+    int32_t norder = 0;
+    for (int32_t r = 0; r < n; r++) {
+        if (seen[r]) continue;
+        int32_t top = 0;
+        stk[top] = r;
+        pos[top] = rp[r];
+        seen[r] = 1;
+        while (top >= 0) {
+            int32_t v = stk[top];
+            if (pos[top] < rp[v + 1]) {
+                int32_t w = col[pos[top]++];
+                if (!seen[w]) {
+                    seen[w] = 1;
+                    top++;
+                    stk[top] = w;
+                    pos[top] = rp[w];
+                }
+            } else {
+                order[norder++] = v; /* v finishes */
+                top--;
+            }
+        }
+    }
+    for (int32_t v = 0; v < n; v++) scc[v] = -1;
+    int32_t nscc = 0;
+    for (int32_t i = n - 1; i >= 0; i--) {
+        int32_t r = order[i];
+        if (scc[r] >= 0) continue;
+        int32_t head = 0, tail = 0;
+        stk[tail++] = r;
+        scc[r] = nscc;
+        while (head < tail) {
+            int32_t u = stk[head++];
+            for (int32_t e = rpT[u]; e < rpT[u + 1]; e++) {
+                int32_t w = colT[e];
+                if (scc[w] < 0) {
+                    scc[w] = nscc;
+                    stk[tail++] = w;
+                }
+            }
+        }
+        nscc++;
+    }
+    free(order);
+    free(stk);
+    free(pos);
+    free(seen);
+    return nscc;
+}
+
 /* READING (Section 2.3: "mostly computing an upper bound on the diameter"):
  * in every component, BFS from its vertex of largest degree (smallest id on
  * ties); the component's diameter is at most 2 ecc(v0).  The vertex-diameter
  * bound is VD = max over components of 2 ecc(v0) + 1. */
-int32_t orc_vd_bound(int32_t n, const int32_t *rp, const int32_t *col) {
-    orc_graph g = {n, rp, col};
+static int32_t vd_bound_undirected(const orc_graph *g) {
+    const int32_t n = g->n;
+    const int32_t *rp = g->rp[0], *col = g->col[0];
     int32_t *comp = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     int32_t *dist = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
@@ -203,12 +317,12 @@ int32_t orc_vd_bound(int32_t n, const int32_t *rp, const int32_t *col) {
         free(queue);
         return -1;
     }
-    int32_t nc = orc_components(n, rp, col, comp);
+    int32_t nc = components(g, comp);
     int32_t *root = (int32_t *)malloc((size_t)nc * sizeof(int32_t));
     for (int32_t c = 0; c < nc; c++) root[c] = -1;
     for (int32_t v = 0; v < n; v++) {
         int32_t c = comp[v];
-        if (root[c] < 0 || deg(&g, v) > deg(&g, root[c])) root[c] = v;
+        if (root[c] < 0 || deg(g, 0, v) > deg(g, 0, root[c])) root[c] = v;
     }
     for (int32_t v = 0; v < n; v++) dist[v] = -1;
     int32_t vd = 1;
@@ -234,6 +348,109 @@ int32_t orc_vd_bound(int32_t n, const int32_t *rp, const int32_t *col) {
     free(dist);
     free(queue);
     return vd;
+}
+
+/* READING (directed graphs; Section 5 only says that KADABRA covers them, and
+ * the bound must hold for directed shortest paths, which 2 ecc does not bound):
+ * a shortest path never returns to a strongly connected component it has left,
+ * so it crosses a chain S_1 -> ... -> S_k of the components' DAG and spends a
+ * shortest sub-path inside each.  Inside S, with r_S its vertex of largest
+ * out- plus in-degree (smallest id on ties), such a sub-path x..y has
+ * d(x, y) <= d(x, r_S) + d(r_S, y), so at most w(S) = min(|S|, ecc_in(r_S) +
+ * ecc_out(r_S) + 1) vertices (eccentricities within S).  VD = the heaviest chain:
+ * max over S of B(S), B(S) = w(S) + max(0, max over arcs S -> S' of B(S')). */
+static int32_t vd_bound_directed(const orc_graph *g) {
+    const int32_t n = g->n;
+    int32_t *scc = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *dist = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!scc || !dist || !queue) {
+        free(scc);
+        free(dist);
+        free(queue);
+        return -1;
+    }
+    int32_t ns = orc_scc(n, g->rp[0], g->col[0], g->rp[1], g->col[1], scc);
+    size_t nsz = (ns > 0) ? (size_t)ns : 1;
+    int32_t *root = (int32_t *)malloc(nsz * sizeof(int32_t));
+    int32_t *size = (int32_t *)calloc(nsz, sizeof(int32_t));
+    int32_t *ecc = (int32_t *)calloc(nsz, sizeof(int32_t)); /* ecc_out + ecc_in */
+    int64_t *B = (int64_t *)malloc(nsz * sizeof(int64_t));
+    int64_t *w = (int64_t *)malloc(nsz * sizeof(int64_t));
+    if (ns < 0 || !root || !size || !ecc || !B || !w) {
+        free(scc);
+        free(dist);
+        free(queue);
+        free(root);
+        free(size);
+        free(ecc);
+        free(B);
+        free(w);
+        return -1;
+    }
+    for (int32_t c = 0; c < ns; c++) root[c] = -1;
+    for (int32_t v = 0; v < n; v++) {
+        int32_t c = scc[v];
+        size[c]++;
+        if (root[c] < 0 || deg(g, 0, v) + deg(g, 1, v) > deg(g, 0, root[c]) + deg(g, 1, root[c])) root[c] = v;
+    }
+    /* z = 0: distances from r_S along out-arcs; z = 1: to r_S, along in-arcs */
+    for (int z = 0; z < 2; z++) {
+        for (int32_t v = 0; v < n; v++) dist[v] = -1;
+        for (int32_t c = 0; c < ns; c++) {
+            int32_t head = 0, tail = 0, far = 0;
+            queue[tail++] = root[c];
+            dist[root[c]] = 0;
+            while (head < tail) {
+                int32_t u = queue[head++];
+                if (dist[u] > far) far = dist[u];
+                for (int32_t e = g->rp[z][u]; e < g->rp[z][u + 1]; e++) {
+                    int32_t x = g->col[z][e];
+                    if (scc[x] == c && dist[x] < 0) {
+                        dist[x] = dist[u] + 1;
+                        queue[tail++] = x;
+                    }
+                }
+            }
+            ecc[c] += far;
+        }
+    }
+    for (int32_t c = 0; c < ns; c++) {
+        w[c] = (ecc[c] + 1 < size[c]) ? ecc[c] + 1 : size[c];
+        B[c] = w[c];
+    }
+    /* the heaviest chain, by relaxing every arc between components until no
+     * value changes (the components' graph is acyclic, so this ends) */
+    for (int changed = 1; changed;) {
+        changed = 0;
+        for (int32_t u = 0; u < n; u++)
+            for (int32_t e = g->rp[0][u]; e < g->rp[0][u + 1]; e++) {
+                int32_t su = scc[u], sv = scc[g->col[0][e]];
+                if (su != sv && w[su] + B[sv] > B[su]) {
+                    B[su] = w[su] + B[sv];
+                    changed = 1;
+                }
+            }
+    }
+    int64_t vd = 1;
+    for (int32_t c = 0; c < ns; c++)
+        if (B[c] > vd) vd = B[c];
+    free(scc);
+    free(dist);
+    free(queue);
+    free(root);
+    free(size);
+    free(ecc);
+    free(B);
+    free(w);
+    return (int32_t)vd;
+}
+
+/* rpT == NULL: undirected (one symmetric CSR); else directed with in-arcs rpT/colT. */
+int32_t orc_vd_bound(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *rpT, const int32_t *colT) {
+    orc_graph g;
+    graph_init(&g, n, rp, col, rpT, colT);
+    return rpT ? vd_bound_directed(&g) : vd_bound_undirected(&g);
 }
 
 static int floor_log2_u64(uint64_t x) {
@@ -392,18 +609,21 @@ static int cmp_i32(const void *a, const void *b) {
  * distance vector): at cur, at distance d >= 1 on side z with path count
  * sig_cur, draw r uniform in [0, sig_cur) and take the first neighbour p, in
  * CSR (ascending) order, at distance d-1 on side z whose running sum of sigma
- * exceeds r.  This picks p with probability sigma(p)/sigma(cur). */
+ * exceeds r.  This picks p with probability sigma(p)/sigma(cur).  The
+ * neighbours toward root z are cur's row on the other side (1 - z): the tails
+ * of its in-arcs toward s, the heads of its out-arcs toward t. */
 static int32_t trace_step(orc_ws *w, orc_stream *st, int z, int32_t cur, int32_t d, uint64_t sig_cur,
                           orc_counters *ctr) {
     const orc_graph *g = w->g;
     uint64_t r = stream_uniform(st, sig_cur);
     uint64_t cum = 0;
-    for (int32_t e = g->rp[cur]; e < g->rp[cur + 1]; e++) {
-        int32_t p = g->col[e];
+    const int32_t *rp = g->rp[1 - z], *col = g->col[1 - z];
+    for (int32_t e = rp[cur]; e < rp[cur + 1]; e++) {
+        int32_t p = col[e];
         if (w->dist[z][p] != d - 1) continue;
         cum = sat_add(cum, w->sigma[z][p]);
         if (cum > r) {
-            if (ctr) ctr->trace_arcs += (uint64_t)(e - g->rp[cur] + 1);
+            if (ctr) ctr->trace_arcs += (uint64_t)(e - rp[cur] + 1);
             return p;
         }
     }
@@ -432,17 +652,19 @@ static int32_t sample_path(orc_ws *w, orc_stream *st, int32_t s, int32_t t, int3
         w->sigma[z][root[z]] = 1;
         w->front[z][0] = root[z];
         w->touched[w->ntouched++] = root[z];
-        dsum[z] = (uint64_t)deg(g, root[z]);
+        dsum[z] = (uint64_t)deg(g, z, root[z]);
     }
     int32_t nm = 0, D = 0, X = 0;
     /* READING (balanced bidirectional BFS; details deferred to the original
      * KADABRA paper in Section 2.3): each round expands the side whose current
      * frontier has the smaller degree sum, the s side on ties.  The first round
-     * that reaches a vertex labelled by the other side is the last one. */
+     * that reaches a vertex labelled by the other side is the last one.  The s
+     * side expands along out-arcs and the t side along in-arcs (the same rows
+     * when undirected), and degrees are counted in the expanding direction. */
     for (;;) {
         X = (dsum[0] <= dsum[1]) ? 0 : 1;
         int Y = 1 - X;
-        if (flen[X] == 0) break; /* no path: cannot happen once components match */
+        if (flen[X] == 0) break; /* no path (within a weak component of a directed graph) */
         int32_t nnext = 0;
         int met = 0;
         uint64_t pred_next = 0, pred_m = 0;
@@ -453,8 +675,8 @@ static int32_t sample_path(orc_ws *w, orc_stream *st, int32_t s, int32_t t, int3
         for (int32_t i = 0; i < flen[X]; i++) {
             int32_t u = w->front[X][i];
             uint64_t su = w->sigma[X][u];
-            for (int32_t e = g->rp[u]; e < g->rp[u + 1]; e++) {
-                int32_t v = g->col[e];
+            for (int32_t e = g->rp[X][u]; e < g->rp[X][u + 1]; e++) {
+                int32_t v = g->col[X][e];
                 if (w->dist[Y][v] >= 0) {
                     /* v lies in the other side's frontier (level lev[Y]). */
                     met = 1;
@@ -488,7 +710,7 @@ static int32_t sample_path(orc_ws *w, orc_stream *st, int32_t s, int32_t t, int3
         flen[X] = nnext;
         memcpy(w->front[X], w->next, (size_t)nnext * sizeof(int32_t));
         dsum[X] = 0;
-        for (int32_t i = 0; i < nnext; i++) dsum[X] += (uint64_t)deg(g, w->next[i]);
+        for (int32_t i = 0; i < nnext; i++) dsum[X] += (uint64_t)deg(g, X, w->next[i]);
     }
 
     int32_t ninterior = 0;
@@ -573,13 +795,15 @@ static void draw_pair(orc_stream *st, int32_t n, int32_t *s, int32_t *t) {
 
 /* Test hook: samples [i0, i0+count) of one domain.  Per sample: s, t, D, sigma_st,
  * overflow flag and the D-1 interior vertices (row of width cap in paths). */
-int orc_samples(int32_t n, const int32_t *rp, const int32_t *col, uint64_t seed, uint32_t domain, uint64_t i0,
-                int64_t count, int32_t *s_out, int32_t *t_out, int32_t *D_out, uint64_t *sst_out, int32_t *ovf_out,
-                int32_t *paths, int32_t cap, uint64_t *counters6) {
-    orc_graph g = {n, rp, col};
+int orc_samples(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *rpT, const int32_t *colT,
+                uint64_t seed, uint32_t domain, uint64_t i0, int64_t count, int32_t *s_out, int32_t *t_out,
+                int32_t *D_out, uint64_t *sst_out, int32_t *ovf_out, int32_t *paths, int32_t cap,
+                uint64_t *counters6) {
+    orc_graph g;
+    graph_init(&g, n, rp, col, rpT, colT);
     int32_t *comp = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     if (!comp) return -1;
-    orc_components(n, rp, col, comp);
+    components(&g, comp);
     orc_ws w;
     if (ws_init(&w, &g, comp)) {
         ws_free(&w);
@@ -621,12 +845,14 @@ int orc_samples(int32_t n, const int32_t *rp, const int32_t *col, uint64_t seed,
 
 /* Test hook: `count` path draws for a fixed pair (s, t); the stream of draw k is
  * (seed, k, domain) with no pair draw in front.  Writes interior vertices. */
-int orc_pair_paths(int32_t n, const int32_t *rp, const int32_t *col, int32_t s, int32_t t, uint64_t seed,
-                   uint32_t domain, int64_t count, int32_t *paths, int32_t cap, uint64_t *sst_out) {
-    orc_graph g = {n, rp, col};
+int orc_pair_paths(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *rpT, const int32_t *colT,
+                   int32_t s, int32_t t, uint64_t seed, uint32_t domain, int64_t count, int32_t *paths, int32_t cap,
+                   uint64_t *sst_out) {
+    orc_graph g;
+    graph_init(&g, n, rp, col, rpT, colT);
     int32_t *comp = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     if (!comp) return -1;
-    orc_components(n, rp, col, comp);
+    components(&g, comp);
     orc_ws w;
     if (ws_init(&w, &g, comp)) {
         ws_free(&w);
@@ -662,13 +888,14 @@ typedef struct {
  * Appendix B), checked every `epoch` samples (Appendix C.2: N = 1000).
  * Outputs: counts[n] (sum of x_i over the used samples), bc[n] = counts/tau,
  * c0[n] (calibration counts), Ltab[tau0+1] (log(1/delta_v) per calibration count). */
-int orc_kadabra(int32_t n, const int32_t *rp, const int32_t *col, double eps, double delta, uint64_t seed,
-                uint32_t epoch, uint32_t calib_div, uint64_t max_epochs, uint32_t *counts, double *bc, uint32_t *c0,
-                double *Ltab, int64_t Ltab_cap, orc_result *res) {
+int orc_kadabra(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *rpT, const int32_t *colT,
+                double eps, double delta, uint64_t seed, uint32_t epoch, uint32_t calib_div, uint64_t max_epochs,
+                uint32_t *counts, double *bc, uint32_t *c0, double *Ltab, int64_t Ltab_cap, orc_result *res) {
     if (n < 2 || !(eps > 0 && eps < 1) || !(delta > 0 && delta < 1) || epoch == 0 || calib_div == 0) return -3;
     memset(res, 0, sizeof(*res));
-    orc_graph g = {n, rp, col};
-    int32_t vd = orc_vd_bound(n, rp, col);
+    orc_graph g;
+    graph_init(&g, n, rp, col, rpT, colT);
+    int32_t vd = orc_vd_bound(n, rp, col, rpT, colT);
     if (vd < 0) return -1;
     uint64_t omega = orc_omega(vd, eps, delta);
     uint64_t tau0 = orc_calib_samples(omega, epoch, calib_div);
@@ -687,7 +914,7 @@ int orc_kadabra(int32_t n, const int32_t *rp, const int32_t *col, double eps, do
         free(hist);
         return -1;
     }
-    orc_components(n, rp, col, comp);
+    components(&g, comp);
     orc_ws w;
     if (ws_init(&w, &g, comp)) {
         ws_free(&w);

@@ -4,7 +4,10 @@ The paper measures on 27 real-world undirected graphs (social, hyperlink and roa
 networks; Section 4 and Appendix E).  Those are not available here, so these
 generators stand in for them.  Each returns the canonical symmetric CSR
 (``row_ptr`` int32[n+1], ``col`` int32[m], rows sorted, no self-loops, no
-duplicates), optionally reduced to the largest connected component.
+duplicates), optionally reduced to the largest connected component.  The
+directed generators (KADABRA also covers directed graphs, Section 5) return the
+out-arc CSR with ``directed`` set, reduced to the largest weakly connected
+component.
 
 This module is the only code shared by the CUDA path's tests and the oracle's:
 it produces inputs and holds none of the sampling method's arithmetic.
@@ -43,6 +46,9 @@ def _load():
             lib.gg_rmat.restype = vp
             lib.gg_rmat.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_uint64, ctypes.c_int]
+            lib.gg_rmat_directed.restype = vp
+            lib.gg_rmat_directed.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_uint64, ctypes.c_int]
             lib.gg_grid.restype = vp
             lib.gg_grid.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_int]
             lib.gg_er.restype = vp
@@ -66,10 +72,12 @@ def _load():
 
 @dataclass
 class CSR:
-    """Undirected graph as a symmetric CSR with int32 indices."""
+    """Graph as a CSR with int32 indices: symmetric when undirected, the out-arc
+    rows when ``directed``."""
     row_ptr: np.ndarray
     col: np.ndarray
     name: str = ""
+    directed: bool = False
 
     @property
     def n(self) -> int:
@@ -83,7 +91,7 @@ class CSR:
         return np.diff(self.row_ptr)
 
 
-def _take(h, name):
+def _take(h, name, directed=False):
     if not h:
         raise MemoryError("graph generator failed (invalid parameters or out of memory)")
     lib = _load()
@@ -94,13 +102,19 @@ def _take(h, name):
         lib.gg_copy(h, rp.ctypes.data, col.ctypes.data)
     finally:
         lib.gg_destroy(h)
-    return CSR(rp, col[:m], name)
+    return CSR(rp, col[:m], name, directed)
 
 
 def rmat(scale: int, edge_factor: int, a=0.57, b=0.19, c=0.19, seed: int = 1, lcc: bool = True) -> CSR:
     """R-MAT with edge_factor * 2^scale edge draws, made undirected and simple."""
     h = _load().gg_rmat(scale, edge_factor, a, b, c, seed, int(lcc))
     return _take(h, f"rmat{scale}_ef{edge_factor}_s{seed}")
+
+
+def rmat_directed(scale: int, edge_factor: int, a=0.57, b=0.19, c=0.19, seed: int = 1, lcc: bool = True) -> CSR:
+    """Directed R-MAT: each of edge_factor * 2^scale draws (u, w) gives the arc u -> w."""
+    h = _load().gg_rmat_directed(scale, edge_factor, a, b, c, seed, int(lcc))
+    return _take(h, f"rmat{scale}d_ef{edge_factor}_s{seed}", True)
 
 
 def grid(side: int, p_remove=0.05, shortcut_frac=0.001, seed: int = 1, lcc: bool = True) -> CSR:
@@ -136,6 +150,56 @@ def from_edges(n: int, edges, name: str = "custom") -> CSR:
     np.add.at(rp, u + 1, 1)
     rp = np.cumsum(rp).astype(np.int32)
     return CSR(rp, v.astype(np.int32), name)
+
+
+def from_arcs(n: int, arcs, name: str = "custom_d") -> CSR:
+    """Directed simple CSR from an arc list (self-loops and duplicates dropped)."""
+    e = np.asarray(arcs if isinstance(arcs, np.ndarray) else list(arcs), dtype=np.int64).reshape(-1, 2)
+    e = e[e[:, 0] != e[:, 1]]
+    key = np.unique(e[:, 0] * n + e[:, 1])
+    u, v = key // n, key % n
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, u + 1, 1)
+    rp = np.cumsum(rp).astype(np.int32)
+    return CSR(rp, v.astype(np.int32), name, True)
+
+
+def largest_weak_component(g: CSR) -> CSR:
+    """The directed graph induced by its largest weakly connected component
+    (ties: the one holding the smallest id), ids renumbered in order."""
+    n = g.n
+    lab = np.arange(n)
+    src = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    dst = g.col.astype(np.int64)
+    while True:  # propagate the smallest id along arcs both ways, then jump
+        new = lab.copy()
+        np.minimum.at(new, dst, new[src])
+        np.minimum.at(new, src, new[dst])
+        new = new[new]
+        if np.array_equal(new, lab):
+            break
+        lab = new
+    best = int(np.argmax(np.bincount(lab, minlength=n)))
+    keep = lab == best
+    newid = np.cumsum(keep) - 1
+    m = keep[src] & keep[dst]
+    arcs = np.stack([newid[src[m]], newid[dst[m]]], axis=1)
+    return from_arcs(int(keep.sum()), arcs, g.name + "_lwcc")
+
+
+def grid_oneway(side: int, p_oneway=0.3, seed: int = 1, lcc: bool = True) -> CSR:
+    """Directed side x side 4-neighbour grid (a street map): each edge is a
+    one-way arc, in a random direction, with probability p_oneway, else both arcs."""
+    rng = np.random.default_rng(seed)
+    ids = np.arange(side * side).reshape(side, side)
+    e = np.concatenate([np.stack([ids[:, :-1].ravel(), ids[:, 1:].ravel()], 1),
+                        np.stack([ids[:-1, :].ravel(), ids[1:, :].ravel()], 1)])
+    one = rng.random(len(e)) < p_oneway
+    flip = rng.random(len(e)) < 0.5
+    fwd = np.where((one & flip)[:, None], e[:, ::-1], e)
+    arcs = np.concatenate([fwd, e[~one][:, ::-1]])
+    g = from_arcs(side * side, arcs, f"grid{side}d_s{seed}")
+    return largest_weak_component(g) if lcc else g
 
 
 def path_graph(n: int) -> CSR:

@@ -201,8 +201,11 @@ static gg_graph *finish(int64_t n, arcvec *v, int lcc) {
 /* ---------------------------------------------------------------- generators */
 
 /* R-MAT (Chakrabarti, Zhan, Faloutsos, SDM 2004): each of edge_factor * 2^scale
- * draws picks one quadrant per id bit with probabilities (a, b, c, 1-a-b-c). */
-gg_graph *gg_rmat(int scale, int edge_factor, double a, double b, double c, uint64_t seed, int lcc) {
+ * draws picks one quadrant per id bit with probabilities (a, b, c, 1-a-b-c).
+ * Undirected: each draw u, w gives both arcs; directed: the arc u -> w only
+ * (lcc then keeps the largest weakly connected component). */
+static gg_graph *rmat_graph(int scale, int edge_factor, double a, double b, double c, uint64_t seed, int lcc,
+                            int directed) {
     if (scale < 1 || scale > 30 || edge_factor < 1) return NULL;
     arcvec v = {0};
     int64_t n = (int64_t)1 << scale;
@@ -228,12 +231,20 @@ gg_graph *gg_rmat(int scale, int edge_factor, double a, double b, double c, uint
             u = (u << 1) | ub;
             w = (w << 1) | wb;
         }
-        if (av_edge(&v, u, w)) {
+        if (directed ? (u != w && av_push(&v, ((uint64_t)u << 32) | w)) : av_edge(&v, u, w)) {
             free(v.a);
             return NULL;
         }
     }
     return finish(n, &v, lcc);
+}
+
+gg_graph *gg_rmat(int scale, int edge_factor, double a, double b, double c, uint64_t seed, int lcc) {
+    return rmat_graph(scale, edge_factor, a, b, c, seed, lcc, 0);
+}
+
+gg_graph *gg_rmat_directed(int scale, int edge_factor, double a, double b, double c, uint64_t seed, int lcc) {
+    return rmat_graph(scale, edge_factor, a, b, c, seed, lcc, 1);
 }
 
 /* side x side 4-neighbour grid, each edge removed with probability p_remove,
