@@ -472,7 +472,7 @@ def main():
     d_rp = torch.from_numpy(g.row_ptr).to(dev)
     d_col = torch.from_numpy(g.col).to(dev)
     t0 = time.perf_counter()
-    G = kad.Graph.from_device(d_rp, d_col)
+    G = kad.Graph.from_device(d_rp, d_col, directed=g.directed)
     torch.cuda.synchronize()
     setup_ms = 1000 * (time.perf_counter() - t0)
     d_bc = torch.empty(g.n, dtype=torch.float64, device=dev)
@@ -544,7 +544,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = ctypes.c_void_p()
-        st = lib.kad_graph_create(g.n, h_rp.data_ptr(), h_col.data_ptr(), 0, stream.cuda_stream, ctypes.byref(h))
+        st = lib.kad_graph_create(g.n, h_rp.data_ptr(), h_col.data_ptr(), kad.KAD_GRAPH_DIRECTED if g.directed else 0,
+                                  stream.cuda_stream, ctypes.byref(h))
         if st != 0:
             raise kad.KadError(st, "kad_graph_create")
         res = kad.Result()

@@ -49,19 +49,28 @@ typedef enum {
 typedef struct kad_graph kad_graph; /* opaque; owns a device copy of the CSR */
 
 /* Flags for kad_graph_create*. */
-#define KAD_GRAPH_TRUSTED 1u /* skip the O(m log d) symmetry/sortedness validation */
+#define KAD_GRAPH_TRUSTED 1u  /* skip the O(m log d) symmetry validation of an undirected CSR */
+#define KAD_GRAPH_DIRECTED 2u /* the CSR lists out-arcs of a directed graph (no symmetry required) */
 
 /*
- * kad_graph_create -- copy an undirected graph to the current CUDA device.
+ * kad_graph_create -- copy a graph to the current CUDA device.
  *
- * Input (host): row_ptr[n+1] and col[row_ptr[n]], int32, a symmetric CSR: every
- * undirected edge {u,v} appears as arcs u->v and v->u, each row sorted strictly
- * ascending, no self-loops, no duplicates.  n >= 2.
+ * Input (host): row_ptr[n+1] and col[row_ptr[n]], int32.  Undirected (default):
+ * a symmetric CSR, every edge {u,v} appearing as arcs u->v and v->u.  With
+ * KAD_GRAPH_DIRECTED: the out-arc rows of a directed graph (Section 5: KADABRA
+ * also covers directed graphs).  Either way each row sorted strictly ascending,
+ * no self-loops, no duplicates.  n >= 2.
  *
  * Graph set-up computes on the device (Section 2.3 preprocessing and
  * Appendix C.1): the connected components, and the vertex-diameter bound
  * VD = max over components of 2 ecc(v0) + 1, v0 = the component's vertex of
- * largest degree (smallest id on ties), by one multi-source BFS.
+ * largest degree (smallest id on ties), by one multi-source BFS.  For a directed
+ * graph: its in-arc rows (sorted; the t side of each sample searches along
+ * them), the weak components, and VD = the heaviest chain of the strongly
+ * connected components' DAG, a component S weighing min(|S|, ecc_in(r) +
+ * ecc_out(r) + 1) with r its vertex of largest out- plus in-degree (smallest id
+ * on ties) and the eccentricities taken within S.  A sample (s, t) with no
+ * directed s-t path counts, with no increments.
  * Errors: KAD_ERR_INVALID_ARG (n < 2, NULL pointer, m >= 2^31), KAD_ERR_BAD_CSR,
  * KAD_ERR_OOM, KAD_ERR_CUDA.  On error *out is NULL.
  */

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkad.so")
-SOURCES = ["kad_sample.cu", "kad_wsample.cu", "kad_shard.cu", "kad_graph.cu", "kad_api.cu", "kad_noalloc.cu"]
+SOURCES = ["kad_sample.cu", "kad_wsample.cu", "kad_sample_dir.cu", "kad_wsample_dir.cu", "kad_shard.cu",
+           "kad_graph.cu", "kad_api.cu", "kad_noalloc.cu"]
 HEADERS = ["kad_internal.cuh", "kad_device.cuh", os.path.join("..", "..", "include", "kad.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

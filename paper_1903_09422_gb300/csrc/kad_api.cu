@@ -724,8 +724,10 @@ kad_status launch_phase(kad_graph *g, Workspace &w, const SampleArgs &a, int blo
 SampleArgs base_args(kad_graph *g, const Workspace &w, uint64_t seed) {
     SampleArgs a;
     memset(&a, 0, sizeof(a));
-    a.rp = g->gd.rp;
-    a.col = g->gd.col;
+    a.rows[0] = g->gd.rp;
+    a.cols[0] = g->gd.col;
+    a.rows[1] = g->gd.rpT;
+    a.cols[1] = g->gd.colT;
     a.comp = g->gd.comp;
     a.n = g->gd.n;
     a.label = w.label;
@@ -1069,6 +1071,7 @@ kad_status create_common(int32_t n, int64_t m, const int32_t *rp, const int32_t 
     cudaGetDevice(&g->device);
     g->gd.n = n;
     g->gd.m = m;
+    g->gd.directed = (flags & KAD_GRAPH_DIRECTED) != 0;
     cudaError_t e = cudaSuccess;
     kad_status s = KAD_OK;
     if (kad_pool_alloc((void **)&g->gd.rp, ((size_t)n + 1) * 4, st) != cudaSuccess ||
@@ -1094,6 +1097,10 @@ kad_status create_common(int32_t n, int64_t m, const int32_t *rp, const int32_t 
     if (vd < 1 || vd >= (1 << 27)) {
         kad_graph_free(g);
         return KAD_ERR_INVALID_ARG;
+    }
+    if (!g->gd.directed) { // one symmetric CSR serves both sides
+        g->gd.rpT = g->gd.rp;
+        g->gd.colT = g->gd.col;
     }
     g->vd = vd;
     g->ncomp = nc;
@@ -1307,6 +1314,8 @@ void kad_graph_free(kad_graph *g) {
     if (g->gd.rp) cudaFreeAsync(g->gd.rp, 0);
     if (g->gd.col) cudaFreeAsync(g->gd.col, 0);
     if (g->gd.comp) cudaFreeAsync(g->gd.comp, 0);
+    if (g->gd.directed && g->gd.rpT) cudaFreeAsync(g->gd.rpT, 0);
+    if (g->gd.directed && g->gd.colT) cudaFreeAsync(g->gd.colT, 0);
     cudaSetDevice(cur);
     delete g;
 }

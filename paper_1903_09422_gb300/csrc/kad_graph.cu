@@ -2,7 +2,11 @@
 // vertex-diameter bound that fixes omega (Section 2.3 preprocessing: "mostly
 // computing an upper bound on the diameter"; Appendix C.1: components are
 // computed with it so that pairs in different components can be skipped).
+// Directed graphs (Section 5: KADABRA also covers them) get their in-arc rows,
+// weak components and a bound through the strongly connected components
+// (setup_directed below).
 //
+// Undirected:
 // VD = max over components C of 2 ecc_C(v0_C) + 1, with v0_C the vertex of
 // largest degree in C (smallest id on ties).  One multi-source BFS from all
 // v0_C at once computes every ecc_C, since the components are disjoint.  The
@@ -235,14 +239,16 @@ __global__ void k_cc_probe(const int32_t *parent, int32_t n, int32_t *out, int c
         out[i] = parent[(int)(((int64_t)i * n) / count)];
 }
 
+// `skip`: leading arcs of each row already linked by the sampling rounds (the
+// in-arc rows of a directed graph had none linked: 0).
 __global__ void k_cc_rest(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
-                          int32_t *parent, int *err, int big) {
+                          int32_t *parent, int *err, int big, int skip) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
         if (*(volatile int32_t *)(parent + v) == big) continue; // inside the large tree
         const int a = rp[v], b = rp[v + 1];
-        for (int e = a + 2 + lane; e < b; e += 32) cc_link(parent, v, col[e], n, err);
+        for (int e = a + skip + lane; e < b; e += 32) cc_link(parent, v, col[e], n, err);
     }
 }
 
@@ -338,6 +344,376 @@ __global__ void k_bfs_bu(const int32_t *__restrict__ rp, const int32_t *__restri
     }
 }
 
+// ------------------------------------------------ directed graphs
+// The in-arc rows (the rows the t side expands along): a count of each head's
+// arcs, a scan, a scatter, and a sort of every row, so that rows are ascending
+// like the out-arc rows (the trace-back walks them in id order).
+
+__global__ void k_tr_count(const int32_t *__restrict__ col, int64_t m, int32_t *cnt1) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt1 + col[e], 1);
+}
+
+// In-place inclusive scan of x[0, len) in tiles of KAD_SCAN_TILE (1024 threads x
+// 4 items): tiles scanned alone, then the tile sums, then the offsets added.
+#define KAD_SCAN_TILE 4096
+__device__ __forceinline__ int block_excl_scan_1024(int v, int *wsum, int &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w; // inclusive per warp
+    }
+    __syncthreads();
+    total = wsum[31];
+    const int before = (wid > 0) ? wsum[wid - 1] : 0;
+    __syncthreads(); // wsum is reused by the next call
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(int32_t *x, int64_t len, int32_t *tile_sum) {
+    __shared__ int wsum[32];
+    const int64_t base = (int64_t)blockIdx.x * KAD_SCAN_TILE + 4 * threadIdx.x;
+    int v[4], run = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        v[k] = (base + k < len) ? x[base + k] : 0;
+        run += v[k];
+        v[k] = run; // inclusive within the thread
+    }
+    int total;
+    const int off = block_excl_scan_1024(run, wsum, total);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (base + k < len) x[base + k] = v[k] + off;
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+// one block: tile sums to exclusive offsets
+__global__ void __launch_bounds__(1024) k_scan_sums(int32_t *tile_sum, int ntiles) {
+    __shared__ int wsum[32];
+    int carry = 0;
+    for (int b = 0; b < ntiles; b += 1024) {
+        const int i = b + (int)threadIdx.x;
+        const int v = (i < ntiles) ? tile_sum[i] : 0;
+        int total;
+        const int ex = block_excl_scan_1024(v, wsum, total);
+        if (i < ntiles) tile_sum[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void k_scan_add(int32_t *x, int64_t len, const int32_t *__restrict__ tile_sum) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += tile_sum[i / KAD_SCAN_TILE];
+}
+
+// every arc u -> v into a free place of row v (warp per tail u)
+__global__ void k_tr_fill(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t n,
+                          const int32_t *__restrict__ rpT, int32_t *cursor, int32_t *colT) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps)
+        for (int e = rp[u] + lane; e < rp[u + 1]; e += 32) {
+            const int v = col[e];
+            colT[rpT[v] + atomicAdd(cursor + v, 1)] = u;
+        }
+}
+
+// Rows of up to 32 arcs are sorted by their thread (insertion sort); longer
+// ones are listed for the block sorts: up to KAD_SORT_MID arcs, else big.
+#define KAD_SORT_MID 4096
+__global__ void k_tr_sort_small(const int32_t *__restrict__ rpT, int32_t *colT, int32_t n, int32_t *mid,
+                                int *nmid, int32_t *big, int *nbig) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int a = rpT[v], len = rpT[v + 1] - a;
+        if (len > KAD_SORT_MID) {
+            big[atomicAdd(nbig, 1)] = v;
+        } else if (len > 32) {
+            mid[atomicAdd(nmid, 1)] = v;
+        } else if (len > 1) {
+            int buf[32];
+            for (int i = 0; i < len; i++) {
+                const int x = colT[a + i];
+                int j = i;
+                while (j > 0 && buf[j - 1] > x) {
+                    buf[j] = buf[j - 1];
+                    j--;
+                }
+                buf[j] = x;
+            }
+            for (int i = 0; i < len; i++) colT[a + i] = buf[i];
+        }
+    }
+}
+
+// a block per listed row: bitonic sort in shared memory, padded to a power of two
+__global__ void __launch_bounds__(1024) k_tr_sort_mid(const int32_t *__restrict__ rpT, int32_t *colT,
+                                                      const int32_t *__restrict__ mid, int nmid) {
+    __shared__ int sh[KAD_SORT_MID];
+    for (int r = blockIdx.x; r < nmid; r += gridDim.x) {
+        const int v = mid[r];
+        const int a = rpT[v], len = rpT[v + 1] - a;
+        int P = 64;
+        while (P < len) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) sh[i] = (i < len) ? colT[a + i] : 0x7fffffff;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const int x = sh[i], y = sh[ixj];
+                        const bool up = (i & k) == 0;
+                        if ((x > y) == up) {
+                            sh[i] = y;
+                            sh[ixj] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = threadIdx.x; i < len; i += blockDim.x) colT[a + i] = sh[i];
+        __syncthreads();
+    }
+}
+
+// a block per listed long row: the row's ids marked in a bitmap over all n
+// vertices (its own slice of `bits`), then read back in id order
+__global__ void __launch_bounds__(1024) k_tr_sort_big(const int32_t *__restrict__ rpT, int32_t *colT,
+                                                      const int32_t *__restrict__ big, int nbig, int32_t n,
+                                                      uint32_t *bits) {
+    __shared__ int wsum[32];
+    const int words = (n + 31) >> 5;
+    uint32_t *mine = bits + (size_t)blockIdx.x * (size_t)words;
+    for (int r = blockIdx.x; r < nbig; r += gridDim.x) {
+        const int v = big[r];
+        const int a = rpT[v], len = rpT[v + 1] - a;
+        for (int i = threadIdx.x; i < words; i += blockDim.x) mine[i] = 0u;
+        __syncthreads();
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+            const int x = colT[a + i];
+            atomicOr(mine + (x >> 5), 1u << (x & 31));
+        }
+        __syncthreads();
+        int carry = 0;
+        for (int b = 0; b < words; b += 1024) {
+            const int i = b + (int)threadIdx.x;
+            const uint32_t w = (i < words) ? mine[i] : 0u;
+            int total;
+            int pos = carry + block_excl_scan_1024(__popc(w), wsum, total);
+            for (uint32_t q = w; q; q &= q - 1) colT[a + pos++] = (i << 5) + __ffs(q) - 1;
+            carry += total;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------ strongly connected components
+// scc[v] = -1 while unassigned, else the id of its component's colour root.
+// A component is assigned whole, so a vertex whose unassigned in-neighbours (or
+// out-neighbours) are none is a component of its own (trim).
+__device__ __forceinline__ bool any_unassigned(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                               const int32_t *scc, int v) {
+    for (int e = rp[v]; e < rp[v + 1]; e++)
+        if (*(volatile const int32_t *)(scc + col[e]) < 0) return true;
+    return false;
+}
+
+__global__ void k_scc_trim(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                           const int32_t *__restrict__ rpT, const int32_t *__restrict__ colT, int32_t n, int32_t *scc,
+                           int *count) {
+    int c = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (scc[v] >= 0) continue;
+        if (!any_unassigned(rpT, colT, scc, v) || !any_unassigned(rp, col, scc, v)) {
+            scc[v] = v;
+            c++;
+        }
+    }
+    if (c) atomicAdd(count, c);
+}
+
+// colour[v] = v for the unassigned; all of them start active
+__global__ void k_scc_color_init(const int32_t *__restrict__ scc, int32_t n, int32_t *color, int32_t *q, int *qlen) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (scc[v] < 0) {
+            color[v] = v;
+            q[atomicAdd(qlen, 1)] = v;
+        }
+}
+
+// colours flow forward along arcs between unassigned vertices, the larger one
+// winning: at the fixed point colour[v] is the largest id among the unassigned
+// vertices that reach v (warp per active vertex; a raised vertex is active in
+// the next step, once: stamp)
+__global__ void k_scc_color_push(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 const int32_t *__restrict__ q, int qlen, const int32_t *scc, int32_t *color,
+                                 int32_t *stamp, int step, int32_t *nq, int *nqlen) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < qlen; i += warps) {
+        const int u = q[i];
+        const int c = *(volatile int32_t *)(color + u);
+        for (int e = rp[u] + lane; e < rp[u + 1]; e += 32) {
+            const int x = col[e];
+            if (*(volatile const int32_t *)(scc + x) >= 0 || *(volatile int32_t *)(color + x) >= c) continue;
+            if (atomicMax(color + x, c) < c && atomicExch(stamp + x, step) != step) nq[atomicAdd(nqlen, 1)] = x;
+        }
+    }
+}
+
+// the roots: unassigned vertices that keep their own colour
+__global__ void k_scc_roots(int32_t *scc, const int32_t *__restrict__ color, int32_t n, int32_t *q, int *qlen) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (scc[v] < 0 && color[v] == v) {
+            scc[v] = v;
+            q[atomicAdd(qlen, 1)] = v;
+        }
+}
+
+// backward from every root among vertices of its colour: the vertices of that
+// colour that reach the root are exactly its strongly connected component
+__global__ void k_scc_back(const int32_t *__restrict__ rpT, const int32_t *__restrict__ colT,
+                           const int32_t *__restrict__ q, int qlen, int32_t *scc, const int32_t *__restrict__ color,
+                           int32_t *nq, int *nqlen) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < qlen; i += warps) {
+        const int v = q[i];
+        const int c = color[v];
+        for (int e = rpT[v] + lane; e < rpT[v + 1]; e += 32) {
+            const int u = colT[e];
+            if (color[u] == c && *(volatile int32_t *)(scc + u) < 0 && atomicCAS(scc + u, -1, c) == -1)
+                nq[atomicAdd(nqlen, 1)] = u;
+        }
+    }
+}
+
+// per component (indexed by its label): size, and the root r_S of largest
+// out- plus in-degree, smallest id on ties, as (deg << 32) | ~v
+__global__ void k_scc_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ rpT,
+                            const int32_t *__restrict__ scc, int32_t n, int32_t *size, unsigned long long *best,
+                            int *maxdeg, int *err) {
+    int md = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int s = scc[v];
+        if (s < 0 || s >= n) { // every vertex is assigned by now; checked, not assumed
+            atomicOr(err, GERR_CC);
+            continue;
+        }
+        const uint32_t d = (uint32_t)(rp[v + 1] - rp[v]) + (uint32_t)(rpT[v + 1] - rpT[v]);
+        atomicAdd(size + s, 1);
+        atomicMax(best + s, ((unsigned long long)d << 32) | (0xffffffffu - (uint32_t)v));
+        md = ((int)d > md) ? (int)d : md;
+    }
+    md = __reduce_max_sync(0xffffffffu, md);
+    if ((threadIdx.x & 31) == 0 && md) atomicMax(maxdeg, md);
+}
+
+// how many v have lab[v] == v (component labels: one per component)
+__global__ void k_count_self(const int32_t *__restrict__ lab, int32_t n, int *count) {
+    int c = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) c += (lab[v] == v);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+__global__ void k_scc_seed(const int32_t *__restrict__ scc, const unsigned long long *__restrict__ best, int32_t n,
+                           int32_t *dist, int32_t *q, int *qlen) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (scc[v] == v) {
+            const int r = (int)(0xffffffffu - (uint32_t)(best[v] & 0xffffffffull));
+            dist[r] = 0;
+            q[atomicAdd(qlen, 1)] = r;
+        }
+}
+
+// one BFS level from every component's root at once, over arcs inside the
+// component (rows: out-arcs for ecc_out, in-arcs for ecc_in); ecc[label] is
+// raised to the level reached
+__global__ void k_scc_bfs(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                          const int32_t *__restrict__ scc, const int32_t *__restrict__ q, int qlen, int parts,
+                          int32_t *dist, int level, int32_t *ecc, int32_t *nq, int *nqlen) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int64_t items = (int64_t)qlen * parts;
+    for (int64_t it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += warps) {
+        const int i = (int)(it / parts), part = (int)(it % parts);
+        const int u = q[i];
+        const int s = scc[u];
+        bool any = false;
+        for (int e = rp[u] + 32 * part + lane; e < rp[u + 1]; e += 32 * parts) {
+            const int x = col[e];
+            if (scc[x] == s && *(volatile int32_t *)(dist + x) < 0 && atomicCAS(dist + x, -1, level + 1) == -1) {
+                nq[atomicAdd(nqlen, 1)] = x;
+                any = true;
+            }
+        }
+        if (__any_sync(0xffffffffu, any) && lane == 0) atomicMax(ecc + s, level + 1);
+    }
+}
+
+// w(S) = min(|S|, ecc_in + ecc_out + 1); B(S) starts at w(S)
+__global__ void k_scc_weight(const int32_t *__restrict__ scc, int32_t n, const int32_t *__restrict__ size,
+                             const int32_t *__restrict__ e_out, const int32_t *__restrict__ e_in, int32_t *w,
+                             int32_t *B) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (scc[v] == v) {
+            const int64_t x = (int64_t)e_out[v] + e_in[v] + 1;
+            w[v] = (x < size[v]) ? (int32_t)x : size[v];
+            B[v] = w[v];
+        }
+}
+
+// one relaxation of B(S) = w(S) + max over arcs S -> S' of B(S') (warp per
+// vertex); sets *changed when some B grew.  Repeated until nothing changes: the
+// components' graph is acyclic, so B stops at the heaviest chain below S.
+__global__ void k_scc_chain(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            const int32_t *__restrict__ scc, int32_t n, const int32_t *__restrict__ w, int32_t *B,
+                            int *changed) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int su = scc[u];
+        if (su < 0 || su >= n) continue; // (k_scc_stats has flagged it)
+        int best = 0;
+        for (int e = rp[u] + lane; e < rp[u + 1]; e += 32) {
+            const int sv = scc[col[e]];
+            if (sv != su && sv >= 0 && sv < n) {
+                const int b = *(volatile int32_t *)(B + sv);
+                best = (b > best) ? b : best;
+            }
+        }
+        best = __reduce_max_sync(0xffffffffu, best);
+        if (lane == 0 && best > 0) {
+            const int cand = w[su] + best;
+            if (cand > *(volatile int32_t *)(B + su) && atomicMax(B + su, cand) < cand) atomicOr(changed, 1);
+        }
+    }
+}
+
+__global__ void k_scc_vd(const int32_t *__restrict__ scc, const int32_t *__restrict__ B, int32_t n, int *vd,
+                         int *nscc) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (scc[v] == v) {
+            atomicMax(vd, B[v]);
+            atomicAdd(nscc, 1);
+        }
+}
+
 int grid_for(int64_t work, int threads, int cap) {
     int64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -356,6 +732,257 @@ int grid_for(int64_t work, int threads, int cap) {
             goto done;                                                                                                \
         }                                                                                                             \
     } while (0)
+
+// Directed graph set-up, after the out-arc rows were validated: the in-arc rows
+// (sorted), the weak components (the pair check of Appendix C.1: no path joins
+// two of them), and the vertex-diameter bound through the strongly connected
+// components -- a shortest path runs through a chain S_1 -> ... -> S_k of the
+// components' DAG and spends at most w(S) = min(|S|, ecc_in(r_S) + ecc_out(r_S) + 1)
+// vertices in each, r_S the vertex of largest out- plus in-degree (smallest id
+// on ties), so VD = the heaviest chain.  The components come from colour
+// propagation (each unassigned vertex takes the largest id that reaches it;
+// the vertices of a colour that reach its root form the root's component),
+// after trimming vertices with no unassigned in- or out-neighbour.  Every loop
+// below ends: each pass of the outer loop assigns at least the largest
+// unassigned id, and each inner loop runs until its frontier is empty.
+kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_out, int32_t *ncomp_out, int32_t *maxdeg_out,
+                          cudaError_t *cerr) {
+    const int32_t n = gd.n;
+    const int64_t m = gd.m;
+    const int T = 256;
+    const int gv = grid_for(n, T, 65535);
+    const int gw = grid_for((int64_t)n * 32, T, 65535);
+    const int ga = grid_for(m, T, 65535);
+    const int ntiles = (int)(((int64_t)n + 1 + KAD_SCAN_TILE - 1) / KAD_SCAN_TILE);
+    const size_t a4 = (((size_t)n * 4) + 255) & ~(size_t)255, a8 = (((size_t)n * 8) + 255) & ~(size_t)255;
+    const size_t at = (((size_t)ntiles * 4) + 255) & ~(size_t)255;
+    kad_status status = KAD_OK;
+    char *scratch = nullptr;
+    uint32_t *bits = nullptr;
+    int *d_cnt = nullptr; // [0] error flags, [1..3] counters, [4] changed, [5] vd, [6] count, [7] largest degree
+    int32_t *parent, *scc, *color, *stamp, *q0, *q1, *dist, *size, *e_out, *e_in, *wt, *B, *tiles;
+    unsigned long long *best;
+    int h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int nmid = 0, nbig = 0, remaining = n, step = 0, qlen = 0, level = 0;
+    int32_t *qa, *qb;
+    if (kad_pool_alloc((void **)&scratch, 256 + 12 * a4 + a8 + at, st) != cudaSuccess ||
+        kad_pool_alloc((void **)&gd.rpT, ((size_t)n + 1) * 4, st) != cudaSuccess ||
+        kad_pool_alloc((void **)&gd.colT, (size_t)(m > 0 ? m : 1) * 4, st) != cudaSuccess) {
+        cudaGetLastError();
+        status = KAD_ERR_OOM;
+        goto done;
+    }
+    d_cnt = (int *)scratch;
+    parent = (int32_t *)(scratch + 256);
+    scc = (int32_t *)(scratch + 256 + a4);
+    color = (int32_t *)(scratch + 256 + 2 * a4);
+    stamp = (int32_t *)(scratch + 256 + 3 * a4);
+    q0 = (int32_t *)(scratch + 256 + 4 * a4);
+    q1 = (int32_t *)(scratch + 256 + 5 * a4);
+    dist = (int32_t *)(scratch + 256 + 6 * a4);
+    size = (int32_t *)(scratch + 256 + 7 * a4);
+    e_out = (int32_t *)(scratch + 256 + 8 * a4);
+    e_in = (int32_t *)(scratch + 256 + 9 * a4);
+    wt = (int32_t *)(scratch + 256 + 10 * a4);
+    B = (int32_t *)(scratch + 256 + 11 * a4);
+    best = (unsigned long long *)(scratch + 256 + 12 * a4);
+    tiles = (int32_t *)(scratch + 256 + 12 * a4 + a8);
+    GCHK(cudaMemsetAsync(d_cnt, 0, 8 * sizeof(int), st));
+
+    // ---- in-arc rows: counts, scan, scatter, per-row sort
+    GCHK(cudaMemsetAsync(gd.rpT, 0, ((size_t)n + 1) * 4, st));
+    k_tr_count<<<ga, T, 0, st>>>(gd.col, m, gd.rpT + 1);
+    k_scan_tiles<<<ntiles, 1024, 0, st>>>(gd.rpT, (int64_t)n + 1, tiles);
+    k_scan_sums<<<1, 1024, 0, st>>>(tiles, ntiles);
+    k_scan_add<<<grid_for((int64_t)n + 1, T, 65535), T, 0, st>>>(gd.rpT, (int64_t)n + 1, tiles);
+    GCHK(cudaMemsetAsync(parent, 0, (size_t)n * 4, st)); // the scatter cursors
+    k_tr_fill<<<gw, T, 0, st>>>(gd.rp, gd.col, n, gd.rpT, parent, gd.colT);
+    k_tr_sort_small<<<gv, T, 0, st>>>(gd.rpT, gd.colT, n, q0, d_cnt + 1, q1, d_cnt + 2);
+    GCHK(cudaGetLastError());
+    GCHK(cudaMemcpyAsync(h, d_cnt, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaStreamSynchronize(st));
+    nmid = h[1];
+    nbig = h[2];
+    if (nmid > 0) k_tr_sort_mid<<<(nmid < 2048 ? nmid : 2048), 1024, 0, st>>>(gd.rpT, gd.colT, q0, nmid);
+    if (nbig > 0) {
+        const int gb = nbig < 64 ? nbig : 64;
+        if (kad_pool_alloc((void **)&bits, (size_t)gb * (size_t)((n + 31) / 32) * 4, st) != cudaSuccess) {
+            cudaGetLastError();
+            status = KAD_ERR_OOM;
+            goto done;
+        }
+        k_tr_sort_big<<<gb, 1024, 0, st>>>(gd.rpT, gd.colT, q1, nbig, n, bits);
+    }
+    GCHK(cudaGetLastError());
+
+    // ---- weak components: union-find over the out-arc and the in-arc rows
+    k_cc_init<<<gv, T, 0, st>>>(parent, n);
+    for (int r = 0; r < 2; r++) k_cc_sample<<<gv, T, 0, st>>>(gd.rp, gd.col, n, parent, d_cnt, r);
+    k_cc_compress<<<gv, T, 0, st>>>(parent, n);
+    {
+        const int probes = (n < 1024) ? n : 1024;
+        int32_t h_probe[1024];
+        k_cc_probe<<<(probes + T - 1) / T, T, 0, st>>>(parent, n, q0, probes);
+        GCHK(cudaGetLastError());
+        GCHK(cudaMemcpyAsync(h_probe, q0, (size_t)probes * 4, cudaMemcpyDeviceToHost, st));
+        GCHK(cudaStreamSynchronize(st));
+        std::sort(h_probe, h_probe + probes);
+        int big = h_probe[0], best_run = 0;
+        for (int i = 0; i < probes;) {
+            int j = i;
+            while (j < probes && h_probe[j] == h_probe[i]) j++;
+            if (j - i > best_run) {
+                best_run = j - i;
+                big = h_probe[i];
+            }
+            i = j;
+        }
+        // an arc with an endpoint outside the large tree is linked from that
+        // endpoint: from the tail's out-arc row or from the head's in-arc row
+        k_cc_rest<<<gw, T, 0, st>>>(gd.rp, gd.col, n, parent, d_cnt, big, 2);
+        k_cc_rest<<<gw, T, 0, st>>>(gd.rpT, gd.colT, n, parent, d_cnt, big, 0);
+    }
+    k_cc_flatten<<<gv, T, 0, st>>>(parent, gd.comp, n);
+    k_count_self<<<gv, T, 0, st>>>(gd.comp, n, d_cnt + 6);
+    GCHK(cudaGetLastError());
+    GCHK(cudaMemcpyAsync(h, d_cnt, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaStreamSynchronize(st));
+    if (h[0] & GERR_CC) {
+        status = KAD_ERR_INTERNAL;
+        goto done;
+    }
+    *ncomp_out = h[6];
+
+    // ---- strongly connected components
+    k_fill<<<gv, T, 0, st>>>(scc, n, -1);
+    k_fill<<<gv, T, 0, st>>>(stamp, n, -1);
+    GCHK(cudaGetLastError());
+    for (int outer = 0; remaining > 0; outer++) {
+        if (outer > n) { // cannot happen: every pass assigns the largest unassigned id
+            status = KAD_ERR_INTERNAL;
+            goto done;
+        }
+        for (int pass = 0; pass < 4 && remaining > 0; pass++) {
+            GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
+            k_scc_trim<<<gv, T, 0, st>>>(gd.rp, gd.col, gd.rpT, gd.colT, n, scc, d_cnt + 1);
+            GCHK(cudaGetLastError());
+            GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GCHK(cudaStreamSynchronize(st));
+            remaining -= h[1];
+            if (h[1] == 0) break;
+        }
+        if (remaining <= 0) break;
+        GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
+        k_scc_color_init<<<gv, T, 0, st>>>(scc, n, color, q0, d_cnt + 1);
+        GCHK(cudaGetLastError());
+        GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GCHK(cudaStreamSynchronize(st));
+        qlen = h[1];
+        qa = q0;
+        qb = q1;
+        while (qlen > 0) {
+            GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
+            k_scc_color_push<<<grid_for((int64_t)qlen * 32, T, 65535), T, 0, st>>>(gd.rp, gd.col, qa, qlen, scc, color,
+                                                                                   stamp, step++, qb, d_cnt + 1);
+            GCHK(cudaGetLastError());
+            GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GCHK(cudaStreamSynchronize(st));
+            qlen = h[1];
+            int32_t *t = qa;
+            qa = qb;
+            qb = t;
+        }
+        GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
+        k_scc_roots<<<gv, T, 0, st>>>(scc, color, n, q0, d_cnt + 1);
+        GCHK(cudaGetLastError());
+        GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GCHK(cudaStreamSynchronize(st));
+        qlen = h[1];
+        remaining -= qlen;
+        qa = q0;
+        qb = q1;
+        while (qlen > 0) {
+            GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
+            k_scc_back<<<grid_for((int64_t)qlen * 32, T, 65535), T, 0, st>>>(gd.rpT, gd.colT, qa, qlen, scc, color, qb,
+                                                                             d_cnt + 1);
+            GCHK(cudaGetLastError());
+            GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GCHK(cudaStreamSynchronize(st));
+            qlen = h[1];
+            remaining -= qlen;
+            int32_t *t = qa;
+            qa = qb;
+            qb = t;
+        }
+    }
+
+    // ---- per component: size, root, eccentricities within it, weight
+    GCHK(cudaMemsetAsync(size, 0, (size_t)n * 4, st));
+    GCHK(cudaMemsetAsync(best, 0, (size_t)n * 8, st));
+    GCHK(cudaMemsetAsync(e_out, 0, (size_t)n * 4, st));
+    GCHK(cudaMemsetAsync(e_in, 0, (size_t)n * 4, st));
+    k_scc_stats<<<gv, T, 0, st>>>(gd.rp, gd.rpT, scc, n, size, best, d_cnt + 7, d_cnt);
+    GCHK(cudaGetLastError());
+    GCHK(cudaMemcpyAsync(h, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaStreamSynchronize(st));
+    if (h[0]) {
+        status = KAD_ERR_INTERNAL;
+        goto done;
+    }
+    for (int z = 0; z < 2; z++) {
+        const int32_t *rows = z ? gd.rpT : gd.rp, *cols = z ? gd.colT : gd.col;
+        k_fill<<<gv, T, 0, st>>>(dist, n, -1);
+        GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
+        k_scc_seed<<<gv, T, 0, st>>>(scc, best, n, dist, q0, d_cnt + 1);
+        GCHK(cudaGetLastError());
+        GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GCHK(cudaStreamSynchronize(st));
+        qlen = h[1];
+        qa = q0;
+        qb = q1;
+        for (level = 0; qlen > 0; level++) {
+            const int parts = (qlen >= 9728) ? 1 : (9728 + qlen - 1) / qlen;
+            GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
+            k_scc_bfs<<<grid_for((int64_t)qlen * parts * 32, T, 65535), T, 0, st>>>(
+                rows, cols, scc, qa, qlen, parts, dist, level, z ? e_in : e_out, qb, d_cnt + 1);
+            GCHK(cudaGetLastError());
+            GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GCHK(cudaStreamSynchronize(st));
+            qlen = h[1];
+            int32_t *t = qa;
+            qa = qb;
+            qb = t;
+        }
+    }
+    k_scc_weight<<<gv, T, 0, st>>>(scc, n, size, e_out, e_in, wt, B);
+    GCHK(cudaGetLastError());
+
+    // ---- the heaviest chain
+    for (int pass = 0;; pass++) {
+        if (pass > n) { // cannot happen: each pass lengthens the chains it changes
+            status = KAD_ERR_INTERNAL;
+            goto done;
+        }
+        GCHK(cudaMemsetAsync(d_cnt + 4, 0, sizeof(int), st));
+        k_scc_chain<<<gw, T, 0, st>>>(gd.rp, gd.col, scc, n, wt, B, d_cnt + 4);
+        GCHK(cudaGetLastError());
+        GCHK(cudaMemcpyAsync(h + 4, d_cnt + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GCHK(cudaStreamSynchronize(st));
+        if (!h[4]) break;
+    }
+    GCHK(cudaMemsetAsync(d_cnt + 5, 0, 2 * sizeof(int), st));
+    k_scc_vd<<<gv, T, 0, st>>>(scc, B, n, d_cnt + 5, d_cnt + 6);
+    GCHK(cudaGetLastError());
+    GCHK(cudaMemcpyAsync(h, d_cnt, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaStreamSynchronize(st));
+    *vd_out = h[5] > 1 ? h[5] : 1;
+    *maxdeg_out = h[7];
+
+done:
+    if (bits) cudaFreeAsync(bits, st);
+    if (scratch) cudaFreeAsync(scratch, st);
+    return status;
+}
 
 kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int32_t *vd_out, int32_t *ncomp_out,
                            int32_t *maxdeg_out,
@@ -400,6 +1027,10 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
         status = KAD_ERR_BAD_CSR;
         goto done;
     }
+    if (gd.directed) {
+        status = setup_directed(gd, st, vd_out, ncomp_out, maxdeg_out, cerr);
+        goto done;
+    }
     if (!(flags & KAD_GRAPH_TRUSTED)) {
         k_validate_sym<<<grid_for((gd.m + KAD_SYM_CHUNK - 1) / KAD_SYM_CHUNK, T, 65535), T, 0, st>>>(
             gd.rp, gd.col, n, gd.m, d_flags, (unsigned long long *)(d_flags + 4));
@@ -436,7 +1067,7 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
             }
             i = j;
         }
-        k_cc_rest<<<gw, T, 0, st>>>(gd.rp, gd.col, n, parent, d_flags, big);
+        k_cc_rest<<<gw, T, 0, st>>>(gd.rp, gd.col, n, parent, d_flags, big, 2);
     }
     k_cc_flatten<<<gv, T, 0, st>>>(parent, gd.comp, n);
     GCHK(cudaGetLastError());

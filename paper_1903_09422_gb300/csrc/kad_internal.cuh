@@ -71,8 +71,13 @@ struct KadHostPage {
 
 // Arguments of the sampling kernel.
 struct SampleArgs {
-    const int32_t *rp;
-    const int32_t *col;
+    // rows[0]/cols[0]: the out-arc rows (the s side expands along them, the t
+    // side traces back over them); rows[1]/cols[1]: the in-arc rows (the t side
+    // expands, the s side traces back); the same arrays for an undirected graph.
+    // Indexed by side, so a kernel reads the pointer it needs from the
+    // parameter space at the point of use.
+    const int32_t *rows[2];
+    const int32_t *cols[2];
     const int32_t *comp;
     int32_t n;
     // per-slot scratch, slot-major: slot k uses [k*n, (k+1)*n) of each array; the
@@ -142,6 +147,27 @@ struct SampleArgs {
     unsigned long long *work;
 };
 
+// Rows of side z (0: s, 1: t) in the direction it expands, and in the direction
+// its trace-back walks toward its root (the other side's expansion rows).  The
+// sampling kernels are compiled twice: with KAD_DIRECTED 1 (kad_*_dir.cu) the
+// sides read their own rows; the undirected build reads rows[0] for both, so
+// its code is that of a one-CSR kernel.
+#ifndef KAD_DIRECTED
+#define KAD_DIRECTED 0
+#endif
+static __device__ __forceinline__ const int32_t *xrp(const SampleArgs &a, int z) {
+    return KAD_DIRECTED ? a.rows[z] : a.rows[0];
+}
+static __device__ __forceinline__ const int32_t *xcol(const SampleArgs &a, int z) {
+    return KAD_DIRECTED ? a.cols[z] : a.cols[0];
+}
+static __device__ __forceinline__ const int32_t *trp(const SampleArgs &a, int z) {
+    return KAD_DIRECTED ? a.rows[z ^ 1] : a.rows[0];
+}
+static __device__ __forceinline__ const int32_t *tcol(const SampleArgs &a, int z) {
+    return KAD_DIRECTED ? a.cols[z ^ 1] : a.cols[0];
+}
+
 // ----------------------------------------------------------------- helpers
 __device__ __forceinline__ unsigned long long kad_sat_add(unsigned long long a, unsigned long long b) {
     unsigned long long s = a + b;
@@ -186,6 +212,11 @@ int kad_sample_max_blocks_per_sm(int threads, int per_sm, size_t dyn_smem);
 // the warp-per-sample kernel (kad_wsample.cu): 1024 threads, one block per SM,
 // a.nctx contexts per block, dyn_smem = a.nctx x a.nw words of bitmap
 cudaError_t kad_launch_wsample(const SampleArgs &a, int blocks, size_t dyn_smem, cudaStream_t st);
+// the directed-graph builds (kad_sample_dir.cu, kad_wsample_dir.cu); the launchers
+// above hand a directed graph (rows[1] != rows[0]) to them
+cudaError_t kad_launch_sample_directed(const SampleArgs &a, int blocks, int threads, int per_sm, size_t dyn_smem,
+                                       cudaStream_t st);
+cudaError_t kad_launch_wsample_directed(const SampleArgs &a, int blocks, size_t dyn_smem, cudaStream_t st);
 size_t kad_wsample_static_smem();
 int kad_wsample_max_blocks_per_sm(size_t dyn_smem);
 // the sharded run's fold of all ranks' path rows and its stop check (kad_shard.cu)
@@ -199,12 +230,17 @@ cudaError_t kad_launch_fg(const uint32_t *counts, const uint32_t *c0, const doub
                           unsigned long long tau, unsigned long long omega, double *f, double *g, cudaStream_t st);
 
 // graph set-up (kad_graph.cu)
+// rp/col: the out-arc rows (the s side expands along them); rpT/colT: the
+// in-arc rows (the t side's), the same arrays when the graph is undirected.
 struct KadGraphDev {
     int32_t n;
     int64_t m;
     int32_t *rp;
     int32_t *col;
     int32_t *comp;
+    int32_t *rpT;
+    int32_t *colT;
+    bool directed;
 };
 kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int32_t *vd, int32_t *ncomp, int32_t *maxdeg,
                            cudaError_t *cerr);

@@ -133,8 +133,8 @@ extern "C" kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row
 
     SampleArgs a;
     memset(&a, 0, sizeof(a));
-    a.rp = d_row_ptr;
-    a.col = d_col;
+    a.rows[0] = a.rows[1] = d_row_ptr; // an undirected graph: in-arc rows = out-arc rows
+    a.cols[0] = a.cols[1] = d_col;
     a.comp = d_comp ? d_comp : zero_comp;
     a.n = n;
     a.label = label;

@@ -204,6 +204,7 @@ __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *
     const int lane = threadIdx.x & 31;
     const uint32_t key = (z ? KAD_SIDE : 0u) | (uint32_t)d; // level d-1
     const bool direct = nobits || reC - rsC <= 32;
+    const int32_t *trow = trp(a, z), *tc = tcol(a, z);
     unsigned long long carry = 0;
     for (int base = rsC; base < reC; base += 128) {
         int pp[4];
@@ -211,7 +212,7 @@ __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const int e = base + 32 * k + lane;
-            pp[k] = (e < reC) ? __ldg(a.col + e) : -1;
+            pp[k] = (e < reC) ? __ldg(tc + e) : -1;
         }
         if (direct) {
 #pragma unroll
@@ -231,8 +232,8 @@ __device__ __forceinline__ void trace_scan(const SampleArgs &a, const uint32_t *
             rk[k] = ek[k] = 0;
             if (pp[k] >= 0 && (lp[k] & KAD_KEY) == key) {
                 wk[k] = (lp[k] & KAD_OVF) ? KAD_U64MAX : kad_ld_u64(sig_at(label, pp[k]));
-                rk[k] = __ldg(a.rp + pp[k]);
-                ek[k] = __ldg(a.rp + pp[k] + 1);
+                rk[k] = __ldg(trow + pp[k]);
+                ek[k] = __ldg(trow + pp[k] + 1);
             }
         }
         // the running sums item by item (a loop, so that the scan exists once)
@@ -290,14 +291,19 @@ __device__ __forceinline__ void team_from_level(const SampleArgs &a, Smem<BLOCK>
     const int lane = threadIdx.x & 31, tw = tl >> 5;
     const int j = tl / G, sub = tl % G;
     const bool mine = j < lcnt;
+    // p precedes cur on side z when cur is in p's expansion row (side z's
+    // direction), equivalently p in cur's trace row [rsC, reC): search the shorter
     int p = -1, lo = 0, hi = 0, key = 0;
+    const int32_t *scol = tcol(a, z);
     if (mine) {
         p = __ldcg(list + phys(z, ls + j, n));
-        const int rsP = __ldg(a.rp + p), reP = __ldg(a.rp + p + 1);
+        const int32_t *xr = xrp(a, z);
+        const int rsP = __ldg(xr + p), reP = __ldg(xr + p + 1);
         if (reP - rsP <= reC - rsC) {
             lo = rsP;
             hi = reP;
             key = cur;
+            scol = xcol(a, z);
         } else {
             lo = rsC;
             hi = reC;
@@ -310,7 +316,7 @@ __device__ __forceinline__ void team_from_level(const SampleArgs &a, Smem<BLOCK>
         const int len = hi - lo;
         if (!done && len <= G) {
             // the last few positions: one per thread of the group
-            found = sub < len && __ldg(a.col + lo + sub) == key;
+            found = sub < len && __ldg(scol + lo + sub) == key;
             probes += (sub < len) ? 1 : 0;
             done = true;
         }
@@ -320,7 +326,7 @@ __device__ __forceinline__ void team_from_level(const SampleArgs &a, Smem<BLOCK>
         const bool probe = !done && sub < P;
         if (probe) {
             q = lo + (int)(((long long)len * (sub + 1)) / (P + 1));
-            v = __ldg(a.col + q);
+            v = __ldg(scol + q);
             probes++;
         }
         int nlo = (probe && v < key) ? q + 1 : -0x7fffffff;
@@ -397,7 +403,7 @@ __device__ __forceinline__ void team_from_level(const SampleArgs &a, Smem<BLOCK>
 }
 
 // Trace one side z of the sample from the meeting vertex `cur` (distance d,
-// path count sc, row [rsC, reC)) back to its root with team t (half of the
+// path count sc) back to its root with team t (half of the
 // block).  Per step the team leader draws a bounded number from the stream (its
 // copy of it); each chosen vertex goes out directly (buf_v == nullptr) or into
 // buf_v/buf_j for later.  The candidates of a step are the neighbours of cur at
@@ -411,12 +417,14 @@ template <int BLOCK>
 __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> &sm, Stream &st, int t,
                                                const uint32_t *label, bool bsh, bool nobits, int gs, const uint32_t *bits,
                                                const int32_t *list, int n, int z, int d,
-                                               unsigned long long sc, int cur, int rsC, int reC, int D, int32_t *out,
+                                               unsigned long long sc, int cur, int D, int32_t *out,
                                                int32_t *buf_v, int32_t *buf_j, unsigned long long &w_trace) {
     constexpr int TT = BLOCK / 2, TW = TT / 32;
     const int tl = (int)threadIdx.x - t * TT;
     const int lane = threadIdx.x & 31, tw = tl >> 5;
     const bool leader = tl == 0;
+    // cur's row toward root z: its in-arcs on the s side, its out-arcs on the t side
+    int rsC = __ldg(trp(a, z) + cur), reC = __ldg(trp(a, z) + cur + 1);
     int nb = 0, par = 0;
     while (d >= 1) {
         if (d == 1) {
@@ -441,8 +449,8 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
                 if (lane == 0) {
                     sm.t_p[t] = p_sel;
                     sm.t_s[t] = s_sel;
-                    sm.t_rs[t] = (p_sel >= 0) ? __ldg(a.rp + p_sel) : 0;
-                    sm.t_re[t] = (p_sel >= 0) ? __ldg(a.rp + p_sel + 1) : 0;
+                    sm.t_rs[t] = (p_sel >= 0) ? __ldg(trp(a, z) + p_sel) : 0;
+                    sm.t_re[t] = (p_sel >= 0) ? __ldg(trp(a, z) + p_sel + 1) : 0;
                 }
             }
             team_bar(t, TT);
@@ -478,7 +486,7 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
                 uint32_t lp[KAD_TITEMS];
                 unsigned long long wk[KAD_TITEMS];
 #pragma unroll
-                for (int k = 0; k < KAD_TITEMS; k++) pp[k] = (e0 + k < reC) ? __ldg(a.col + e0 + k) : -1;
+                for (int k = 0; k < KAD_TITEMS; k++) pp[k] = (e0 + k < reC) ? __ldg(tcol(a, z) + e0 + k) : -1;
                 if (direct) {
 #pragma unroll
                     for (int k = 0; k < KAD_TITEMS; k++) lp[k] = (pp[k] >= 0) ? kad_ld_u32(lab_at(label, pp[k])) : 0u;
@@ -536,8 +544,8 @@ __device__ __forceinline__ int trace_side_team(const SampleArgs &a, Smem<BLOCK> 
                     if (hit == sel) {
                         sm.t_p[t] = hp;
                         sm.t_s[t] = hs;
-                        sm.t_rs[t] = __ldg(a.rp + hp);
-                        sm.t_re[t] = __ldg(a.rp + hp + 1);
+                        sm.t_rs[t] = __ldg(trp(a, z) + hp);
+                        sm.t_re[t] = __ldg(trp(a, z) + hp + 1);
                     }
                     team_bar(t, TT);
                     p_sel = sm.t_p[t];
@@ -634,7 +642,7 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
                 else
                     hi = mid - 1;
             }
-            vv[k] = __ldg(a.col + sm.rs[lo] + (e - sm.off[lo]));
+            vv[k] = __ldg(xcol(a, c.X) + sm.rs[lo] + (e - sm.off[lo]));
             ix[k] = lo;
         }
     }
@@ -726,8 +734,8 @@ __device__ __forceinline__ bool expand_items(const SampleArgs &a, Smem<BLOCK> &s
     for (int k = 0; k < KAD_ITEMS; k++) {
         rs0[k] = rs1[k] = 0;
         if (fresh[k] && kind[k] == 1) {
-            rs0[k] = __ldg(a.rp + vv[k]);
-            rs1[k] = __ldg(a.rp + vv[k] + 1);
+            rs0[k] = __ldg(xrp(a, c.X) + vv[k]);
+            rs1[k] = __ldg(xrp(a, c.X) + vv[k] + 1);
         }
     }
     bool claimed[KAD_ITEMS];
@@ -800,7 +808,7 @@ __device__ __forceinline__ bool probe_items(const SampleArgs &a, Smem<BLOCK> &sm
                 else
                     hi = mid - 1;
             }
-            vv[k] = __ldg(a.col + sm.rs[lo] + (e - sm.off[lo]));
+            vv[k] = __ldg(xcol(a, c.X) + sm.rs[lo] + (e - sm.off[lo]));
             ix[k] = lo;
         }
     }
@@ -949,16 +957,20 @@ __device__ __noinline__ void pairs_many(const SampleArgs &a, Smem<BLOCK> &sm, co
                                         unsigned long long *sigma2, int32_t *mext_id, int mcap, int mext, int Y,
                                         int yb, int fx, long long np, int n, int rb, unsigned long long &pred_m) {
     const int tid = threadIdx.x;
+    // u in F_X has an arc toward w in F_Y when w is in u's row (X's direction)
+    // or u in w's row (Y's direction)
+    const int32_t *xcX = xcol(a, 1 - Y), *xcY = xcol(a, Y), *xrY = xrp(a, Y);
     // four pairs per thread and step, their binary searches interleaved
     for (long long p0 = tid; p0 < np; p0 += 4ll * BLOCK) {
         int pi[4], pw[4], lo[4], hi[4], key[4];
-        bool hit[4];
+        bool hit[4], inU[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const long long p = p0 + (long long)k * BLOCK;
             pi[k] = -1;
             pw[k] = -1;
             hit[k] = false;
+            inU[k] = false;
             lo[k] = hi[k] = key[k] = 0;
             if (p < np) {
                 pi[k] = (int)(p % fx);
@@ -968,12 +980,13 @@ __device__ __noinline__ void pairs_many(const SampleArgs &a, Smem<BLOCK> &sm, co
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             if (pw[k] < 0) continue;
-            const int rsW = __ldg(a.rp + pw[k]), reW = __ldg(a.rp + pw[k] + 1);
+            const int rsW = __ldg(xrY + pw[k]), reW = __ldg(xrY + pw[k] + 1);
             const int rsU = sm.rs[pi[k]], reU = sm.off[pi[k]];
             if (reU - rsU <= reW - rsW) { // search w in the row of u
                 lo[k] = rsU;
                 hi[k] = reU;
                 key[k] = pw[k];
+                inU[k] = true;
             } else { // search u in the row of w
                 lo[k] = rsW;
                 hi[k] = reW;
@@ -987,7 +1000,7 @@ __device__ __noinline__ void pairs_many(const SampleArgs &a, Smem<BLOCK> &sm, co
                 if (hit[k] || lo[k] >= hi[k]) continue;
                 any = true;
                 const int mid = (lo[k] + hi[k]) >> 1;
-                const int v = __ldg(a.col + mid);
+                const int v = __ldg((inU[k] ? xcX : xcY) + mid);
                 if (v < key[k])
                     lo[k] = mid + 1;
                 else if (v > key[k])
@@ -1224,10 +1237,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 sm.lev[0] = sm.lev[1] = 0;
                 sm.lvs[0][0] = sm.lvs[1][0] = 0;
                 sm.lvs[0][1] = sm.lvs[1][1] = 1;
-                sm.root_rs[0] = __ldg(a.rp + s);
-                sm.root_rs[1] = __ldg(a.rp + t);
-                sm.dsum[0] = (unsigned long long)(__ldg(a.rp + s + 1) - sm.root_rs[0]);
-                sm.dsum[1] = (unsigned long long)(__ldg(a.rp + t + 1) - sm.root_rs[1]);
+                // each root's row in its side's direction: out-arcs of s, in-arcs of t
+                sm.root_rs[0] = __ldg(a.rows[0] + s);
+                sm.root_rs[1] = __ldg(a.rows[1] + t);
+                sm.dsum[0] = (unsigned long long)(__ldg(a.rows[0] + s + 1) - sm.root_rs[0]);
+                sm.dsum[1] = (unsigned long long)(__ldg(a.rows[1] + t + 1) - sm.root_rs[1]);
                 sm.D = -1; // searching
                 // round 0: its flags, and its expansion counted ahead (one root)
                 sm.met[0] = 0;
@@ -1285,8 +1299,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     unsigned long long su;
                     ld_vs(label, u, lu, su);
                     sm.uid[tid] = u;
-                    sm.rs[tid] = __ldg(a.rp + u);
-                    sm.off[tid] = __ldg(a.rp + u + 1);
+                    sm.rs[tid] = __ldg(xrp(a, X) + u);
+                    sm.off[tid] = __ldg(xrp(a, X) + u + 1);
                     sm.sig[tid] = sig_val(lu, su);
                 }
                 __syncthreads();
@@ -1299,11 +1313,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     while (G < 32 && 2 * G * np <= BLOCK) G *= 2;
                     const int sub = tid & (G - 1);
                     const long long p = tid / G;
+                    // an arc from u in F_X toward w in F_Y: w in u's row (X's
+                    // direction) or u in w's row (Y's direction)
                     int pi = -1, pw = -1, lo = 0, hi = 0, key = 0;
+                    bool inW = false; // searching w's row (else u's)
                     if (p < np) {
                         pi = (int)(p % fx);
                         pw = __ldcg(list + phys(Y, yb + (int)(p / fx), n));
-                        const int rsW = __ldg(a.rp + pw), reW = __ldg(a.rp + pw + 1);
+                        const int rsW = __ldg(xrp(a, Y) + pw), reW = __ldg(xrp(a, Y) + pw + 1);
                         const int rsU = sm.rs[pi], reU = sm.off[pi];
                         if (reU - rsU <= reW - rsW) {
                             lo = rsU;
@@ -1313,6 +1330,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                             lo = rsW;
                             hi = reW;
                             key = sm.uid[pi];
+                            inW = true;
                         }
                     }
                     const int P = (G > 1) ? G - 1 : 1;
@@ -1325,7 +1343,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
 #pragma unroll
                             for (int k = 0; k < 4; k++) {
                                 const int q = lo + sub + k * G;
-                                if (q < hi && __ldg(a.col + q) == key) found = true;
+                                if (q < hi && __ldg(xcol(a, inW ? Y : X) + q) == key) found = true;
                             }
                             done = true;
                         }
@@ -1333,7 +1351,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                         const bool probe = !done && sub < P;
                         if (probe) {
                             q = lo + (int)(((long long)len * (sub + 1)) >> lgP1);
-                            v = __ldg(a.col + q);
+                            v = __ldg(xcol(a, inW ? Y : X) + q);
                         }
                         int nlo = (probe && v < key) ? q + 1 : -0x7fffffff;
                         int nhi = (probe && v > key) ? q : 0x7fffffff;
@@ -1400,7 +1418,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     }
                 } else if (tid < cnt) {
                     const int u = __ldcg(list + phys(X, cb + tid, n));
-                    const int rs = __ldg(a.rp + u), re = __ldg(a.rp + u + 1);
+                    const int rs = __ldg(xrp(a, X) + u), re = __ldg(xrp(a, X) + u + 1);
                     uint32_t lu;
                     unsigned long long su;
                     ld_vs(label, u, lu, su);
@@ -1702,7 +1720,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
         if (D > 0 && !traced && tid == 0) kad_set_err(a.ctl, KAD_DERR_SELECT);
         int dz[2] = {0, 0};
         unsigned long long gz[2] = {0, 0};
-        int rsM = 0, reM = 0;
         constexpr int TT = BLOCK / 2;
         const int team = tid / TT, tl = tid - team * TT;
         if (traced) {
@@ -1720,8 +1737,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             dz[1] = (X == 1) ? dX : dY;
             gz[0] = (X == 0) ? gX : gY;
             gz[1] = (X == 1) ? gX : gY;
-            rsM = __ldg(a.rp + mid);
-            reM = __ldg(a.rp + mid + 1);
         }
         const bool spec = traced && dz[1] <= KAD_TBUF && !(a.debug & KAD_DEBUG_SERIAL_TRACE);
         if (spec && team == 1 && tl == 0) {
@@ -1761,7 +1776,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 unsigned long long wt = 0;
                 if (z == 0 && tl == 0) emit(a, out, D, dz[0], mid);
                 const int nb = trace_side_team<BLOCK>(a, sm, st, team, label, bsh, nobits, gs, bits, list, n, z,
-                                                      z ? dz[1] : dz[0], z ? gz[1] : gz[0], mid, rsM, reM, D, out,
+                                                      z ? dz[1] : dz[0], z ? gz[1] : gz[0], mid, D, out,
                                                       buffered ? sm.tbuf_v : nullptr, buffered ? sm.tbuf_j : nullptr, wt);
                 if (tl == 0) {
                     if (buffered) {
@@ -1925,9 +1940,16 @@ __global__ void k_fg(const uint32_t *__restrict__ counts, const uint32_t *__rest
 // register budget is sized for (64K registers per SM).
 #define KAD_VARIANTS(X) X(128, 4) X(128, 8) X(256, 2) X(256, 4) X(512, 1) X(512, 2) X(1024, 1)
 
+#if KAD_DIRECTED
+cudaError_t kad_launch_sample_directed(const SampleArgs &a, int blocks, int threads, int per_sm, size_t dyn_smem,
+                                       cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+#else
 cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, int per_sm, size_t dyn_smem,
                               cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
+    if (a.rows[1] != a.rows[0]) return kad_launch_sample_directed(a, blocks, threads, per_sm, dyn_smem, st);
+#endif
 #define KAD_LAUNCH(T, B)                                                                                              \
     if (threads == T && per_sm == B) {                                                                                \
         if (dyn_smem > 0) {                                                                                           \
@@ -1942,6 +1964,8 @@ cudaError_t kad_launch_sample(const SampleArgs &a, int blocks, int threads, int 
 #undef KAD_LAUNCH
     return cudaErrorInvalidConfiguration;
 }
+
+#if !KAD_DIRECTED // one copy of the queries and the other kernels' launchers
 
 bool kad_sample_variant_exists(int threads, int per_sm) {
 #define KAD_HAS(T, B)                                                                                                 \
@@ -1993,3 +2017,4 @@ cudaError_t kad_launch_fg(const uint32_t *counts, const uint32_t *c0, const doub
     k_fg<<<blocks, threads, 0, st>>>(counts, c0, ltab, n, tau, omega, f, g);
     return cudaGetLastError();
 }
+#endif // !KAD_DIRECTED

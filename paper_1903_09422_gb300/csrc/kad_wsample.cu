@@ -196,6 +196,7 @@ __device__ __noinline__ bool w_expand_pass(const SampleArgs &a, WShared &S, int 
     const bool probe = vload(C.probe) != 0;
     const int cnt = W.cnt;
     const uint32_t sideX = C.sideX, keyNext = C.keyNext;
+    const int X = C.X; // side X's rows (its direction) are a.rows[X], a.cols[X]
     int vv[W_ITEMS], ix[W_ITEMS];
     uint32_t ll[W_ITEMS];
 #pragma unroll
@@ -212,7 +213,7 @@ __device__ __noinline__ bool w_expand_pass(const SampleArgs &a, WShared &S, int 
                 else
                     hi = mid - 1;
             }
-            vv[k] = __ldg(a.col + W.u.ch.rs[lo] + (e - W.u.ch.off[lo]));
+            vv[k] = __ldg(xcol(a, X) + W.u.ch.rs[lo] + (e - W.u.ch.off[lo]));
             ix[k] = lo;
         }
     }
@@ -280,8 +281,8 @@ __device__ __noinline__ bool w_expand_pass(const SampleArgs &a, WShared &S, int 
     for (int k = 0; k < W_ITEMS; k++) {
         rs0[k] = rs1[k] = 0;
         if (fresh[k] && kind[k] == 1) {
-            rs0[k] = __ldg(a.rp + vv[k]);
-            rs1[k] = __ldg(a.rp + vv[k] + 1);
+            rs0[k] = __ldg(xrp(a, X) + vv[k]);
+            rs1[k] = __ldg(xrp(a, X) + vv[k] + 1);
         }
     }
     bool claimed[W_ITEMS];
@@ -319,7 +320,7 @@ __device__ __noinline__ bool w_expand_pass(const SampleArgs &a, WShared &S, int 
         if (claimed[k]) mydeg += (unsigned long long)(rs1[k] - rs0[k]);
     }
     if (nclaim) {
-        const int X = C.X, tailY = C.tailY, n = a.n;
+        const int tailY = C.tailY, n = a.n;
         int pos0 = 0;
         if (lane == 0) pos0 = atomicAdd(&C.tail[X], nclaim);
         pos0 = __shfl_sync(FULL_MASK, pos0, 0);
@@ -364,17 +365,20 @@ __device__ __noinline__ void w_pair_range(const SampleArgs &a, WShared &S, int c
     const int lane = threadIdx.x & 31;
     const int fx = C.pfx, yb = C.pyb, Y = 1 - C.X, n = a.n;
     const int mcap = (a.mcap < W_MC) ? a.mcap : W_MC;
+    // u in F_X has an arc toward w in F_Y when w is in u's row (X's direction)
+    // or u in w's row (Y's direction)
     unsigned long long pm = 0;
     for (int q0 = p0; q0 < p1; q0 += 128) {
         if (vload(C.abort)) break;
         int pi[4], pw[4], lo[4], hi[4], key[4];
-        bool hit[4];
+        bool hit[4], inU[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const int p = q0 + lane + 32 * k;
             pi[k] = -1;
             pw[k] = -1;
             hit[k] = false;
+            inU[k] = false;
             lo[k] = hi[k] = key[k] = 0;
             if (p < p1) {
                 pi[k] = p % fx;
@@ -384,12 +388,13 @@ __device__ __noinline__ void w_pair_range(const SampleArgs &a, WShared &S, int c
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             if (pw[k] < 0) continue;
-            const int rsW = __ldg(a.rp + pw[k]), reW = __ldg(a.rp + pw[k] + 1);
+            const int rsW = __ldg(xrp(a, Y) + pw[k]), reW = __ldg(xrp(a, Y) + pw[k] + 1);
             const int rsU = F.u.ch.rs[pi[k]], reU = F.u.ch.re[pi[k]];
             if (reU - rsU <= reW - rsW) {
                 lo[k] = rsU;
                 hi[k] = reU;
                 key[k] = pw[k];
+                inU[k] = true;
             } else {
                 lo[k] = rsW;
                 hi[k] = reW;
@@ -403,7 +408,7 @@ __device__ __noinline__ void w_pair_range(const SampleArgs &a, WShared &S, int c
                 if (hit[k] || lo[k] >= hi[k]) continue;
                 any = true;
                 const int mid = (lo[k] + hi[k]) >> 1;
-                const int v = __ldg(a.col + mid);
+                const int v = __ldg(xcol(a, inU[k] ? 1 - Y : Y) + mid);
                 if (v < key[k])
                     lo[k] = mid + 1;
                 else if (v > key[k])
@@ -456,7 +461,7 @@ __device__ __forceinline__ void w_build_chunk(const SampleArgs &a, WShared &S, i
         }
     } else if (lane < cnt) {
         const int u = __ldcg(sl.list + phys(X, j0 + lane, a.n));
-        const int rs = __ldg(a.rp + u), re = __ldg(a.rp + u + 1);
+        const int rs = __ldg(xrp(a, X) + u), re = __ldg(xrp(a, X) + u + 1);
         uint32_t lu;
         unsigned long long su;
         ld_vs(sl.label, u, lu, su);
@@ -701,8 +706,8 @@ __device__ __noinline__ void w_search(const SampleArgs &a, WShared &S, int c) {
                 unsigned long long su;
                 ld_vs(sl.label, u, lu, su);
                 W.u.ch.uid[lane] = u;
-                W.u.ch.rs[lane] = __ldg(a.rp + u);
-                W.u.ch.re[lane] = __ldg(a.rp + u + 1);
+                W.u.ch.rs[lane] = __ldg(xrp(a, X) + u);
+                W.u.ch.re[lane] = __ldg(xrp(a, X) + u + 1);
                 W.u.ch.sig[lane] = sig_val(lu, su);
             }
             if (lane == 0) {
@@ -923,14 +928,18 @@ __device__ __forceinline__ void w_from_level(const SampleArgs &a, WShared &S, in
     for (int base = 0; base < lcnt; base += per) {
         const int j = base + j_sub;
         const bool mine = j < lcnt;
+        // p precedes cur on side z when cur is in p's row in side z's
+        // direction, equivalently p in cur's trace row [rsC, reC)
         int p = -1, lo = 0, hi = 0, key = 0;
+        const int32_t *scol = tcol(a, z);
         if (mine) {
             p = __ldcg(sl.list + phys(z, ls + j, n));
-            const int rsP = __ldg(a.rp + p), reP = __ldg(a.rp + p + 1);
+            const int rsP = __ldg(xrp(a, z) + p), reP = __ldg(xrp(a, z) + p + 1);
             if (reP - rsP <= reC - rsC) {
                 lo = rsP;
                 hi = reP;
                 key = cur;
+                scol = xcol(a, z);
             } else {
                 lo = rsC;
                 hi = reC;
@@ -941,7 +950,7 @@ __device__ __forceinline__ void w_from_level(const SampleArgs &a, WShared &S, in
         while (__any_sync(FULL_MASK, !done)) {
             const int len = hi - lo;
             if (!done && len <= G) {
-                found = sub < len && __ldg(a.col + lo + sub) == key;
+                found = sub < len && __ldg(scol + lo + sub) == key;
                 probes += (sub < len) ? 1 : 0;
                 done = true;
             }
@@ -949,7 +958,7 @@ __device__ __forceinline__ void w_from_level(const SampleArgs &a, WShared &S, in
             const bool probe = !done && sub < P;
             if (probe) {
                 q = lo + (int)(((long long)len * (sub + 1)) >> lgP1);
-                v = __ldg(a.col + q);
+                v = __ldg(scol + q);
                 probes++;
             }
             int nlo = (probe && v < key) ? q + 1 : -0x7fffffff;
@@ -1038,7 +1047,7 @@ __device__ __forceinline__ void w_trace_scan(const SampleArgs &a, const Slot &sl
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const int e = base + 32 * k + lane;
-            pp[k] = (e < reC) ? __ldg(a.col + e) : -1;
+            pp[k] = (e < reC) ? __ldg(tcol(a, z) + e) : -1;
         }
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -1091,7 +1100,8 @@ __device__ __noinline__ bool w_trace_side(const SampleArgs &a, WShared &S, int c
                              unsigned long long sc, int cur, int D, int32_t *out) {
     WCtx &C = S.c[c];
     const int lane = threadIdx.x & 31;
-    int rsC = __ldg(a.rp + cur), reC = __ldg(a.rp + cur + 1);
+    // rows toward root z: in-arcs for s, out-arcs for t
+    int rsC = __ldg(trp(a, z) + cur), reC = __ldg(trp(a, z) + cur + 1);
     unsigned long long wtr = 0;
     while (d >= 1) {
         unsigned long long r = 0;
@@ -1117,8 +1127,8 @@ __device__ __noinline__ bool w_trace_side(const SampleArgs &a, WShared &S, int c
         if (d >= 1 && lane == 0) emit(a, out, D, (z == 0) ? d : D - d, p_sel);
         cur = p_sel;
         sc = s_sel;
-        rsC = __ldg(a.rp + cur);
-        reC = __ldg(a.rp + cur + 1);
+        rsC = __ldg(trp(a, z) + cur);
+        reC = __ldg(trp(a, z) + cur + 1);
     }
     if (lane == 0) C.acc[4] += wtr;
     return true;
@@ -1299,10 +1309,11 @@ __device__ void w_owner(const SampleArgs &a, WShared &S, int c) {
                 C.lev[0] = C.lev[1] = 0;
                 C.lvs[0][0] = C.lvs[1][0] = 0;
                 C.lvs[0][1] = C.lvs[1][1] = 1;
-                C.root_rs[0] = __ldg(a.rp + s);
-                C.root_rs[1] = __ldg(a.rp + t);
-                C.dsum[0] = (unsigned long long)(__ldg(a.rp + s + 1) - C.root_rs[0]);
-                C.dsum[1] = (unsigned long long)(__ldg(a.rp + t + 1) - C.root_rs[1]);
+                // each root's row in its side's direction: out-arcs of s, in-arcs of t
+                C.root_rs[0] = __ldg(a.rows[0] + s);
+                C.root_rs[1] = __ldg(a.rows[1] + t);
+                C.dsum[0] = (unsigned long long)(__ldg(a.rows[0] + s + 1) - C.root_rs[0]);
+                C.dsum[1] = (unsigned long long)(__ldg(a.rows[1] + t + 1) - C.root_rs[1]);
                 C.D = -1; // searching
             }
             __threadfence_block();
@@ -1540,16 +1551,24 @@ __global__ void __launch_bounds__(W_THREADS, 1) k_wsample(const SampleArgs a) {
 } // namespace
 
 // ---------------------------------------------------------------- launchers
+#if KAD_DIRECTED
+cudaError_t kad_launch_wsample_directed(const SampleArgs &a, int blocks, size_t dyn_smem, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+#else
 size_t kad_wsample_static_smem() { return sizeof(WShared); }
 
 cudaError_t kad_launch_wsample(const SampleArgs &a, int blocks, size_t dyn_smem, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
+    if (a.rows[1] != a.rows[0]) return kad_launch_wsample_directed(a, blocks, dyn_smem, st);
+#endif
     if (a.nctx < 1 || a.nctx > W_WARPS) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_wsample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
     if (e != cudaSuccess) return e;
     k_wsample<<<blocks, W_THREADS, dyn_smem, st>>>(a);
     return cudaGetLastError();
 }
+
+#if !KAD_DIRECTED
 
 int kad_wsample_max_blocks_per_sm(size_t dyn_smem) {
     int nb = 0;
@@ -1558,3 +1577,4 @@ int kad_wsample_max_blocks_per_sm(size_t dyn_smem) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wsample, W_THREADS, dyn_smem) != cudaSuccess) return 0;
     return nb;
 }
+#endif // !KAD_DIRECTED

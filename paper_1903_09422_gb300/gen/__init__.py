@@ -229,6 +229,8 @@ WORKLOADS = {
     "rmat18": dict(kind="rmat", scale=18, edge_factor=16, eps=0.01, delta=0.1, seed=1),
     "rmat20": dict(kind="rmat", scale=20, edge_factor=16, eps=0.01, delta=0.1, seed=1),
     "grid2048": dict(kind="grid", side=2048, eps=0.01, delta=0.1, seed=1),
+    "rmat18d": dict(kind="rmat_directed", scale=18, edge_factor=16, eps=0.01, delta=0.1, seed=1),
+    "rmat20d": dict(kind="rmat_directed", scale=20, edge_factor=16, eps=0.01, delta=0.1, seed=1),
     "hyp4m": dict(kind="hyperbolic", n=4 * (1 << 20), eps=0.005, delta=0.1, seed=1),
 }
 
@@ -237,6 +239,8 @@ def describe(name: str) -> str:
     w = WORKLOADS[name]
     if w["kind"] == "rmat":
         g = f"R-MAT scale {w['scale']} ef {w['edge_factor']} (a,b,c=.57,.19,.19) undirected LCC"
+    elif w["kind"] == "rmat_directed":
+        g = f"R-MAT scale {w['scale']} ef {w['edge_factor']} (a,b,c=.57,.19,.19) directed, largest weak component"
     elif w["kind"] == "grid":
         g = f"{w['side']}x{w['side']} grid, 5% edges removed, 0.1% shortcuts, LCC"
     else:
@@ -248,6 +252,8 @@ def workload_graph(name: str, graph_seed: int = 1) -> CSR:
     w = WORKLOADS[name]
     if w["kind"] == "rmat":
         return rmat(w["scale"], w["edge_factor"], seed=graph_seed)
+    if w["kind"] == "rmat_directed":
+        return rmat_directed(w["scale"], w["edge_factor"], seed=graph_seed)
     if w["kind"] == "grid":
         return grid(w["side"], seed=graph_seed)
     if w["kind"] == "hyperbolic":

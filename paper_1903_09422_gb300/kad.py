@@ -14,6 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libkad.so")
 
 KAD_GRAPH_TRUSTED = 1
+KAD_GRAPH_DIRECTED = 2
 KAD_RUN_TIMING = 1
 KAD_RUN_AUTOTUNE = 2
 KAD_RUN_COMPLETION_ORDER = 4
@@ -206,9 +207,12 @@ def options(**kw):
 class Graph:
     """A graph resident on the current CUDA device (kad_graph)."""
 
-    def __init__(self, row_ptr, col, trusted=False, stream=None, _handle=None):
+    def __init__(self, row_ptr, col, trusted=False, stream=None, directed=False, _handle=None):
+        """directed: row_ptr/col list the out-arcs of a directed graph."""
         lib = load()
         self._h = None
+        self.directed = bool(directed)
+        flags = (KAD_GRAPH_TRUSTED if trusted else 0) | (KAD_GRAPH_DIRECTED if directed else 0)
         if _handle is not None:
             self._h = _handle
         else:
@@ -217,9 +221,8 @@ class Graph:
             if cl.size == 0:
                 cl = np.zeros(1, np.int32)
             h = ctypes.c_void_p()
-            _check(lib.kad_graph_create(rp.size - 1, rp.ctypes.data, cl.ctypes.data,
-                                        KAD_GRAPH_TRUSTED if trusted else 0, _stream_handle(stream), ctypes.byref(h)),
-                   "kad_graph_create")
+            _check(lib.kad_graph_create(rp.size - 1, rp.ctypes.data, cl.ctypes.data, flags, _stream_handle(stream),
+                                        ctypes.byref(h)), "kad_graph_create")
             self._h = h
         n, m, vd, nc = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
         _check(lib.kad_graph_info(self._h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(vd), ctypes.byref(nc)),
@@ -228,18 +231,21 @@ class Graph:
 
     @classmethod
     def from_csr(cls, csr, **kw):
+        kw.setdefault("directed", bool(getattr(csr, "directed", False)))
         return cls(csr.row_ptr, csr.col, **kw)
 
     @classmethod
-    def from_device(cls, d_row_ptr, d_col, trusted=False, stream=None):
+    def from_device(cls, d_row_ptr, d_col, trusted=False, stream=None, directed=False):
         """From device tensors (torch, int32, contiguous); copied device-to-device."""
         lib = load()
         h = ctypes.c_void_p()
         n = d_row_ptr.numel() - 1
-        _check(lib.kad_graph_create_device(n, d_col.numel(), d_row_ptr.data_ptr(), d_col.data_ptr(),
-                                           KAD_GRAPH_TRUSTED if trusted else 0, _stream_handle(stream),
-                                           ctypes.byref(h)), "kad_graph_create_device")
-        return cls(None, None, _handle=h)
+        flags = (KAD_GRAPH_TRUSTED if trusted else 0) | (KAD_GRAPH_DIRECTED if directed else 0)
+        _check(lib.kad_graph_create_device(n, d_col.numel(), d_row_ptr.data_ptr(), d_col.data_ptr(), flags,
+                                           _stream_handle(stream), ctypes.byref(h)), "kad_graph_create_device")
+        g = cls(None, None, _handle=h)
+        g.directed = bool(directed)
+        return g
 
     @property
     def path_cap(self):
@@ -406,13 +412,15 @@ class Server:
         self._bufs = {}
 
     def add_graph(self, csr, trusted=False):
+        directed = bool(getattr(csr, "directed", False))
         rp = np.ascontiguousarray(csr.row_ptr, dtype=np.int32)
         cl = np.ascontiguousarray(csr.col, dtype=np.int32)
         if cl.size == 0:
             cl = np.zeros(1, np.int32)
         gid = ctypes.c_int32()
         _check(load().kad_server_add_graph(self._h, rp.size - 1, rp.ctypes.data, cl.ctypes.data,
-                                           KAD_GRAPH_TRUSTED if trusted else 0, ctypes.byref(gid)),
+                                           (KAD_GRAPH_TRUSTED if trusted else 0) |
+                                           (KAD_GRAPH_DIRECTED if directed else 0), ctypes.byref(gid)),
                "kad_server_add_graph")
         self._n.append(rp.size - 1)
         return gid.value
