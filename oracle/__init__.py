@@ -65,6 +65,8 @@ def _load():
             lib.orc_scc.restype = i32
             lib.orc_vd_bound.argtypes = [i32, vp, vp, vp, vp]
             lib.orc_vd_bound.restype = i32
+            lib.orc_vd_bound_tight.argtypes = [i32, vp, vp]
+            lib.orc_vd_bound_tight.restype = i32
             lib.orc_omega.argtypes = [i32, dbl, dbl]
             lib.orc_omega.restype = u64
             lib.orc_calib_samples.argtypes = [u64, u32, u32]
@@ -80,7 +82,7 @@ def _load():
             lib.orc_samples.restype = ctypes.c_int
             lib.orc_pair_paths.argtypes = [i32, vp, vp, vp, vp, i32, i32, u64, u32, i64, vp, i32, vp]
             lib.orc_pair_paths.restype = ctypes.c_int
-            lib.orc_kadabra.argtypes = [i32, vp, vp, vp, vp, dbl, dbl, u64, u32, u32, u64, vp, vp, vp, vp, i64,
+            lib.orc_kadabra.argtypes = [i32, vp, vp, vp, vp, i32, dbl, dbl, u64, u32, u32, u64, vp, vp, vp, vp, i64,
                                         ctypes.POINTER(_Result)]
             lib.orc_kadabra.restype = ctypes.c_int
             _lib = lib
@@ -169,6 +171,14 @@ def vd_bound(g, directed=None):
     return int(_load().orc_vd_bound(*r.args()))
 
 
+def vd_bound_tight(g):
+    """The opt-in double-sweep bound of an undirected graph (see the C source)."""
+    r = _Rows(g)
+    if r.rpT is not None:
+        raise ValueError("the double-sweep bound is defined for undirected graphs")
+    return int(_load().orc_vd_bound_tight(r.n, r.rp.ctypes.data, r.col.ctypes.data))
+
+
 def omega(vd, eps, delta):
     return int(_load().orc_omega(vd, eps, delta))
 
@@ -230,11 +240,12 @@ def pair_paths(g, s, t, count, seed=1, domain=0, cap=None):
     return paths, int(sst.value)
 
 
-def kadabra(g, eps, delta, seed, epoch=1000, calib_div=100, max_epochs=0):
-    """Full KADABRA run.  max_epochs > 0 truncates the adaptive phase (timing samples)."""
+def kadabra(g, eps, delta, seed, epoch=1000, calib_div=100, max_epochs=0, tight_vd=False):
+    """Full KADABRA run.  max_epochs > 0 truncates the adaptive phase (timing samples);
+    tight_vd: omega from the double-sweep bound (undirected graphs)."""
     r = _Rows(g)
     lib = _load()
-    vd = lib.orc_vd_bound(*r.args())
+    vd = vd_bound_tight(g) if tight_vd else lib.orc_vd_bound(*r.args())
     om = lib.orc_omega(vd, eps, delta)
     t0 = lib.orc_calib_samples(om, epoch, calib_div)
     counts = np.zeros(g.n, np.uint32)
@@ -242,7 +253,7 @@ def kadabra(g, eps, delta, seed, epoch=1000, calib_div=100, max_epochs=0):
     c0 = np.zeros(g.n, np.uint32)
     Ltab = np.zeros(t0 + 1, np.float64)
     res = _Result()
-    rc = lib.orc_kadabra(*r.args(), eps, delta, seed, epoch, calib_div, max_epochs,
+    rc = lib.orc_kadabra(*r.args(), vd, eps, delta, seed, epoch, calib_div, max_epochs,
                          counts.ctypes.data, bc.ctypes.data, c0.ctypes.data, Ltab.ctypes.data, Ltab.size,
                          ctypes.byref(res))
     if rc != 0:

@@ -446,6 +446,104 @@ static int32_t vd_bound_directed(const orc_graph *g) {
     return (int32_t)vd;
 }
 
+/* BFS over the out-arc rows from src; dist[] must be -1 outside.  Returns the
+ * number of vertices reached (all stored in queue[]). */
+static int32_t bfs_from(const orc_graph *g, int32_t src, int32_t *dist, int32_t *queue) {
+    int32_t head = 0, tail = 0;
+    queue[tail++] = src;
+    dist[src] = 0;
+    while (head < tail) {
+        int32_t u = queue[head++];
+        for (int32_t e = g->rp[0][u]; e < g->rp[0][u + 1]; e++) {
+            int32_t w = g->col[0][e];
+            if (dist[w] < 0) {
+                dist[w] = dist[u] + 1;
+                queue[tail++] = w;
+            }
+        }
+    }
+    return tail;
+}
+
+/* The farthest of the `cnt` vertices in list[] by dist[] (smallest id on ties). */
+static int32_t farthest(const int32_t *list, int32_t cnt, const int32_t *dist) {
+    int32_t best = list[0];
+    for (int32_t i = 1; i < cnt; i++) {
+        int32_t v = list[i];
+        if (dist[v] > dist[best] || (dist[v] == dist[best] && v < best)) best = v;
+    }
+    return best;
+}
+
+/* READING (opt-in; Section 2.3 asks only for an upper bound on the diameter, and
+ * any vertex x gives diam <= 2 ecc(x)): a tighter bound per component from a
+ * double sweep.  a = the vertex farthest from v0, b = the vertex farthest from
+ * a (smallest id on ties); d = d(a, b) is a lower bound on the diameter.  m =
+ * the midpoint of an a-b shortest path nearest v0: among the x with
+ * d(a,x) + d(x,b) = d and d(a,x) = ceil(d/2), the one of smallest d(v0,x),
+ * then smallest id.  The component's bound is 2 min(ecc(v0), ecc(m)) + 1, and
+ * VD the maximum over components. */
+int32_t orc_vd_bound_tight(int32_t n, const int32_t *rp, const int32_t *col) {
+    orc_graph g;
+    graph_init(&g, n, rp, col, NULL, NULL);
+    int32_t *comp = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *d0 = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *da = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *db = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *dm = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *members = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t vd = 1;
+    if (!comp || !d0 || !da || !db || !dm || !queue || !members) {
+        vd = -1;
+        goto out;
+    }
+    int32_t nc = components(&g, comp);
+    /* v0 of each component: its vertex of largest degree, smallest id on ties
+     * (kept in dm[c] until the component's turn; components are numbered below n) */
+    for (int32_t c = 0; c < nc; c++) dm[c] = -1;
+    for (int32_t v = 0; v < n; v++)
+        if (dm[comp[v]] < 0 || deg(&g, 0, v) > deg(&g, 0, dm[comp[v]])) dm[comp[v]] = v;
+    for (int32_t c = 0; c < nc; c++) queue[c] = dm[c];
+    for (int32_t v = 0; v < n; v++) d0[v] = da[v] = db[v] = dm[v] = -1;
+    int32_t *v0s = (int32_t *)malloc((size_t)nc * sizeof(int32_t));
+    if (!v0s) {
+        vd = -1;
+        goto out;
+    }
+    memcpy(v0s, queue, (size_t)nc * sizeof(int32_t));
+    for (int32_t c = 0; c < nc; c++) {
+        int32_t v0 = v0s[c];
+        int32_t cnt = bfs_from(&g, v0, d0, members);
+        int32_t a = farthest(members, cnt, d0);
+        int32_t ecc0 = d0[a];
+        bfs_from(&g, a, da, queue);
+        int32_t b = farthest(members, cnt, da);
+        int32_t d = da[b];
+        bfs_from(&g, b, db, queue);
+        int32_t half = (d + 1) / 2, m = -1;
+        for (int32_t i = 0; i < cnt; i++) {
+            int32_t x = members[i];
+            if (da[x] + db[x] != d || da[x] != half) continue;
+            if (m < 0 || d0[x] < d0[m] || (d0[x] == d0[m] && x < m)) m = x;
+        }
+        bfs_from(&g, m, dm, queue);
+        int32_t eccm = dm[farthest(members, cnt, dm)];
+        int32_t e = (eccm < ecc0) ? eccm : ecc0;
+        if (2 * e + 1 > vd) vd = 2 * e + 1;
+    }
+    free(v0s);
+out:
+    free(comp);
+    free(d0);
+    free(da);
+    free(db);
+    free(dm);
+    free(queue);
+    free(members);
+    return vd;
+}
+
 /* rpT == NULL: undirected (one symmetric CSR); else directed with in-arcs rpT/colT. */
 int32_t orc_vd_bound(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *rpT, const int32_t *colT) {
     orc_graph g;
@@ -889,13 +987,15 @@ typedef struct {
  * Outputs: counts[n] (sum of x_i over the used samples), bc[n] = counts/tau,
  * c0[n] (calibration counts), Ltab[tau0+1] (log(1/delta_v) per calibration count). */
 int orc_kadabra(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *rpT, const int32_t *colT,
-                double eps, double delta, uint64_t seed, uint32_t epoch, uint32_t calib_div, uint64_t max_epochs,
-                uint32_t *counts, double *bc, uint32_t *c0, double *Ltab, int64_t Ltab_cap, orc_result *res) {
+                int32_t vd_in, double eps, double delta, uint64_t seed, uint32_t epoch, uint32_t calib_div,
+                uint64_t max_epochs, uint32_t *counts, double *bc, uint32_t *c0, double *Ltab, int64_t Ltab_cap,
+                orc_result *res) {
     if (n < 2 || !(eps > 0 && eps < 1) || !(delta > 0 && delta < 1) || epoch == 0 || calib_div == 0) return -3;
     memset(res, 0, sizeof(*res));
     orc_graph g;
     graph_init(&g, n, rp, col, rpT, colT);
-    int32_t vd = orc_vd_bound(n, rp, col, rpT, colT);
+    /* vd_in > 0: a vertex-diameter bound given by the caller (another rule) */
+    int32_t vd = (vd_in > 0) ? vd_in : orc_vd_bound(n, rp, col, rpT, colT);
     if (vd < 0) return -1;
     uint64_t omega = orc_omega(vd, eps, delta);
     uint64_t tau0 = orc_calib_samples(omega, epoch, calib_div);
