@@ -418,6 +418,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="rmat20")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tight-vd", action="store_true", help="the double-sweep vertex-diameter bound (undirected)")
     ap.add_argument("--no-completion-order", action="store_true", help="skip the completion-order comparison")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--block-threads", type=int, default=0)
@@ -472,7 +473,7 @@ def main():
     d_rp = torch.from_numpy(g.row_ptr).to(dev)
     d_col = torch.from_numpy(g.col).to(dev)
     t0 = time.perf_counter()
-    G = kad.Graph.from_device(d_rp, d_col, directed=g.directed)
+    G = kad.Graph.from_device(d_rp, d_col, directed=g.directed, tight_vd=args.tight_vd)
     torch.cuda.synchronize()
     setup_ms = 1000 * (time.perf_counter() - t0)
     d_bc = torch.empty(g.n, dtype=torch.float64, device=dev)
@@ -544,8 +545,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = ctypes.c_void_p()
-        st = lib.kad_graph_create(g.n, h_rp.data_ptr(), h_col.data_ptr(), kad.KAD_GRAPH_DIRECTED if g.directed else 0,
-                                  stream.cuda_stream, ctypes.byref(h))
+        gflags = (kad.KAD_GRAPH_DIRECTED if g.directed else 0) | (kad.KAD_GRAPH_TIGHT_VD if args.tight_vd else 0)
+        st = lib.kad_graph_create(g.n, h_rp.data_ptr(), h_col.data_ptr(), gflags, stream.cuda_stream, ctypes.byref(h))
         if st != 0:
             raise kad.KadError(st, "kad_graph_create")
         res = kad.Result()
@@ -594,7 +595,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {gen.describe(args.workload)}; n={g.n} arcs={g.m}",
                        "step": "one full KADABRA query (calibration + adaptive sampling to stop + b~)",
-                       "l2": f"flushed between steps ({args.flush_mb} MB write)", "parallelism": f"replicas x{world}"},
+                       "l2": f"flushed between steps ({args.flush_mb} MB write)", "parallelism": f"replicas x{world}",
+                       "vd_bound": "double sweep (KAD_GRAPH_TIGHT_VD)" if args.tight_vd else "2 ecc(v0) + 1"},
             "time_to_stop_ms": statistics.median(step_ms),
             "step_ms": [round(x, 3) for x in step_ms],
             "time_to_stop_ads_ms": statistics.median(r["t_ads_ms"] for r in results),

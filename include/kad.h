@@ -51,6 +51,7 @@ typedef struct kad_graph kad_graph; /* opaque; owns a device copy of the CSR */
 /* Flags for kad_graph_create*. */
 #define KAD_GRAPH_TRUSTED 1u  /* skip the O(m log d) symmetry validation of an undirected CSR */
 #define KAD_GRAPH_DIRECTED 2u /* the CSR lists out-arcs of a directed graph (no symmetry required) */
+#define KAD_GRAPH_TIGHT_VD 4u /* undirected: the double-sweep vertex-diameter bound (see below) */
 
 /*
  * kad_graph_create -- copy a graph to the current CUDA device.
@@ -70,7 +71,13 @@ typedef struct kad_graph kad_graph; /* opaque; owns a device copy of the CSR */
  * connected components' DAG, a component S weighing min(|S|, ecc_in(r) +
  * ecc_out(r) + 1) with r its vertex of largest out- plus in-degree (smallest id
  * on ties) and the eccentricities taken within S.  A sample (s, t) with no
- * directed s-t path counts, with no increments.
+ * directed s-t path counts, with no increments.  With KAD_GRAPH_TIGHT_VD (an
+ * undirected graph; ignored for a directed one) each component's bound becomes
+ * 2 min(ecc(v0), ecc(m)) + 1, m the midpoint of a double sweep: a = the vertex
+ * farthest from v0, b = the vertex farthest from a (smallest ids on ties), m =
+ * the vertex with d(a,m) + d(m,b) = d(a,b) and d(a,m) = ceil(d(a,b)/2) nearest
+ * v0 (then smallest id).  It is never above the default bound, costs four more
+ * BFSs, and lowers omega when it crosses a power of two.
  * Errors: KAD_ERR_INVALID_ARG (n < 2, NULL pointer, m >= 2^31), KAD_ERR_BAD_CSR,
  * KAD_ERR_OOM, KAD_ERR_CUDA.  On error *out is NULL.
  */

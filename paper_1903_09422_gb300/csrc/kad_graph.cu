@@ -714,6 +714,72 @@ __global__ void k_scc_vd(const int32_t *__restrict__ scc, const int32_t *__restr
         }
 }
 
+// ------------------------------------------------ double sweep (opt-in)
+// key[comp root] = max over the component of (dist << 32) | ~v: the farthest
+// vertex, smallest id on ties (dist >= 0 for every vertex after a BFS from
+// every component)
+__global__ void k_far(const int32_t *__restrict__ comp, const int32_t *__restrict__ dist, int32_t n,
+                      unsigned long long *key) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t v = base + threadIdx.x;
+        const bool in = v < n && dist[v] >= 0;
+        const int c = in ? comp[v] : -1;
+        const unsigned long long k =
+            in ? (((unsigned long long)(uint32_t)dist[v] << 32) | (0xffffffffu - (uint32_t)v)) : 0ull;
+        const int c0 = __shfl_sync(0xffffffffu, c, 0);
+        if (__all_sync(0xffffffffu, c == c0)) {
+            unsigned long long x = k;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+                x = (y > x) ? y : x;
+            }
+            if (lane == 0 && c0 >= 0) atomicMax(key + c0, x);
+        } else if (in) {
+            atomicMax(key + c, k);
+        }
+    }
+}
+
+// one BFS source per component: the vertex in the low word of key[root], stored
+// as ~v (inverted = 1, from k_far) or as v (inverted = 0, from k_mid)
+__global__ void k_seed_key(const int32_t *__restrict__ comp, const unsigned long long *__restrict__ key, int32_t n,
+                           int inverted, int32_t *dist, int32_t *q, int *qlen) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (comp[v] == v) {
+            const uint32_t lo = (uint32_t)(key[v] & 0xffffffffull);
+            const int src = (int)(inverted ? 0xffffffffu - lo : lo);
+            if (src < 0 || src >= n) continue; // cannot happen: every component has a vertex
+            dist[src] = 0;
+            q[atomicAdd(qlen, 1)] = src;
+        }
+}
+
+// key_m[root] = min over the component's midpoints x (d(a,x) + d(x,b) = d(a,b)
+// and d(a,x) = ceil(d(a,b)/2)) of (d(v0,x) << 32) | x
+__global__ void k_mid(const int32_t *__restrict__ comp, const int32_t *__restrict__ d0, const int32_t *__restrict__ da,
+                      const int32_t *__restrict__ db, const unsigned long long *__restrict__ key_b, int32_t n,
+                      unsigned long long *key_m) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int c = comp[v];
+        const int d = (int)(key_b[c] >> 32);
+        if (da[v] + db[v] == d && da[v] == (d + 1) / 2)
+            atomicMin(key_m + c, ((unsigned long long)(uint32_t)d0[v] << 32) | (uint32_t)v);
+    }
+}
+
+// VD = max over components of 2 min(ecc(v0), ecc(m)) + 1
+__global__ void k_tight_vd(const int32_t *__restrict__ comp, const unsigned long long *__restrict__ key_a,
+                           const unsigned long long *__restrict__ key_e, int32_t n, int *vd) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (comp[v] == v) {
+            const int e0 = (int)(key_a[v] >> 32), em = (int)(key_e[v] >> 32);
+            atomicMax(vd, 2 * (em < e0 ? em : e0) + 1);
+        }
+}
+
 int grid_for(int64_t work, int threads, int cap) {
     int64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -745,7 +811,7 @@ int grid_for(int64_t work, int threads, int cap) {
 // after trimming vertices with no unassigned in- or out-neighbour.  Every loop
 // below ends: each pass of the outer loop assigns at least the largest
 // unassigned id, and each inner loop runs until its frontier is empty.
-kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_out, int32_t *ncomp_out, int32_t *maxdeg_out,
+static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_out, int32_t *ncomp_out, int32_t *maxdeg_out,
                           cudaError_t *cerr) {
     const int32_t n = gd.n;
     const int64_t m = gd.m;
@@ -984,6 +1050,120 @@ done:
     return status;
 }
 
+// Level-synchronous multi-source BFS from the qlen sources in q0 (dist 0 there,
+// -1 everywhere else): top-down while the frontier's arcs are few, bottom-up
+// once they are a large share of the graph.  *levels = the largest distance
+// reached.  q0 and q1 are frontier buffers of n entries; d_cnt one int and
+// d_arcs one u64 of device scratch.
+static cudaError_t bfs_multi(const KadGraphDev &gd, int32_t *dist, int32_t *q0, int32_t *q1, int qlen, int *d_cnt,
+                      unsigned long long *d_arcs, cudaStream_t st, int *levels) {
+    const int32_t n = gd.n;
+    const int T = 256;
+    const int gv = grid_for(n, T, 65535);
+    int32_t *qa = q0, *qb = q1;
+    unsigned long long arcs = 0; // unknown for the seed level: start top-down
+    cudaError_t e = cudaSuccess;
+    int level = 0;
+    for (;; level++) {
+        if ((e = cudaMemsetAsync(d_cnt, 0, sizeof(int), st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(d_arcs, 0, 8, st)) != cudaSuccess) return e;
+        const bool bottom_up = (int64_t)arcs * 14 > gd.m && qlen > n / 64;
+        if (bottom_up)
+            k_bfs_bu<<<gv, T, 0, st>>>(gd.rp, gd.col, n, dist, qb, d_cnt, d_arcs, level);
+        else {
+            // about 152 SMs x 64 warps in flight: split rows when the frontier is small
+            const int parts = (qlen >= 9728) ? 1 : (9728 + qlen - 1) / qlen;
+            k_bfs_td<<<grid_for((int64_t)qlen * parts * 32, T, 65535), T, 0, st>>>(gd.rp, gd.col, qa, qlen, parts,
+                                                                                  dist, qb, d_cnt, d_arcs, level);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(&qlen, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(&arcs, d_arcs, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        if (qlen == 0) break;
+        int32_t *t = qa;
+        qa = qb;
+        qb = t;
+    }
+    *levels = level;
+    return cudaSuccess;
+}
+
+// The opt-in double-sweep bound (KAD_GRAPH_TIGHT_VD), after the BFS from each
+// component's v0 left its distances in d0: per component a = the farthest
+// vertex from v0, b = the farthest from a (smallest ids on ties), m = the
+// midpoint of an a-b shortest path nearest v0 (d(a,m) = ceil(d(a,b)/2), then
+// smallest d(v0,m), then smallest id), and the bound 2 min(ecc(v0), ecc(m)) + 1;
+// VD is the maximum over components.  Every vertex's diameter bound 2 ecc(x)
+// holds, so any m gives an upper bound; the double sweep looks for a central one.
+// Four more multi-source BFSs, all components at once.
+static kad_status tighten_vd(const KadGraphDev &gd, const int32_t *d0, int32_t *q0, int32_t *q1, int *d_flags,
+                      unsigned long long *d_arcs, cudaStream_t st, int32_t *vd_out, cudaError_t *cerr) {
+    const int32_t n = gd.n;
+    const int T = 256;
+    const int gv = grid_for(n, T, 65535);
+    const size_t a4 = (((size_t)n * 4) + 255) & ~(size_t)255, a8 = (((size_t)n * 8) + 255) & ~(size_t)255;
+    kad_status status = KAD_OK;
+    char *scratch = nullptr;
+    int32_t *da, *db;
+    unsigned long long *key_a, *key_b, *key_m, *key_e;
+    int h[2] = {0, 0};
+    int qlen = 0, level = 0;
+    if (kad_pool_alloc((void **)&scratch, 2 * a4 + 4 * a8, st) != cudaSuccess) {
+        cudaGetLastError();
+        return KAD_ERR_OOM;
+    }
+    da = (int32_t *)scratch;
+    db = (int32_t *)(scratch + a4);
+    key_a = (unsigned long long *)(scratch + 2 * a4);
+    key_b = (unsigned long long *)(scratch + 2 * a4 + a8);
+    key_m = (unsigned long long *)(scratch + 2 * a4 + 2 * a8);
+    key_e = (unsigned long long *)(scratch + 2 * a4 + 3 * a8);
+    GCHK(cudaMemsetAsync(key_a, 0, 2 * a8, st));         // key_a, key_b: maxima
+    GCHK(cudaMemsetAsync(key_m, 0xff, a8, st));          // key_m: minimum
+    GCHK(cudaMemsetAsync(key_e, 0, a8, st));
+    k_far<<<gv, T, 0, st>>>(gd.comp, d0, n, key_a);
+    // from a
+    k_fill<<<gv, T, 0, st>>>(da, n, -1);
+    GCHK(cudaMemsetAsync(d_flags + 1, 0, sizeof(int), st));
+    k_seed_key<<<gv, T, 0, st>>>(gd.comp, key_a, n, 1, da, q0, d_flags + 1);
+    GCHK(cudaGetLastError());
+    GCHK(cudaMemcpyAsync(h, d_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaStreamSynchronize(st));
+    qlen = h[0];
+    GCHK(bfs_multi(gd, da, q0, q1, qlen, d_flags + 1, d_arcs, st, &level));
+    k_far<<<gv, T, 0, st>>>(gd.comp, da, n, key_b);
+    // from b
+    k_fill<<<gv, T, 0, st>>>(db, n, -1);
+    GCHK(cudaMemsetAsync(d_flags + 1, 0, sizeof(int), st));
+    k_seed_key<<<gv, T, 0, st>>>(gd.comp, key_b, n, 1, db, q0, d_flags + 1);
+    GCHK(cudaGetLastError());
+    GCHK(cudaMemcpyAsync(h, d_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaStreamSynchronize(st));
+    qlen = h[0];
+    GCHK(bfs_multi(gd, db, q0, q1, qlen, d_flags + 1, d_arcs, st, &level));
+    // the midpoint nearest v0, then from it (its distances replace a's)
+    k_mid<<<gv, T, 0, st>>>(gd.comp, d0, da, db, key_b, n, key_m);
+    k_fill<<<gv, T, 0, st>>>(da, n, -1);
+    GCHK(cudaMemsetAsync(d_flags + 1, 0, sizeof(int), st));
+    k_seed_key<<<gv, T, 0, st>>>(gd.comp, key_m, n, 0, da, q0, d_flags + 1);
+    GCHK(cudaGetLastError());
+    GCHK(cudaMemcpyAsync(h, d_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaStreamSynchronize(st));
+    qlen = h[0];
+    GCHK(bfs_multi(gd, da, q0, q1, qlen, d_flags + 1, d_arcs, st, &level));
+    k_far<<<gv, T, 0, st>>>(gd.comp, da, n, key_e);
+    GCHK(cudaMemsetAsync(d_flags + 1, 0, sizeof(int), st));
+    k_tight_vd<<<gv, T, 0, st>>>(gd.comp, key_a, key_e, n, d_flags + 1);
+    GCHK(cudaGetLastError());
+    GCHK(cudaMemcpyAsync(h, d_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaStreamSynchronize(st));
+    *vd_out = (h[0] > 1) ? h[0] : 1;
+done:
+    if (scratch) cudaFreeAsync(scratch, st);
+    return status;
+}
+
 kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int32_t *vd_out, int32_t *ncomp_out,
                            int32_t *maxdeg_out,
                            cudaError_t *cerr) {
@@ -998,8 +1178,6 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
     const int gw = grid_for((int64_t)n * 32, T, 65535); // warp-per-vertex kernels
     const int gv = grid_for(n, T, 65535);
     int level = 0, qlen = 0;
-    unsigned long long arcs = 0;
-    int32_t *qa, *qb;
     // one stream-ordered block from the graph pool, cut into the scratch arrays
     // (each start rounded up to 256 bytes)
     char *scratch = nullptr;
@@ -1086,34 +1264,11 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
     *ncomp_out = h_flags[2];
     *maxdeg_out = h_flags[3];
 
-    // multi-source BFS, level by level
-    qa = q0;
-    qb = q1;
-    arcs = 0; // unknown for the seed level: start top-down
-    for (level = 0;; level++) {
-        GCHK(cudaMemsetAsync(d_flags + 1, 0, sizeof(int), st));
-        GCHK(cudaMemsetAsync(d_arcs, 0, 8, st));
-        const bool bottom_up = (int64_t)arcs * 14 > gd.m && qlen > n / 64;
-        if (bottom_up)
-            k_bfs_bu<<<gv, T, 0, st>>>(gd.rp, gd.col, n, dist, qb, d_flags + 1, d_arcs, level);
-        else {
-            // about 152 SMs x 64 warps in flight: split rows when the frontier is small
-            const int parts = (qlen >= 9728) ? 1 : (9728 + qlen - 1) / qlen;
-            k_bfs_td<<<grid_for((int64_t)qlen * parts * 32, T, 65535), T, 0, st>>>(gd.rp, gd.col, qa, qlen, parts,
-                                                                                  dist, qb, d_flags + 1, d_arcs, level);
-        }
-        GCHK(cudaGetLastError());
-        GCHK(cudaMemcpyAsync(h_flags + 1, d_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-        GCHK(cudaMemcpyAsync(&arcs, d_arcs, 8, cudaMemcpyDeviceToHost, st));
-        GCHK(cudaStreamSynchronize(st));
-        qlen = h_flags[1];
-        if (qlen == 0) break;
-        int32_t *t = qa;
-        qa = qb;
-        qb = t;
-    }
+    // multi-source BFS from every component's v0
+    GCHK(bfs_multi(gd, dist, q0, q1, qlen, d_flags + 1, d_arcs, st, &level));
     // `level` is now the largest distance reached from any source
     *vd_out = 2 * level + 1;
+    if (flags & KAD_GRAPH_TIGHT_VD) status = tighten_vd(gd, dist, q0, q1, d_flags, d_arcs, st, vd_out, cerr);
 
 done:
     if (scratch) cudaFreeAsync(scratch, st); // after the set-up's last kernel, in stream order

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libkad.so")
 
 KAD_GRAPH_TRUSTED = 1
 KAD_GRAPH_DIRECTED = 2
+KAD_GRAPH_TIGHT_VD = 4
 KAD_RUN_TIMING = 1
 KAD_RUN_AUTOTUNE = 2
 KAD_RUN_COMPLETION_ORDER = 4
@@ -207,12 +208,14 @@ def options(**kw):
 class Graph:
     """A graph resident on the current CUDA device (kad_graph)."""
 
-    def __init__(self, row_ptr, col, trusted=False, stream=None, directed=False, _handle=None):
-        """directed: row_ptr/col list the out-arcs of a directed graph."""
+    def __init__(self, row_ptr, col, trusted=False, stream=None, directed=False, tight_vd=False, _handle=None):
+        """directed: row_ptr/col list the out-arcs of a directed graph; tight_vd: the
+        double-sweep vertex-diameter bound (undirected graphs)."""
         lib = load()
         self._h = None
         self.directed = bool(directed)
-        flags = (KAD_GRAPH_TRUSTED if trusted else 0) | (KAD_GRAPH_DIRECTED if directed else 0)
+        flags = ((KAD_GRAPH_TRUSTED if trusted else 0) | (KAD_GRAPH_DIRECTED if directed else 0) |
+                 (KAD_GRAPH_TIGHT_VD if tight_vd else 0))
         if _handle is not None:
             self._h = _handle
         else:
@@ -235,12 +238,13 @@ class Graph:
         return cls(csr.row_ptr, csr.col, **kw)
 
     @classmethod
-    def from_device(cls, d_row_ptr, d_col, trusted=False, stream=None, directed=False):
+    def from_device(cls, d_row_ptr, d_col, trusted=False, stream=None, directed=False, tight_vd=False):
         """From device tensors (torch, int32, contiguous); copied device-to-device."""
         lib = load()
         h = ctypes.c_void_p()
         n = d_row_ptr.numel() - 1
-        flags = (KAD_GRAPH_TRUSTED if trusted else 0) | (KAD_GRAPH_DIRECTED if directed else 0)
+        flags = ((KAD_GRAPH_TRUSTED if trusted else 0) | (KAD_GRAPH_DIRECTED if directed else 0) |
+                 (KAD_GRAPH_TIGHT_VD if tight_vd else 0))
         _check(lib.kad_graph_create_device(n, d_col.numel(), d_row_ptr.data_ptr(), d_col.data_ptr(), flags,
                                            _stream_handle(stream), ctypes.byref(h)), "kad_graph_create_device")
         g = cls(None, None, _handle=h)
