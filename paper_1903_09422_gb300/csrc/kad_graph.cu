@@ -433,16 +433,20 @@ __global__ void k_tr_fill(const int32_t *__restrict__ rp, const int32_t *__restr
 }
 
 // Rows of up to 32 arcs are sorted by their thread (insertion sort); longer
-// ones are listed for the block sorts: up to KAD_SORT_MID arcs, else big.
+// ones are listed for the warp sort (up to KAD_SORT_WARP arcs), the block sort
+// (up to KAD_SORT_MID) or the bitmap sort.
+#define KAD_SORT_WARP 256
 #define KAD_SORT_MID 4096
-__global__ void k_tr_sort_small(const int32_t *__restrict__ rpT, int32_t *colT, int32_t n, int32_t *mid,
-                                int *nmid, int32_t *big, int *nbig) {
+__global__ void k_tr_sort_small(const int32_t *__restrict__ rpT, int32_t *colT, int32_t n, int32_t *wl, int *nwl,
+                                int32_t *mid, int *nmid, int32_t *big, int *nbig) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const int a = rpT[v], len = rpT[v + 1] - a;
         if (len > KAD_SORT_MID) {
             big[atomicAdd(nbig, 1)] = v;
-        } else if (len > 32) {
+        } else if (len > KAD_SORT_WARP) {
             mid[atomicAdd(nmid, 1)] = v;
+        } else if (len > 32) {
+            wl[atomicAdd(nwl, 1)] = v;
         } else if (len > 1) {
             int buf[32];
             for (int i = 0; i < len; i++) {
@@ -456,6 +460,29 @@ __global__ void k_tr_sort_small(const int32_t *__restrict__ rpT, int32_t *colT, 
             }
             for (int i = 0; i < len; i++) colT[a + i] = buf[i];
         }
+    }
+}
+
+// a warp per listed row of at most KAD_SORT_WARP arcs: the row goes to shared
+// memory, and each element is written at its rank, the number of smaller
+// elements (the ids of a row are distinct)
+__global__ void __launch_bounds__(256) k_tr_sort_warp(const int32_t *__restrict__ rpT, int32_t *colT,
+                                                      const int32_t *__restrict__ wl, int nwl) {
+    __shared__ int sh[8][KAD_SORT_WARP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nwl; r += warps) {
+        const int v = wl[r];
+        const int a = rpT[v], len = rpT[v + 1] - a;
+        for (int i = lane; i < len; i += 32) sh[w][i] = colT[a + i];
+        __syncwarp();
+        for (int i = lane; i < len; i += 32) {
+            const int x = sh[w][i];
+            int rank = 0;
+            for (int j = 0; j < len; j++) rank += (sh[w][j] < x) ? 1 : 0;
+            colT[a + rank] = x;
+        }
+        __syncwarp();
     }
 }
 
@@ -602,6 +629,76 @@ __global__ void k_scc_back(const int32_t *__restrict__ rpT, const int32_t *__res
     }
 }
 
+// The forward-backward step for the component of the pivot p, the unassigned
+// vertex of largest out- plus in-degree (smallest id on ties; so p is r_S of
+// its component): the vertices reached from p and reaching p, over unassigned
+// vertices, are its component, and their distances from and to p are within it
+// (a path between two vertices of one component never leaves it), so they give
+// ecc_out(p) and ecc_in(p) directly.
+__global__ void k_scc_pivot(const int32_t *__restrict__ rp, const int32_t *__restrict__ rpT,
+                            const int32_t *__restrict__ scc, int32_t n, unsigned long long *key) {
+    unsigned long long best = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (scc[v] < 0) {
+            const uint32_t d = (uint32_t)(rp[v + 1] - rp[v]) + (uint32_t)(rpT[v + 1] - rpT[v]);
+            const unsigned long long k = ((unsigned long long)d << 32) | (0xffffffffu - (uint32_t)v);
+            best = (k > best) ? k : best;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+        best = (y > best) ? y : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(key, best);
+}
+
+__global__ void k_pivot_seed(const unsigned long long *__restrict__ key, int32_t *dist, int32_t *q) {
+    const int p = (int)(0xffffffffu - (uint32_t)(*key & 0xffffffffull));
+    dist[p] = 0;
+    q[0] = p;
+}
+
+// one BFS level over unassigned vertices (warp per frontier vertex, `parts`
+// warps per row when the frontier is small)
+__global__ void k_reach_bfs(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            const int32_t *__restrict__ scc, const int32_t *__restrict__ q, int qlen, int parts,
+                            int32_t *dist, int level, int32_t *nq, int *nqlen) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int64_t items = (int64_t)qlen * parts;
+    for (int64_t it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += warps) {
+        const int i = (int)(it / parts), part = (int)(it % parts);
+        const int u = q[i];
+        for (int e = rp[u] + 32 * part + lane; e < rp[u + 1]; e += 32 * parts) {
+            const int x = col[e];
+            if (scc[x] < 0 && *(volatile int32_t *)(dist + x) < 0 && atomicCAS(dist + x, -1, level + 1) == -1)
+                nq[atomicAdd(nqlen, 1)] = x;
+        }
+    }
+}
+
+// the pivot's component: reached both ways; its eccentricities from the distances
+__global__ void k_scc_fwbw(int32_t *scc, const int32_t *__restrict__ df, const int32_t *__restrict__ db, int32_t n,
+                           const unsigned long long *__restrict__ key, int32_t *e_out, int32_t *e_in, int *count) {
+    const int p = (int)(0xffffffffu - (uint32_t)(*key & 0xffffffffull));
+    int c = 0, mf = 0, mb = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (scc[v] < 0 && df[v] >= 0 && db[v] >= 0) {
+            scc[v] = p;
+            c++;
+            mf = (df[v] > mf) ? df[v] : mf;
+            mb = (db[v] > mb) ? db[v] : mb;
+        }
+    c = __reduce_add_sync(0xffffffffu, c);
+    mf = __reduce_max_sync(0xffffffffu, mf);
+    mb = __reduce_max_sync(0xffffffffu, mb);
+    if ((threadIdx.x & 31) == 0 && c) {
+        atomicAdd(count, c);
+        atomicMax(e_out + p, mf);
+        atomicMax(e_in + p, mb);
+    }
+}
+
 // per component (indexed by its label): size, and the root r_S of largest
 // out- plus in-degree, smallest id on ties, as (deg << 32) | ~v
 __global__ void k_scc_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ rpT,
@@ -631,10 +728,14 @@ __global__ void k_count_self(const int32_t *__restrict__ lab, int32_t n, int *co
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
-__global__ void k_scc_seed(const int32_t *__restrict__ scc, const unsigned long long *__restrict__ best, int32_t n,
+// BFS sources: the roots of components of two or more vertices, except the
+// pivot's (its eccentricities are known; a single vertex has none)
+__global__ void k_scc_seed(const int32_t *__restrict__ scc, const unsigned long long *__restrict__ best,
+                           const int32_t *__restrict__ size, const unsigned long long *__restrict__ pivot, int32_t n,
                            int32_t *dist, int32_t *q, int *qlen) {
+    const int p = *pivot ? (int)(0xffffffffu - (uint32_t)(*pivot & 0xffffffffull)) : -1;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        if (scc[v] == v) {
+        if (scc[v] == v && size[v] > 1 && v != p) {
             const int r = (int)(0xffffffffu - (uint32_t)(best[v] & 0xffffffffull));
             dist[r] = 0;
             q[atomicAdd(qlen, 1)] = r;
@@ -805,12 +906,15 @@ int grid_for(int64_t work, int threads, int cap) {
 // components -- a shortest path runs through a chain S_1 -> ... -> S_k of the
 // components' DAG and spends at most w(S) = min(|S|, ecc_in(r_S) + ecc_out(r_S) + 1)
 // vertices in each, r_S the vertex of largest out- plus in-degree (smallest id
-// on ties), so VD = the heaviest chain.  The components come from colour
-// propagation (each unassigned vertex takes the largest id that reaches it;
-// the vertices of a colour that reach its root form the root's component),
-// after trimming vertices with no unassigned in- or out-neighbour.  Every loop
-// below ends: each pass of the outer loop assigns at least the largest
-// unassigned id, and each inner loop runs until its frontier is empty.
+// on ties), so VD = the heaviest chain.  The components: trim vertices with no
+// unassigned in- or out-neighbour (components of their own); one
+// forward-backward step from the unassigned vertex of largest out+in degree
+// (its component, on skewed graphs the large one, with its eccentricities); the
+// rest by colour propagation (each unassigned vertex takes the largest id that
+// reaches it; the vertices of a colour that reach its root form the root's
+// component).  Every loop below ends: each pass of the outer loop assigns at
+// least the largest unassigned id, and each inner loop runs until its frontier
+// is empty.
 static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_out, int32_t *ncomp_out, int32_t *maxdeg_out,
                           cudaError_t *cerr) {
     const int32_t n = gd.n;
@@ -826,6 +930,7 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
     char *scratch = nullptr;
     uint32_t *bits = nullptr;
     int *d_cnt = nullptr; // [0] error flags, [1..3] counters, [4] changed, [5] vd, [6] count, [7] largest degree
+    unsigned long long *pivot = nullptr; // the forward-backward pivot's key (after the counters)
     int32_t *parent, *scc, *color, *stamp, *q0, *q1, *dist, *size, *e_out, *e_in, *wt, *B, *tiles;
     unsigned long long *best;
     int h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -839,6 +944,7 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
         goto done;
     }
     d_cnt = (int *)scratch;
+    pivot = (unsigned long long *)(scratch + 64);
     parent = (int32_t *)(scratch + 256);
     scc = (int32_t *)(scratch + 256 + a4);
     color = (int32_t *)(scratch + 256 + 2 * a4);
@@ -863,12 +969,13 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
     k_scan_add<<<grid_for((int64_t)n + 1, T, 65535), T, 0, st>>>(gd.rpT, (int64_t)n + 1, tiles);
     GCHK(cudaMemsetAsync(parent, 0, (size_t)n * 4, st)); // the scatter cursors
     k_tr_fill<<<gw, T, 0, st>>>(gd.rp, gd.col, n, gd.rpT, parent, gd.colT);
-    k_tr_sort_small<<<gv, T, 0, st>>>(gd.rpT, gd.colT, n, q0, d_cnt + 1, q1, d_cnt + 2);
+    k_tr_sort_small<<<gv, T, 0, st>>>(gd.rpT, gd.colT, n, dist, d_cnt + 3, q0, d_cnt + 1, q1, d_cnt + 2);
     GCHK(cudaGetLastError());
-    GCHK(cudaMemcpyAsync(h, d_cnt, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCHK(cudaMemcpyAsync(h, d_cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     GCHK(cudaStreamSynchronize(st));
     nmid = h[1];
     nbig = h[2];
+    if (h[3] > 0) k_tr_sort_warp<<<grid_for((int64_t)h[3] * 32, T, 65535), T, 0, st>>>(gd.rpT, gd.colT, dist, h[3]);
     if (nmid > 0) k_tr_sort_mid<<<(nmid < 2048 ? nmid : 2048), 1024, 0, st>>>(gd.rpT, gd.colT, q0, nmid);
     if (nbig > 0) {
         const int gb = nbig < 64 ? nbig : 64;
@@ -922,7 +1029,54 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
     // ---- strongly connected components
     k_fill<<<gv, T, 0, st>>>(scc, n, -1);
     k_fill<<<gv, T, 0, st>>>(stamp, n, -1);
+    GCHK(cudaMemsetAsync(e_out, 0, (size_t)n * 4, st));
+    GCHK(cudaMemsetAsync(e_in, 0, (size_t)n * 4, st));
+    GCHK(cudaMemsetAsync(pivot, 0, sizeof(unsigned long long), st));
     GCHK(cudaGetLastError());
+    for (int pass = 0; pass < 4 && remaining > 0; pass++) {
+        GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
+        k_scc_trim<<<gv, T, 0, st>>>(gd.rp, gd.col, gd.rpT, gd.colT, n, scc, d_cnt + 1);
+        GCHK(cudaGetLastError());
+        GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GCHK(cudaStreamSynchronize(st));
+        remaining -= h[1];
+        if (h[1] == 0) break;
+    }
+    if (remaining > 0) {
+        // forward-backward from the pivot (on skewed graphs: the large component)
+        k_scc_pivot<<<gv, T, 0, st>>>(gd.rp, gd.rpT, scc, n, pivot);
+        for (int z = 0; z < 2; z++) {
+            const int32_t *rows = z ? gd.rpT : gd.rp, *cols = z ? gd.colT : gd.col;
+            int32_t *dz = z ? dist : color;
+            k_fill<<<gv, T, 0, st>>>(dz, n, -1);
+            k_pivot_seed<<<1, 1, 0, st>>>(pivot, dz, q0);
+            GCHK(cudaGetLastError());
+            qlen = 1;
+            qa = q0;
+            qb = q1;
+            for (level = 0; qlen > 0; level++) {
+                const int parts = (qlen >= 9728) ? 1 : (9728 + qlen - 1) / qlen;
+                GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
+                k_reach_bfs<<<grid_for((int64_t)qlen * parts * 32, T, 65535), T, 0, st>>>(rows, cols, scc, qa, qlen,
+                                                                                          parts, dz, level, qb,
+                                                                                          d_cnt + 1);
+                GCHK(cudaGetLastError());
+                GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+                GCHK(cudaStreamSynchronize(st));
+                qlen = h[1];
+                int32_t *t = qa;
+                qa = qb;
+                qb = t;
+            }
+        }
+        GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
+        k_scc_fwbw<<<gv, T, 0, st>>>(scc, color, dist, n, pivot, e_out, e_in, d_cnt + 1);
+        GCHK(cudaGetLastError());
+        GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GCHK(cudaStreamSynchronize(st));
+        remaining -= h[1];
+    }
+    // the rest by colour propagation
     for (int outer = 0; remaining > 0; outer++) {
         if (outer > n) { // cannot happen: every pass assigns the largest unassigned id
             status = KAD_ERR_INTERNAL;
@@ -985,8 +1139,6 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
     // ---- per component: size, root, eccentricities within it, weight
     GCHK(cudaMemsetAsync(size, 0, (size_t)n * 4, st));
     GCHK(cudaMemsetAsync(best, 0, (size_t)n * 8, st));
-    GCHK(cudaMemsetAsync(e_out, 0, (size_t)n * 4, st));
-    GCHK(cudaMemsetAsync(e_in, 0, (size_t)n * 4, st));
     k_scc_stats<<<gv, T, 0, st>>>(gd.rp, gd.rpT, scc, n, size, best, d_cnt + 7, d_cnt);
     GCHK(cudaGetLastError());
     GCHK(cudaMemcpyAsync(h, d_cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -999,7 +1151,7 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
         const int32_t *rows = z ? gd.rpT : gd.rp, *cols = z ? gd.colT : gd.col;
         k_fill<<<gv, T, 0, st>>>(dist, n, -1);
         GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
-        k_scc_seed<<<gv, T, 0, st>>>(scc, best, n, dist, q0, d_cnt + 1);
+        k_scc_seed<<<gv, T, 0, st>>>(scc, best, size, pivot, n, dist, q0, d_cnt + 1);
         GCHK(cudaGetLastError());
         GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
         GCHK(cudaStreamSynchronize(st));
