@@ -372,6 +372,64 @@ def serve_specs(count, seed=20261203):
     return [(i, i % 3, int(round(10 ** (4 + 2 * rng.random())))) for i in range(count)]
 
 
+# The other configured workloads (C1, C3, C4), measured in the default run like
+# the main line: inputs resident in HBM, L2 flushed between queries, CUDA events
+# on the launching stream, clocks sampled during the timed queries.
+OTHER_WORKLOADS = ("rmat12", "grid2048", "hyp4m")
+
+
+def _workload_graph(name):
+    from paper_1903_09422_gb300 import gen
+    return name, gen.workload_graph(name)
+
+
+def workloads_record(kad, graphs, flush, uuid, steps=5, warmup=3):
+    import torch
+    from paper_1903_09422_gb300 import gen
+    peak, peak_kind = load_peaks()
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, g in graphs:
+        w = gen.WORKLOADS[name]
+        d_rp = torch.from_numpy(g.row_ptr).cuda()
+        d_col = torch.from_numpy(g.col).cuda()
+        d_bc = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        G = kad.Graph.from_device(d_rp, d_col, directed=g.directed)
+        try:
+            for _ in range(warmup):
+                G.run_device(w["eps"], w["delta"], w["seed"], d_bc=d_bc, timing=True)
+            torch.cuda.synchronize()
+            clocks = ClockSampler(uuid)
+            clocks.start()
+            time.sleep(0.4)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            res = []
+            for i in range(steps):
+                flush.fill_(i & 0xff)
+                ev[i][0].record(stream)
+                res.append(G.run_device(w["eps"], w["delta"], w["seed"], d_bc=d_bc, timing=True))
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            clk = clocks.stop()
+        finally:
+            G.close()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        used = sum(r["tau"] + r["calib_samples"] for r in res)
+        ab = sum(alg_bytes(r["counters"]) for r in res)
+        kt = sum(r["t_ads_kernel_ms"] for r in res)
+        r0 = res[-1]
+        out[name] = {"workload": f"{name}: {gen.describe(name)}; n={g.n} arcs={g.m}",
+                     "value": used / (sum(ms) / 1000.0), "unit": UNIT, "time_to_stop_ms": statistics.median(ms),
+                     "step_ms": [round(x, 3) for x in ms], "tau": r0["tau"], "epochs": r0["epochs"],
+                     "vd_bound": r0["vd_bound"], "samples_computed": int(statistics.median(r["samples_computed"] for r in res)),
+                     "roofline_frac": (ab / (kt / 1000.0) / 1e9) / peak, "peak_kind": peak_kind,
+                     "kernel_variant": f"{r0['block_threads_used']} threads x {r0['blocks_per_sm_used']} blocks/SM",
+                     "clocks": clk}
+        del d_rp, d_col, d_bc
+        torch.cuda.empty_cache()
+    return out
+
+
 def serving_record(kad, graphs, queries=300, plain_n=150, load=4.0, workers=4):
     """A bounded sample of the serving stream for the default bench line: the
     plain arm's back-to-back capacity (one query at a time with every sampling
@@ -435,6 +493,8 @@ def main():
     ap.add_argument("--serve-load", default="0.5,1,2,4", help="arrival rates, as multiples of plain queries/s")
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving record of the default line")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the record of the other configured workloads (C1, C3, C4) in the default line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -449,6 +509,12 @@ def main():
         import multiprocessing as mpx
         serve_pool = mpx.get_context("spawn").Pool(8)
         serve_async = serve_pool.map_async(_serve_graph, serve_specs(args.serve_graphs), chunksize=1)
+    others_pool = others_async = None
+    if (not args.no_other_workloads and args.workload == "rmat20" and args.gpus == 1 and
+            int(os.environ.get("WORLD_SIZE", "1")) == 1):
+        import multiprocessing as mpx
+        others_pool = mpx.get_context("spawn").Pool(len(OTHER_WORKLOADS))
+        others_async = others_pool.map_async(_workload_graph, OTHER_WORKLOADS, chunksize=1)
 
     import torch
     rank, world, dist = dist_setup(args.gpus)
@@ -630,6 +696,13 @@ def main():
             "completion_order": co,
             "cpu_baseline": cpu,
         }
+        if others_async is not None:
+            try:
+                line["other_workloads"] = workloads_record(kad, others_async.get(timeout=900), flush, uuid)
+            except Exception as ex:  # the record must not sink the bench line
+                line["other_workloads"] = {"error": str(ex)}
+            finally:
+                others_pool.close()
         if serve_async is not None:
             try:
                 graphs = serve_async.get(timeout=900)
