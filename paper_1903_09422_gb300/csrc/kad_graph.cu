@@ -662,7 +662,7 @@ __global__ void k_pivot_seed(const unsigned long long *__restrict__ key, int32_t
 // warps per row when the frontier is small)
 __global__ void k_reach_bfs(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                             const int32_t *__restrict__ scc, const int32_t *__restrict__ q, int qlen, int parts,
-                            int32_t *dist, int level, int32_t *nq, int *nqlen) {
+                            int32_t *dist, int level, int32_t *nq, int *nqlen, unsigned long long *narcs) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     const int64_t items = (int64_t)qlen * parts;
@@ -671,8 +671,29 @@ __global__ void k_reach_bfs(const int32_t *__restrict__ rp, const int32_t *__res
         const int u = q[i];
         for (int e = rp[u] + 32 * part + lane; e < rp[u + 1]; e += 32 * parts) {
             const int x = col[e];
-            if (scc[x] < 0 && *(volatile int32_t *)(dist + x) < 0 && atomicCAS(dist + x, -1, level + 1) == -1)
+            if (scc[x] < 0 && *(volatile int32_t *)(dist + x) < 0 && atomicCAS(dist + x, -1, level + 1) == -1) {
                 nq[atomicAdd(nqlen, 1)] = x;
+                atomicAdd(narcs, (unsigned long long)(rp[x + 1] - rp[x]));
+            }
+        }
+    }
+}
+
+// the same level bottom-up: each unvisited unassigned vertex looks for a parent
+// at `level` among the tails of its rows in the other direction (rpo/colo);
+// rp gives the degrees counted for the direction switch
+__global__ void k_reach_bu(const int32_t *__restrict__ rp, const int32_t *__restrict__ rpo,
+                           const int32_t *__restrict__ colo, const int32_t *__restrict__ scc, int32_t n, int32_t *dist,
+                           int level, int32_t *nq, int *nqlen, unsigned long long *narcs) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        if (dist[x] >= 0 || scc[x] >= 0) continue;
+        for (int e = rpo[x]; e < rpo[x + 1]; e++) {
+            if (*(volatile int32_t *)(dist + colo[e]) == level) {
+                dist[x] = level + 1;
+                nq[atomicAdd(nqlen, 1)] = x;
+                atomicAdd(narcs, (unsigned long long)(rp[x + 1] - rp[x]));
+                break;
+            }
         }
     }
 }
@@ -704,20 +725,45 @@ __global__ void k_scc_fwbw(int32_t *scc, const int32_t *__restrict__ df, const i
 __global__ void k_scc_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ rpT,
                             const int32_t *__restrict__ scc, int32_t n, int32_t *size, unsigned long long *best,
                             int *maxdeg, int *err) {
+    // one atomic per warp when its vertices share a component (most of a large
+    // component's vertices), else one per vertex
+    const int lane = threadIdx.x & 31;
     int md = 0;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const int s = scc[v];
-        if (s < 0 || s >= n) { // every vertex is assigned by now; checked, not assumed
-            atomicOr(err, GERR_CC);
-            continue;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t v = base + threadIdx.x;
+        int s = -1;
+        unsigned long long key = 0;
+        if (v < n) {
+            s = scc[v];
+            if (s < 0 || s >= n) { // every vertex is assigned by now; checked, not assumed
+                atomicOr(err, GERR_CC);
+                s = -1;
+            } else {
+                const uint32_t d = (uint32_t)(rp[v + 1] - rp[v]) + (uint32_t)(rpT[v + 1] - rpT[v]);
+                key = ((unsigned long long)d << 32) | (0xffffffffu - (uint32_t)v);
+                md = ((int)d > md) ? (int)d : md;
+            }
         }
-        const uint32_t d = (uint32_t)(rp[v + 1] - rp[v]) + (uint32_t)(rpT[v + 1] - rpT[v]);
-        atomicAdd(size + s, 1);
-        atomicMax(best + s, ((unsigned long long)d << 32) | (0xffffffffu - (uint32_t)v));
-        md = ((int)d > md) ? (int)d : md;
+        const int s0 = __shfl_sync(0xffffffffu, s, 0);
+        if (__all_sync(0xffffffffu, s == s0)) {
+            unsigned long long k = key;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, k, o);
+                k = (y > k) ? y : k;
+            }
+            if (lane == 0 && s0 >= 0) {
+                atomicAdd(size + s0, 32);
+                atomicMax(best + s0, k);
+            }
+        } else if (s >= 0) {
+            atomicAdd(size + s, 1);
+            atomicMax(best + s, key);
+        }
     }
     md = __reduce_max_sync(0xffffffffu, md);
-    if ((threadIdx.x & 31) == 0 && md) atomicMax(maxdeg, md);
+    if (lane == 0 && md) atomicMax(maxdeg, md);
 }
 
 // how many v have lab[v] == v (component labels: one per component)
@@ -777,6 +823,35 @@ __global__ void k_scc_weight(const int32_t *__restrict__ scc, int32_t n, const i
             w[v] = (x < size[v]) ? (int32_t)x : size[v];
             B[v] = w[v];
         }
+}
+
+// every arc e as pairs[e] = (S, S') when it joins two components, else (-1, -1)
+// (warp per vertex; each arc keeps its own slot, so no counter is shared)
+__global__ void k_chain_arcs(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                             const int32_t *__restrict__ scc, int32_t n, int2 *pairs) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int su = scc[u];
+        for (int e = rp[u] + lane; e < rp[u + 1]; e += 32) {
+            const int sv = scc[col[e]];
+            const bool cross = su >= 0 && su < n && sv != su && sv >= 0 && sv < n;
+            pairs[e] = cross ? make_int2(su, sv) : make_int2(-1, -1);
+        }
+    }
+}
+
+// one relaxation of B(S) = w(S) + B(S') over the arcs between components; sets
+// *changed when some B grew.  Repeated until nothing changes: the components'
+// graph is acyclic, so B stops at the heaviest chain below S.
+__global__ void k_chain_relax(const int2 *__restrict__ pairs, int64_t npairs, const int32_t *__restrict__ w,
+                              int32_t *B, int *changed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npairs; i += (int64_t)gridDim.x * blockDim.x) {
+        const int2 p = pairs[i];
+        if (p.x < 0) continue;
+        const int cand = w[p.x] + *(volatile int32_t *)(B + p.y);
+        if (cand > *(volatile int32_t *)(B + p.x) && atomicMax(B + p.x, cand) < cand) atomicOr(changed, 1);
+    }
 }
 
 // one relaxation of B(S) = w(S) + max over arcs S -> S' of B(S') (warp per
@@ -929,8 +1004,10 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
     kad_status status = KAD_OK;
     char *scratch = nullptr;
     uint32_t *bits = nullptr;
+    int2 *pairs = nullptr; // the arcs between components, for the heaviest chain
     int *d_cnt = nullptr; // [0] error flags, [1..3] counters, [4] changed, [5] vd, [6] count, [7] largest degree
     unsigned long long *pivot = nullptr; // the forward-backward pivot's key (after the counters)
+    unsigned long long *d_arcs = nullptr; // arcs of a BFS frontier (direction switch)
     int32_t *parent, *scc, *color, *stamp, *q0, *q1, *dist, *size, *e_out, *e_in, *wt, *B, *tiles;
     unsigned long long *best;
     int h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -945,6 +1022,7 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
     }
     d_cnt = (int *)scratch;
     pivot = (unsigned long long *)(scratch + 64);
+    d_arcs = (unsigned long long *)(scratch + 72);
     parent = (int32_t *)(scratch + 256);
     scc = (int32_t *)(scratch + 256 + a4);
     color = (int32_t *)(scratch + 256 + 2 * a4);
@@ -1054,14 +1132,23 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
             qlen = 1;
             qa = q0;
             qb = q1;
+            unsigned long long arcs = 0; // unknown for the seed level: start top-down
             for (level = 0; qlen > 0; level++) {
-                const int parts = (qlen >= 9728) ? 1 : (9728 + qlen - 1) / qlen;
                 GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
-                k_reach_bfs<<<grid_for((int64_t)qlen * parts * 32, T, 65535), T, 0, st>>>(rows, cols, scc, qa, qlen,
-                                                                                          parts, dz, level, qb,
-                                                                                          d_cnt + 1);
+                GCHK(cudaMemsetAsync(d_arcs, 0, sizeof(unsigned long long), st));
+                if ((int64_t)arcs * 14 > m && qlen > n / 64) {
+                    // a frontier with a large share of the arcs: bottom-up over the
+                    // other direction's rows
+                    k_reach_bu<<<gv, T, 0, st>>>(rows, z ? gd.rp : gd.rpT, z ? gd.col : gd.colT, scc, n, dz, level,
+                                                 qb, d_cnt + 1, d_arcs);
+                } else {
+                    const int parts = (qlen >= 9728) ? 1 : (9728 + qlen - 1) / qlen;
+                    k_reach_bfs<<<grid_for((int64_t)qlen * parts * 32, T, 65535), T, 0, st>>>(
+                        rows, cols, scc, qa, qlen, parts, dz, level, qb, d_cnt + 1, d_arcs);
+                }
                 GCHK(cudaGetLastError());
                 GCHK(cudaMemcpyAsync(h + 1, d_cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+                GCHK(cudaMemcpyAsync(&arcs, d_arcs, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
                 GCHK(cudaStreamSynchronize(st));
                 qlen = h[1];
                 int32_t *t = qa;
@@ -1175,14 +1262,23 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
     k_scc_weight<<<gv, T, 0, st>>>(scc, n, size, e_out, e_in, wt, B);
     GCHK(cudaGetLastError());
 
-    // ---- the heaviest chain
+    // ---- the heaviest chain, over the arcs between components (marked once)
+    if (m > 0 && kad_pool_alloc((void **)&pairs, (size_t)m * sizeof(int2), st) != cudaSuccess) {
+        cudaGetLastError();
+        pairs = nullptr; // no room for the list: relax over the CSR itself
+    }
+    if (pairs) k_chain_arcs<<<gw, T, 0, st>>>(gd.rp, gd.col, scc, n, pairs);
     for (int pass = 0;; pass++) {
         if (pass > n) { // cannot happen: each pass lengthens the chains it changes
             status = KAD_ERR_INTERNAL;
             goto done;
         }
         GCHK(cudaMemsetAsync(d_cnt + 4, 0, sizeof(int), st));
-        k_scc_chain<<<gw, T, 0, st>>>(gd.rp, gd.col, scc, n, wt, B, d_cnt + 4);
+        if (pairs) {
+            k_chain_relax<<<ga, T, 0, st>>>(pairs, m, wt, B, d_cnt + 4);
+        } else {
+            k_scc_chain<<<gw, T, 0, st>>>(gd.rp, gd.col, scc, n, wt, B, d_cnt + 4);
+        }
         GCHK(cudaGetLastError());
         GCHK(cudaMemcpyAsync(h + 4, d_cnt + 4, sizeof(int), cudaMemcpyDeviceToHost, st));
         GCHK(cudaStreamSynchronize(st));
@@ -1197,6 +1293,7 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
     *maxdeg_out = h[7];
 
 done:
+    if (pairs) cudaFreeAsync(pairs, st);
     if (bits) cudaFreeAsync(bits, st);
     if (scratch) cudaFreeAsync(scratch, st);
     return status;

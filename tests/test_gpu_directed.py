@@ -230,3 +230,38 @@ def test_directed_rmat20_run_to_stop_matches_oracle(kad):
         r = G.run(w["eps"], w["delta"], w["seed"], c0=True)
     compare_runs(r, ref)
     np.testing.assert_array_equal(r["c0"], ref["c0"])
+
+
+def test_directed_graphs_served_beside_undirected_ones(kad):
+    # the query server holds directed and undirected graphs at once; every
+    # query's result equals the same query run alone, and the oracle's
+    graphs = [gen.rmat_directed(11, 8, seed=3), gen.rmat(11, 8, seed=3), gen.grid_oneway(30, seed=5)]
+    queries = [(i % 3, (0.05, 0.03)[i % 2], 40 + i) for i in range(12)]
+    alone = {}
+    for gi, g in enumerate(graphs):
+        with kad.Graph.from_csr(g) as G:
+            for qi, (qg, eps, seed) in enumerate(queries):
+                if qg == gi:
+                    alone[qi] = G.run(eps, 0.1, seed)
+    with kad.Server(workers=4) as S:
+        gids = [S.add_graph(g) for g in graphs]
+        mixed = [S.wait(t) for t in [S.submit(gids[qg], eps, 0.1, seed) for qg, eps, seed in queries]]
+    for qi, r in enumerate(mixed):
+        a = alone[qi]
+        assert (r["tau"], r["epochs"], r["omega"]) == (a["tau"], a["epochs"], a["omega"])
+        np.testing.assert_array_equal(r["bc"], a["bc"])
+    for qi in (0, 2):
+        qg, eps, seed = queries[qi]
+        np.testing.assert_array_equal(mixed[qi]["bc"], O.kadabra(graphs[qg], eps, 0.1, seed)["bc"])
+
+
+def test_autotuner_on_a_directed_graph(kad):
+    # the autotuner's candidates (block and warp variants) all run the directed
+    # build; the tuned run and a second one equal the oracle's
+    g = gen.rmat_directed(13, 8, seed=4)
+    ref = O.kadabra(g, 0.03, 0.1, 8)
+    with kad.Graph.from_csr(g) as G:
+        r1 = G.run(0.03, 0.1, 8, flags=kad.KAD_RUN_AUTOTUNE)
+        r2 = G.run(0.03, 0.1, 8, flags=kad.KAD_RUN_AUTOTUNE)
+    for r in (r1, r2):
+        compare_runs(r, ref)
