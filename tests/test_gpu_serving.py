@@ -91,3 +91,23 @@ def test_server_rejects_bad_queries(kad):
             S.submit(gid, 1.5, 0.1, 1)
         t = S.submit(gid, 0.05, 0.1, 1)
         assert S.wait(t)["tau"] > 0
+
+
+def test_serving_stream_graphs_against_the_oracle(kad):
+    # graphs of the serving stream itself (the bench's recipe: R-MAT, grid with
+    # shortcuts and hyperbolic graphs of 10^4..10^6 vertices), queried
+    # concurrently through the server at the stream's accuracies: every result
+    # equals the oracle's full run, bit for bit
+    import bench
+    specs = {i: (i, k, n) for i, k, n in bench.serve_specs(64)}
+    picks = [6, 5, 16, 36, 8, 10]  # R-MAT, hyperbolic, grid at ~1.1e4 and ~1e5 vertices
+    graphs = [bench._serve_graph(specs[i]) for i in picks]
+    queries = [(j, (0.05, 0.02, 0.01)[j % 3], 500 + j) for j in range(len(picks))]
+    queries += [(j, 0.05, 600 + j) for j in range(len(picks))]
+    with kad.Server(workers=4) as S:
+        gids = [S.add_graph(g, trusted=True) for g in graphs]
+        res = [S.wait(t) for t in [S.submit(gids[qg], eps, 0.1, seed) for qg, eps, seed in queries]]
+    for (qg, eps, seed), r in zip(queries, res):
+        ref = O.kadabra(graphs[qg], eps, 0.1, seed)
+        assert (r["tau"], r["epochs"], r["omega"]) == (ref["tau"], ref["epochs"], ref["omega"]), (qg, eps)
+        np.testing.assert_array_equal(r["bc"], ref["bc"])
