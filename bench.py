@@ -47,14 +47,14 @@ BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=0, 
 # whose kernel source has changed since, reports traffic null.  Each figure is a
 # query's first sampling launch, which under ncu computes every sample its ring
 # admits: rmat20 2.691 GB over 31,000 samples; rmat20d (directed) 2.152 GB over
-# 36,000; rmat18 0.768 GB over 31,000 (an earlier kernel source); hyp4m 28.65 GB
+# 36,000; rmat18 0.770 GB over 31,000; hyp4m 28.65 GB
 # over 142,000; grid2048 715.1 GB over 56,000 (profiles/k_sample_rmat20_dram.md,
 # profiles/k_sample_rmat20d_dram.md, profiles/k_sample_rmat18_full.md,
 # profiles/k_sample_hyp4m_grid2048_dram.md).
 NCU_TRAFFIC_PER_SAMPLE = {
     ("k_sample", "rmat20"): (86_809, "9a16df1404cf79cd"),
     ("k_sample", "rmat20d"): (59_780, "9a16df1404cf79cd"),
-    ("k_sample", "rmat18"): (24_781, "839ec422ce812ac4"),
+    ("k_sample", "rmat18"): (24_842, "9a16df1404cf79cd"),
     ("k_sample", "hyp4m"): (201_773, "9a16df1404cf79cd"),
     ("k_sample", "grid2048"): (12_769_398, "9a16df1404cf79cd"),
 }
