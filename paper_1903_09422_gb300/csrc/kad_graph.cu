@@ -1418,7 +1418,10 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
                            cudaError_t *cerr) {
     const int32_t n = gd.n;
     kad_status status = KAD_OK;
-    int *d_flags = nullptr; // [0] err, [1] qlen, [2] ncomp, [3] largest degree, [4..7] two u64 arc counts
+    int *d_flags = nullptr; // [0] err, [1] qlen, [2] ncomp, [3] largest degree, [4..7] two u64 arc counts,
+                            // [16] the symmetry check's flag, [18..21] its two u64 counts
+    cudaStream_t side = nullptr; // the symmetry check's stream
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int32_t *parent = nullptr, *dist = nullptr, *q0 = nullptr, *q1 = nullptr;
     unsigned long long *best = nullptr, *d_arcs = nullptr;
     int h_flags[4] = {0, 0, 0, 0};
@@ -1459,16 +1462,19 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
         goto done;
     }
     if (!(flags & KAD_GRAPH_TRUSTED)) {
-        k_validate_sym<<<grid_for((gd.m + KAD_SYM_CHUNK - 1) / KAD_SYM_CHUNK, T, 65535), T, 0, st>>>(
-            gd.rp, gd.col, n, gd.m, d_flags, (unsigned long long *)(d_flags + 4));
+        // The symmetry check runs on a side stream, concurrently with the
+        // components and the BFS (both are safe on any CSR that passed the row
+        // checks, and their result is discarded if the check fails); its flag
+        // and counts (d_flags[16], d_flags + 18) are read once both are done.
+        GCHK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        GCHK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        GCHK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+        GCHK(cudaMemsetAsync(d_flags + 16, 0, 8 * sizeof(int), st));
+        GCHK(cudaEventRecord(ev_fork, st));
+        GCHK(cudaStreamWaitEvent(side, ev_fork, 0));
+        k_validate_sym<<<grid_for((gd.m + KAD_SYM_CHUNK - 1) / KAD_SYM_CHUNK, T, 65535), T, 0, side>>>(
+            gd.rp, gd.col, n, gd.m, d_flags + 16, (unsigned long long *)(d_flags + 18));
         GCHK(cudaGetLastError());
-        GCHK(cudaMemcpyAsync(h_flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-        GCHK(cudaMemcpyAsync(h_counts, d_flags + 4, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-        GCHK(cudaStreamSynchronize(st));
-        if (h_flags[0] || h_counts[0] != h_counts[1]) {
-            status = KAD_ERR_BAD_CSR;
-            goto done;
-        }
     }
 
     // components
@@ -1518,8 +1524,24 @@ kad_status kad_graph_setup(KadGraphDev &gd, uint32_t flags, cudaStream_t st, int
     // `level` is now the largest distance reached from any source
     *vd_out = 2 * level + 1;
     if (flags & KAD_GRAPH_TIGHT_VD) status = tighten_vd(gd, dist, q0, q1, d_flags, d_arcs, st, vd_out, cerr);
+    if (status == KAD_OK && side) {
+        GCHK(cudaEventRecord(ev_join, side));
+        GCHK(cudaStreamWaitEvent(st, ev_join, 0));
+        GCHK(cudaMemcpyAsync(h_flags, d_flags + 16, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GCHK(cudaMemcpyAsync(h_counts, d_flags + 18, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        GCHK(cudaStreamSynchronize(st));
+        if (h_flags[0] || h_counts[0] != h_counts[1]) status = KAD_ERR_BAD_CSR;
+    }
 
 done:
+    if (side) {
+        // whatever happened, the side stream's work ends before the scratch is freed
+        cudaEventRecord(ev_join, side);
+        cudaStreamWaitEvent(st, ev_join, 0);
+        cudaStreamDestroy(side);
+    }
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     if (scratch) cudaFreeAsync(scratch, st); // after the set-up's last kernel, in stream order
     return status;
 }
