@@ -265,3 +265,36 @@ def test_autotuner_on_a_directed_graph(kad):
         r2 = G.run(0.03, 0.1, 8, flags=kad.KAD_RUN_AUTOTUNE)
     for r in (r1, r2):
         compare_runs(r, ref)
+
+
+def _digraph_case(seed):
+    """Random digraphs of varied shape: density, reciprocity, a planted cycle
+    chain, and isolated parts (weak components of several kinds)."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(30, 400))
+    p = float(rng.uniform(0.3, 4.0)) / n
+    a = rng.random((n, n)) < p
+    recip = float(rng.uniform(0, 0.6))
+    a |= a.T & (rng.random((n, n)) < recip)
+    np.fill_diagonal(a, False)
+    arcs = [tuple(x) for x in np.argwhere(a)]
+    # a chain of three cycles (a long chain of components)
+    k = int(rng.integers(3, 9))
+    base = int(rng.integers(0, max(1, n - 3 * k)))
+    for c in range(3):
+        ids = [base + c * k + i for i in range(k)]
+        arcs += [(ids[i], ids[(i + 1) % k]) for i in range(k)]
+        if c:
+            arcs.append((base + (c - 1) * k, ids[0]))
+    return gen.from_arcs(n, arcs, f"case{seed}")
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_digraphs_match_oracle(kad, seed):
+    g = _digraph_case(seed)
+    with kad.Graph.from_csr(g) as G:
+        assert (G.vd_bound, G.components) == (O.vd_bound(g), O.components(g)[0])
+        rec = G.sample_records(seed, 0, 600, domain=seed % 2)
+        r = G.run(0.08, 0.1, seed, samples_per_block=(8 if seed % 3 == 0 else None))
+    compare_records(rec, O.samples(g, seed, 0, 600, domain=seed % 2))
+    compare_runs(r, O.kadabra(g, 0.08, 0.1, seed))
