@@ -982,7 +982,8 @@ int grid_for(int64_t work, int threads, int cap) {
 // components' DAG and spends at most w(S) = min(|S|, ecc_in(r_S) + ecc_out(r_S) + 1)
 // vertices in each, r_S the vertex of largest out- plus in-degree (smallest id
 // on ties), so VD = the heaviest chain.  The components: trim vertices with no
-// unassigned in- or out-neighbour (components of their own); one
+// unassigned in- or out-neighbour (components of their own) until none is left,
+// which removes every vertex on no cycle (a chain of n costs about n/2 passes); one
 // forward-backward step from the unassigned vertex of largest out+in degree
 // (its component, on skewed graphs the large one, with its eccentricities); the
 // rest by colour propagation (each unassigned vertex takes the largest id that
@@ -1111,7 +1112,7 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
     GCHK(cudaMemsetAsync(e_in, 0, (size_t)n * 4, st));
     GCHK(cudaMemsetAsync(pivot, 0, sizeof(unsigned long long), st));
     GCHK(cudaGetLastError());
-    for (int pass = 0; pass < 4 && remaining > 0; pass++) {
+    for (int pass = 0; pass <= n && remaining > 0; pass++) { // to the fixed point
         GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
         k_scc_trim<<<gv, T, 0, st>>>(gd.rp, gd.col, gd.rpT, gd.colT, n, scc, d_cnt + 1);
         GCHK(cudaGetLastError());
@@ -1169,7 +1170,7 @@ static kad_status setup_directed(KadGraphDev &gd, cudaStream_t st, int32_t *vd_o
             status = KAD_ERR_INTERNAL;
             goto done;
         }
-        for (int pass = 0; pass < 4 && remaining > 0; pass++) {
+        for (int pass = 0; pass <= n && remaining > 0; pass++) { // to the fixed point
             GCHK(cudaMemsetAsync(d_cnt + 1, 0, sizeof(int), st));
             k_scc_trim<<<gv, T, 0, st>>>(gd.rp, gd.col, gd.rpT, gd.colT, n, scc, d_cnt + 1);
             GCHK(cudaGetLastError());

@@ -298,3 +298,36 @@ def test_random_digraphs_match_oracle(kad, seed):
         r = G.run(0.08, 0.1, seed, samples_per_block=(8 if seed % 3 == 0 else None))
     compare_records(rec, O.samples(g, seed, 0, 600, domain=seed % 2))
     compare_runs(r, O.kadabra(g, 0.08, 0.1, seed))
+
+
+@pytest.mark.parametrize("case", ["no_arcs", "one_arc", "path_up", "path_down"])
+def test_directed_edge_cases(kad, case):
+    # no arcs (every pair unreachable, VD 1); a single arc; directed paths of
+    # 3,000 vertices with ids rising or falling along the path (a chain of 3,000
+    # singleton components: long forward-backward BFSs, colour propagation one
+    # vertex per pass when ids fall, 3,000 relaxations of the chain)
+    n = 3000
+    if case == "no_arcs":
+        g = gen.from_arcs(50, np.zeros((0, 2), np.int64))
+    elif case == "one_arc":
+        g = gen.from_arcs(2, [(0, 1)])
+    elif case == "path_up":
+        g = gen.from_arcs(n, [(i, i + 1) for i in range(n - 1)])
+    else:
+        g = gen.from_arcs(n, [(i + 1, i) for i in range(n - 1)])
+    want = O.vd_bound(g)
+    assert want == {"no_arcs": 1, "one_arc": 2}.get(case, n)
+    ref = O.kadabra(g, 0.1, 0.1, 5)
+    with kad.Graph.from_csr(g) as G:
+        assert (G.vd_bound, G.components) == (want, O.components(g)[0])
+        r = G.run(0.1, 0.1, 5)
+        rec = G.sample_records(5, 0, 300)
+    compare_runs(r, ref)
+    compare_records(rec, O.samples(g, 5, 0, 300))
+
+
+def test_tight_bound_with_isolated_vertices(kad):
+    # components of one vertex: a = b = m = v0, eccentricity 0
+    g = gen.from_edges(9, [(0, 1), (1, 2), (5, 6)])
+    with kad.Graph.from_csr(g, tight_vd=True) as G:
+        assert G.vd_bound == O.vd_bound_tight(g) == 3
