@@ -432,3 +432,18 @@ def test_smallest_workload_exact_triple(kad):
     np.testing.assert_array_equal(r["counts"], ref["counts"])
     np.testing.assert_array_equal(r["bc"], ref["bc"])
     assert r["overflow_samples"] == ref["overflow_samples"]
+
+
+def test_graph_without_edges(kad):
+    # n isolated vertices: VD 1, every pair unreachable, counts all zero
+    g = gen.from_edges(40, [])
+    assert g.m == 0
+    ref = O.kadabra(g, 0.1, 0.1, 2)
+    for tight in (False, True):
+        with kad.Graph.from_csr(g, tight_vd=tight) as G:
+            assert (G.vd_bound, G.components) == (1, 40)
+            r = G.run(0.1, 0.1, 2)
+            rec = G.sample_records(2, 0, 200)
+        assert (r["tau"], r["epochs"], r["omega"]) == (ref["tau"], ref["epochs"], ref["omega"])
+        assert not r["counts"].any()
+        compare_records(rec, O.samples(g, 2, 0, 200))
