@@ -1476,15 +1476,19 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 ec.probe = ph == 0;
                 long long tp = 0;
                 if (tid == 0) tp = clock64();
+                // a warp whose first arc of a pass (base + 32 w) is past the end has
+                // none in it, nor in any later pass: it skips them (small rounds
+                // then run on the warps that hold arcs)
+                const int wfirst = tid & ~31;
                 if (ec.probe) {
-                    for (int base = 0; base < total; base += BLOCK * KAD_PITEMS) {
+                    for (int base = 0; base + wfirst < total; base += BLOCK * KAD_PITEMS) {
                         if (probe_items<BLOCK>(a, sm, ec, base + tid, BLOCK, total, pred_m)) {
                             if (lane == 0) sm.abort = 1;
                             break;
                         }
                     }
                 } else {
-                    for (int base = 0; base < total; base += BLOCK * KAD_ITEMS) {
+                    for (int base = 0; base + wfirst < total; base += BLOCK * KAD_ITEMS) {
                         if (expand_items<BLOCK>(a, sm, ec, base + tid, BLOCK, total, pred_next, pred_m)) {
                             if (lane == 0) sm.abort = 1;
                             break;
