@@ -132,6 +132,12 @@ typedef struct {
                                   samples, all of them expanding large rounds for each other through
                                   a job board in shared memory; 0 = the library's choice of kernel.
                                   block_threads / blocks_per_sm then do not apply */
+    int32_t pair_cost;   /* the meeting round's pairwise test (|F_X| x |F_Y| adjacency tests between
+                            the two frontiers instead of scanning X's rows) runs when |F_X| x |F_Y| x
+                            pair_cost is below the arcs of F_X: the cost of one test counted in arc
+                            reads.  1..1048576; 0 = 16, or with KAD_RUN_AUTOTUNE the fastest of 4, 16
+                            and 64 on this graph; KAD_ERR_INVALID_ARG outside.  Results do not depend
+                            on it */
 } kad_options;
 
 #define KAD_RUN_TIMING 1u      /* fill kad_result.t_* with CUDA-event times of each phase */
@@ -139,9 +145,11 @@ typedef struct {
                                   all 0) times the same query, truncated after 4 epochs, twice under each
                                   candidate -- block per sample 512x2, 256x4, 256x2, 1024x1, 128x8, and
                                   warp per sample with 8 or 24 samples per block -- and keeps the fastest
-                                  for the graph's later runs (graphs under 16384 vertices keep the
-                                  default).  Off by default: the degree rule picks the fastest on every
-                                  configured workload, and tuning costs 14 truncated runs */
+                                  for the graph's later runs; then, when pair_cost is 0, it times the
+                                  chosen variant the same way with pair_cost 4 and 64 and keeps the
+                                  fastest of those and 16 (graphs under 16384 vertices keep the
+                                  defaults).  Off by default: the degree rule picks the fastest on every
+                                  configured workload, and tuning costs 18 truncated runs */
 #define KAD_RUN_COMPLETION_ORDER 4u /* the non-deterministic mode of the epoch-based framework
                                   (Section 3.1; local-/shared-frame of Section 3.2): epoch k holds
                                   the samples that were the (kN+1)-th to (k+1)N-th to complete,
@@ -214,7 +222,7 @@ typedef struct {
     uint64_t issued_at_stop;
     /* the warp-per-sample kernel's sampling contexts per block (0: the block-per-sample kernel ran) */
     int32_t samples_per_block_used;
-    int32_t reserved_;
+    int32_t pair_cost_used;    /* the pairwise test's cost factor the sampling kernel ran with */
     /* of phase_cycles' BFS stage: cycles in expansion passes, and in round closes
        (the rest is pairwise tests and loading frontiers) */
     uint64_t bfs_split_cycles[2];

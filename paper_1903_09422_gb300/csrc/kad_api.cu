@@ -34,6 +34,8 @@ namespace {
 const int kDefaultEpoch = 1000;   // N = 1000 (Appendix C.2)
 const int kDefaultCalibDiv = 100; // tau0 ~ omega / 100
 const int kDefaultMcap = 256;
+const int kDefaultPairCost = KAD_DEFAULT_PAIR_COST;
+const int kMaxPairCost = 1 << 20;
 const int kMext = 3840; // meeting-set members per slot recorded beyond the first mcap
 const int32_t kTuneMinVertices = 16384;   // smaller graphs keep the default variant
 const uint32_t kTuneEpochs = 4;           // epochs of the truncated query timed per candidate
@@ -102,6 +104,7 @@ struct kad_graph {
     bool poisoned = false;
     Workspace ws;
     int tuned_threads = 0, tuned_per_sm = 0; // sampling-kernel variant chosen for this graph (0 = not yet)
+    int tuned_pair_cost = 0;                 // pairwise-test cost factor chosen for it (0 = not yet)
 };
 
 namespace {
@@ -549,12 +552,16 @@ struct LaunchCfg {
     size_t dyn_smem; // bytes of dynamic shared memory (the slot bitmap) or 0
     int warp = 0;    // 1: the warp-per-sample kernel (1024 threads, one block per SM)
     int nctx = 0;    // its sampling contexts (owner warps) per block
+    int pair_cost = kDefaultPairCost; // the pairwise test's cost factor
 };
+
+bool pair_cost_ok(const kad_options &o) { return o.pair_cost >= 0 && o.pair_cost <= kMaxPairCost; }
 
 // Threads per block and blocks per SM.  Unknown combinations fall back to the
 // variant with the same block size and the default occupancy.
 LaunchCfg resolve_cfg(const kad_options &o) {
     LaunchCfg c;
+    if (o.pair_cost > 0) c.pair_cost = o.pair_cost;
     if (o.samples_per_block > 0) {
         c.threads = 1024;
         c.per_sm = 1;
@@ -740,6 +747,7 @@ SampleArgs base_args(kad_graph *g, const Workspace &w, uint64_t seed) {
     a.ctl = w.ctl;
     a.work = w.work;
     a.mcap = kDefaultMcap;
+    a.pair_cost = kDefaultPairCost;
     return a;
 }
 
@@ -761,55 +769,79 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
 
 // The autotuner: the first run on a graph that leaves the kernel variant to the
 // library runs the same query, truncated after kTuneEpochs epochs, twice under
-// each candidate variant and keeps the fastest for the graph.  Every variant
-// computes the same samples, so the choice changes speed only.
+// each candidate variant and keeps the fastest for the graph; when the caller
+// leaves the pairwise test's cost factor open too, the chosen variant is timed
+// the same way under each candidate factor.  Every variant and factor computes
+// the same samples, so the choice changes speed only.
 kad_status autotune(kad_graph *g, Workspace &w, double eps, double delta, const kad_options &o, cudaStream_t st,
                     LaunchCfg &best) {
     best = default_cfg(g, o);
-    if (!g->tuned_threads && g->gd.n < kTuneMinVertices) { // too small to matter
+    // the faster of two truncated runs: the first launch of a variant also pays
+    // for loading its code and for growing the workspace
+    auto time_opts = [&](kad_options o2, double *ms) -> kad_status {
+        o2.max_epochs = kTuneEpochs;
+        o2.flags = (o2.flags | KAD_RUN_TIMING) & ~KAD_RUN_AUTOTUNE;
+        for (int rep = 0; rep < 2; rep++) {
+            kad_result r;
+            memset(&r, 0, sizeof(r));
+            const kad_status s = run_impl(g, w, eps, delta, kTuneSeed, st, &o2, nullptr, nullptr, &r, false);
+            if (s != KAD_OK) return s;
+            if (rep == 0 || r.t_total_ms < *ms) *ms = r.t_total_ms;
+        }
+        return KAD_OK;
+    };
+    const bool small = g->gd.n < kTuneMinVertices; // too small to matter
+    if (!g->tuned_threads && small) {
         g->tuned_threads = best.threads;
         g->tuned_per_sm = best.per_sm;
     }
+    double best_ms = -1.0; // the chosen variant's time at the default factor, if measured here
     if (!g->tuned_threads) {
         // block per sample (threads, blocks per SM), then warp per sample
         // (0, samples per block): one block of 1024 threads per SM
         static const int cand[7][2] = {{512, 2}, {256, 4}, {256, 2}, {1024, 1}, {128, 8}, {0, 8}, {0, 24}};
-        double best_ms = 0.0;
         for (int c = 0; c < 7; c++) {
             kad_options o2 = o;
             o2.block_threads = cand[c][0];
             o2.blocks_per_sm = cand[c][0] ? cand[c][1] : 0;
             o2.samples_per_block = cand[c][0] ? 0 : cand[c][1];
-            o2.max_epochs = kTuneEpochs;
-            o2.flags = (o2.flags | KAD_RUN_TIMING) & ~KAD_RUN_AUTOTUNE;
-            // twice, keeping the faster: the first launch of a variant also pays
-            // for loading its code and for growing the workspace
             double ms = 0.0;
-            for (int rep = 0; rep < 2; rep++) {
-                kad_result r;
-                memset(&r, 0, sizeof(r));
-                const kad_status s = run_impl(g, w, eps, delta, kTuneSeed, st, &o2, nullptr, nullptr, &r, false);
-                if (s != KAD_OK) return s;
-                if (rep == 0 || r.t_total_ms < ms) ms = r.t_total_ms;
-            }
+            const kad_status s = time_opts(o2, &ms);
+            if (s != KAD_OK) return s;
             if (c == 0 || ms < best_ms) {
                 best_ms = ms;
                 g->tuned_threads = cand[c][0] ? cand[c][0] : -1; // -1: warp per sample
                 g->tuned_per_sm = cand[c][1];
             }
         }
+        if (o.pair_cost != 0) best_ms = -1.0; // measured at the caller's factor
     }
-    if (g->tuned_threads > 0) {
-        best.threads = g->tuned_threads;
-        best.per_sm = g->tuned_per_sm;
-        best.dyn_smem = 0;
-        best.warp = 0;
-        best.nctx = 0;
-    } else {
-        kad_options o3 = o;
-        o3.samples_per_block = g->tuned_per_sm;
-        best = resolve_cfg(o3);
+    kad_options o3 = o;
+    o3.block_threads = g->tuned_threads > 0 ? g->tuned_threads : 0;
+    o3.blocks_per_sm = g->tuned_threads > 0 ? g->tuned_per_sm : 0;
+    o3.samples_per_block = g->tuned_threads > 0 ? 0 : g->tuned_per_sm;
+    if (o.pair_cost == 0) {
+        if (!g->tuned_pair_cost && small) g->tuned_pair_cost = kDefaultPairCost;
+        if (!g->tuned_pair_cost) {
+            static const int pcand[3] = {kDefaultPairCost, 4, 64};
+            double pbest = 0.0;
+            for (int c = 0; c < 3; c++) {
+                double ms = best_ms;
+                if (c > 0 || ms < 0.0) {
+                    kad_options o4 = o3;
+                    o4.pair_cost = pcand[c];
+                    const kad_status s = time_opts(o4, &ms);
+                    if (s != KAD_OK) return s;
+                }
+                if (c == 0 || ms < pbest) {
+                    pbest = ms;
+                    g->tuned_pair_cost = pcand[c];
+                }
+            }
+        }
+        o3.pair_cost = g->tuned_pair_cost;
     }
+    best = resolve_cfg(o3);
     return KAD_OK;
 }
 
@@ -836,7 +868,7 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
         o = *opt_in;
     else
         fill_defaults(&o);
-    if (o.epoch_size == 0 || o.calib_div == 0) return KAD_ERR_INVALID_ARG;
+    if (o.epoch_size == 0 || o.calib_div == 0 || !pair_cost_ok(o)) return KAD_ERR_INVALID_ARG;
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(g, cudaGetLastError());
 
     const int32_t n = g->gd.n;
@@ -890,6 +922,7 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
 
     SampleArgs a = base_args(g, w, seed);
     a.mcap = (o.mcap < 0) ? kDefaultMcap : o.mcap;
+    a.pair_cost = cfg.pair_cost;
     a.debug = o.debug;
     a.mode = KAD_MODE_RING;
     a.calib_n = tau0;
@@ -1034,6 +1067,7 @@ kad_status run_impl(kad_graph *g, Workspace &w, double eps, double delta, uint64
     out->slots_used = slots;
     out->block_threads_used = cfg.threads;
     out->blocks_per_sm_used = cfg.per_sm;
+    out->pair_cost_used = cfg.pair_cost;
     out->samples_per_block_used = 0;
     if (cfg.warp) {
         int K = 0, nb = 0;
@@ -1366,7 +1400,8 @@ kad_status kad_run_sharded(kad_graph *g, double eps, double delta, uint64_t seed
         o = *opt_in;
     else
         fill_defaults(&o);
-    if (o.epoch_size == 0 || o.calib_div == 0 || (o.flags & KAD_RUN_COMPLETION_ORDER)) return KAD_ERR_INVALID_ARG;
+    if (o.epoch_size == 0 || o.calib_div == 0 || (o.flags & KAD_RUN_COMPLETION_ORDER) || !pair_cost_ok(o))
+        return KAD_ERR_INVALID_ARG;
     if (cudaSetDevice(g->device) != cudaSuccess) return fail(g, cudaGetLastError());
     ws_adopt(g);
     Workspace &w = g->ws;
@@ -1445,6 +1480,7 @@ kad_status kad_run_sharded(kad_graph *g, double eps, double delta, uint64_t seed
         if (c > 0) {
             SampleArgs a = base_args(g, w, seed);
             a.mcap = (o.mcap < 0) ? kDefaultMcap : o.mcap;
+            a.pair_cost = cfg.pair_cost;
             a.debug = o.debug;
             a.domain = calib ? 1 : 0;
             a.i0 = base + (uint64_t)lo;
@@ -1569,6 +1605,7 @@ kad_status kad_run_sharded(kad_graph *g, double eps, double delta, uint64_t seed
     out->block_threads_used = cfg.threads;
     out->blocks_per_sm_used = cfg.per_sm;
     out->samples_per_block_used = cfg.warp ? cfg.nctx : 0;
+    out->pair_cost_used = cfg.pair_cost;
     out->t_host_ms = now_ms() - t_entry;
     out->t_total_ms = out->t_host_ms;
     s = KAD_OK;
@@ -1615,6 +1652,7 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
         o = *opt;
     else
         fill_defaults(&o);
+    if (!pair_cost_ok(o)) return KAD_ERR_INVALID_ARG;
     LaunchCfg cfg = default_cfg(g, o);
     if (o.debug & KAD_DEBUG_SMEM_BITMAP) choose_bitmap_home(cfg, g->gd.n, g->device);
     Workspace &w = g->ws;
@@ -1638,6 +1676,7 @@ kad_status kad_sample_records(kad_graph *g, uint64_t seed, uint32_t domain, uint
     {
         SampleArgs a = base_args(g, w, seed);
         a.mcap = (o.mcap < 0) ? kDefaultMcap : o.mcap;
+        a.pair_cost = cfg.pair_cost;
         a.debug = o.debug;
         a.domain = domain;
         a.i0 = i0;

@@ -24,6 +24,7 @@
 
 #define KAD_U64MAX 0xffffffffffffffffull
 #define KAD_WORK_WORDS 16
+#define KAD_DEFAULT_PAIR_COST 16 // one pairwise adjacency test counted as 16 arc reads
 
 // sample-kernel output modes
 #define KAD_MODE_RING 1   // a KADABRA run: calibration samples first (counted into c0 and
@@ -106,6 +107,7 @@ struct SampleArgs {
     unsigned long long i0, i1;
     int mode;
     int mcap;
+    int pair_cost; // the meeting round's pairwise test runs when |F_X| |F_Y| pair_cost < arcs of F_X
     int nctx; // warp-per-sample kernel: sampling contexts (owner warps) per block
     uint32_t debug; // KAD_DEBUG_*
     // outputs (RING, RECORD)

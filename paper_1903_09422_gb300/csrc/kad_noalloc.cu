@@ -144,6 +144,7 @@ extern "C" kad_status kad_sample_records_noalloc(int32_t n, const int32_t *d_row
     a.nw = (int32_t)nwords(n);
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
+    a.pair_cost = KAD_DEFAULT_PAIR_COST;
     a.domain = domain;
     a.i0 = i0;
     a.i1 = i0 + (uint64_t)count;

@@ -47,7 +47,6 @@
 #define KAD_LCAP 64     // largest predecessor level searched from its list
 #define KAD_DEG_SCAN 64 // adjacency lists up to this length are always scanned
 #define KAD_PAIR_MIN_ARCS 1024 // rounds with fewer arcs always expand by scanning
-#define KAD_PAIR_COST 16       // one pairwise adjacency test counts as this many arc reads
 #define KAD_WARP_SCAN 256       // adjacency lists up to this length are traced by one warp
 #define KAD_TITEMS 2            // consecutive arcs per thread and pass of a team's adjacency scan
 #define KAD_TBUF 64            // t-side trace steps team 1 can buffer (longer: team 0 traces both sides)
@@ -1290,7 +1289,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             // -- without reading X's rows.  No adjacent pair means no meeting in
             // this round, and the expansion below runs as usual.
             const bool pairs = !(a.debug & KAD_DEBUG_FULL_SCAN) && fx <= BLOCK && sm.dsum[X] >= KAD_PAIR_MIN_ARCS &&
-                               (unsigned long long)fx * (unsigned long long)fy * KAD_PAIR_COST < sm.dsum[X];
+                               (unsigned long long)fx * (unsigned long long)fy * (unsigned)a.pair_cost < sm.dsum[X];
             unsigned long long pred_next = 0, pred_m = 0;
             if (pairs) {
                 if (tid < fx) {

@@ -49,7 +49,6 @@
 #define W_DEG_SCAN 128     // adjacency lists up to this length are always scanned in a trace step
 #define W_PAIR_MIN_ARCS 1024
 #define W_PROBE_MIN_ARCS 256 // rounds with more arcs are probed for the meeting before claiming
-#define W_PAIR_COST 16
 #define W_WAIT_NS 20000000000ull // a wait without progress gives up after 20 s
 
 namespace {
@@ -697,7 +696,7 @@ __device__ __noinline__ void w_search(const SampleArgs &a, WShared &S, int c) {
         }
         __syncwarp();
         const bool pairs = !(a.debug & KAD_DEBUG_FULL_SCAN) && fx <= 32 && dX >= W_PAIR_MIN_ARCS &&
-                           (unsigned long long)fx * (unsigned long long)fy * W_PAIR_COST < dX;
+                           (unsigned long long)fx * (unsigned long long)fy * (unsigned)a.pair_cost < dX;
         if (pairs) {
             WWarp &W = S.w[c];
             if (lane < fx) {

@@ -32,7 +32,7 @@ class Options(ctypes.Structure):
     _fields_ = [("epoch_size", ctypes.c_uint32), ("calib_div", ctypes.c_uint32), ("ring_epochs", ctypes.c_uint32),
                 ("slots", ctypes.c_int32), ("mcap", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("flags", ctypes.c_uint32), ("debug", ctypes.c_uint32),
-                ("max_epochs", ctypes.c_uint32), ("samples_per_block", ctypes.c_int32)]
+                ("max_epochs", ctypes.c_uint32), ("samples_per_block", ctypes.c_int32), ("pair_cost", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -51,7 +51,7 @@ class Result(ctypes.Structure):
                 ("t_table_ms", ctypes.c_double), ("t_dev_calib_ms", ctypes.c_double),
                 ("t_dev_first_close_ms", ctypes.c_double), ("t_dev_stop_ms", ctypes.c_double),
                 ("t_dev_end_ms", ctypes.c_double), ("issued_at_stop", ctypes.c_uint64),
-                ("samples_per_block_used", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("samples_per_block_used", ctypes.c_int32), ("pair_cost_used", ctypes.c_int32),
                 ("bfs_split_cycles", ctypes.c_uint64 * 2)]
 
 PHASE_NAMES = ("draw", "bfs", "meet", "trace", "reset", "close")
@@ -376,7 +376,8 @@ def _result_scalars(r):
                                     "t_calib_ms", "t_ads_ms", "t_ads_kernel_ms", "ads_launches", "slots_used",
                                     "kernel_launches", "block_threads_used", "blocks_per_sm_used", "t_host_ms",
                                     "t_setup_ms", "t_table_ms", "t_dev_calib_ms", "t_dev_first_close_ms",
-                                    "t_dev_stop_ms", "t_dev_end_ms", "issued_at_stop", "samples_per_block_used")}
+                                    "t_dev_stop_ms", "t_dev_end_ms", "issued_at_stop", "samples_per_block_used",
+                                    "pair_cost_used")}
     d["counters"] = dict(zip(WORK_NAMES, (int(x) for x in r.work)))
     d["phase_cycles"] = dict(zip(PHASE_NAMES, (int(x) for x in r.phase_cycles)))
     d["bfs_split_cycles"] = dict(passes=int(r.bfs_split_cycles[0]), close=int(r.bfs_split_cycles[1]))

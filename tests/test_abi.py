@@ -58,3 +58,39 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     assert lib.kad_run(None, 0.1, 0.1, 1, None, None, None) == 1
     assert lib.kad_run_order(None, None, 0) == 1
     lib.kad_graph_free(None)
+
+
+def header_struct_fields(name):
+    """(field, bytes) of `typedef struct { ... } name;` in include/kad.h, in order."""
+    src = open(os.path.join(ROOT, "include", "kad.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src).group(1)
+    scalar = {"int32_t": 4, "uint32_t": 4, "int64_t": 8, "uint64_t": 8, "double": 8}
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, rest = decl.split(None, 1)
+        for item in rest.split(","):
+            item = item.strip()
+            m = re.fullmatch(r"(\*?)\s*(\w+)(?:\[(\d+)\])?", item)
+            assert m, item
+            size = 8 if m.group(1) else scalar[ctype]
+            out.append((m.group(2), size * int(m.group(3) or 1)))
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("kad_options", "Options"), ("kad_result", "Result"),
+                                          ("kad_server_options", "ServerOptions")])
+def test_binding_structs_match_the_header(cname, pyname):
+    from paper_1903_09422_gb300 import kad
+    cls = getattr(kad, pyname)
+    py = [(f[0], ctypes.sizeof(f[1])) for f in cls._fields_]
+    assert py == header_struct_fields(cname)
+
+
+def test_pair_cost_defaults_to_the_library_choice(lib):
+    from paper_1903_09422_gb300 import kad
+    assert kad.options().pair_cost == 0
+    assert kad.options(pair_cost=64).pair_cost == 64

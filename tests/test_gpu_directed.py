@@ -124,7 +124,8 @@ def test_symmetric_graph_as_directed_equals_undirected_run(kad):
                                  dict(debug=1), dict(debug=4), dict(debug=8), dict(debug=16), dict(debug=64),
                                  dict(mcap=0), dict(mcap=0, debug=128), dict(slots=3, ring_epochs=2),
                                  dict(samples_per_block=8), dict(samples_per_block=32),
-                                 dict(samples_per_block=32, debug=1), dict(samples_per_block=32, debug=4)])
+                                 dict(samples_per_block=32, debug=1), dict(samples_per_block=32, debug=4),
+                                 dict(pair_cost=1), dict(pair_cost=1, samples_per_block=8)])
 def test_directed_result_independent_of_launch_configuration(kad, opt):
     g = gen.rmat_directed(13, 8, seed=3)
     eps, delta, seed = 0.03, 0.1, 11

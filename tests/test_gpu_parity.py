@@ -182,6 +182,31 @@ def test_meeting_round_methods_agree_on_hub_graph(kad):
         assert a["counters"][k] == orc["counters"][k] == b["counters"][k], k
 
 
+@pytest.mark.parametrize("pair_cost", [1, 4, 64, 1 << 20])
+def test_pair_cost_changes_speed_not_results(kad, pair_cost):
+    # The pairwise test's cost factor decides how often the meeting round tests
+    # frontier pairs instead of scanning the expanding side's rows (1: whenever
+    # the frontiers' product is below the arcs; 2^20: practically never).  The
+    # block- and warp-per-sample kernels' records, work counters and full runs
+    # equal the oracle's at every factor.
+    g = gen.rmat(15, 16, seed=4)
+    orc = O.samples(g, 13, 0, 1500)
+    ref = O.kadabra(g, 0.02, 0.1, 13)
+    with kad.Graph.from_csr(g) as G:
+        recs = [G.sample_records(13, 0, 1500, pair_cost=pair_cost),
+                G.sample_records(13, 0, 1500, pair_cost=pair_cost, samples_per_block=8)]
+        runs = [G.run(0.02, 0.1, 13, pair_cost=pair_cost),
+                G.run(0.02, 0.1, 13, pair_cost=pair_cost, samples_per_block=24)]
+    for rec in recs:
+        compare_records(rec, orc)
+        for k in ("expanded", "scanned", "labelled", "pred_arcs", "increments"):
+            assert rec["counters"][k] == orc["counters"][k], k
+    for r in runs:
+        assert r["pair_cost_used"] == pair_cost
+        assert (r["tau"], r["epochs"]) == (ref["tau"], ref["epochs"])
+        np.testing.assert_array_equal(r["counts"], ref["counts"])
+
+
 def test_hub_graph_records_and_runs_per_variant(kad):
     # A graph with hub rows (long levels, meetings found mid-level, samples
     # abandoned after the stop): records, work counters and full-run counts
@@ -251,11 +276,16 @@ def test_autotuner_keeps_results_and_choice(kad):
         r1 = G.run(0.05, 0.1, 8, flags=kad.KAD_RUN_AUTOTUNE)
         r2 = G.run(0.05, 0.1, 8, flags=kad.KAD_RUN_AUTOTUNE)
         r3 = G.run(0.05, 0.1, 8)  # without the flag: the average-degree rule
+        # the caller's factor stands; the tuned variant is kept
+        r4 = G.run(0.05, 0.1, 8, flags=kad.KAD_RUN_AUTOTUNE, pair_cost=32)
     pick = lambda r: (r["block_threads_used"], r["blocks_per_sm_used"], r["samples_per_block_used"])
     assert pick(r1) in {(512, 2, 0), (256, 4, 0), (256, 2, 0), (1024, 1, 0), (128, 8, 0), (1024, 1, 8), (1024, 1, 24)}
-    assert pick(r1) == pick(r2)
+    assert pick(r1) == pick(r2) == pick(r4)
+    assert r1["pair_cost_used"] in {4, 16, 64} and r2["pair_cost_used"] == r1["pair_cost_used"]
+    assert r4["pair_cost_used"] == 32
     assert (r3["block_threads_used"], r3["blocks_per_sm_used"]) == ((256, 4) if g.m <= 8 * g.n else (512, 2))
-    for r in (r1, r2, r3):
+    assert r3["pair_cost_used"] == 16
+    for r in (r1, r2, r3, r4):
         assert r["tau"] == ref["tau"]
         np.testing.assert_array_equal(r["counts"], ref["counts"])
 
@@ -357,8 +387,15 @@ def test_invalid_run_arguments(kad):
             with pytest.raises(kad.KadError) as e:
                 G.run(eps, delta, 1)
             assert e.value.status == 1
+        for pc in (-1, (1 << 20) + 1):
+            with pytest.raises(kad.KadError) as e:
+                G.run(0.1, 0.1, 1, pair_cost=pc)
+            assert e.value.status == 1
+            with pytest.raises(kad.KadError) as e:
+                G.sample_records(1, 0, 10, pair_cost=pc)
+            assert e.value.status == 1
         r = G.run(0.1, 0.1, 1)  # the handle stays usable
-        assert r["tau"] > 0
+        assert r["tau"] > 0 and r["pair_cost_used"] == 16
 
 
 def test_workspace_kept_across_graphs(kad):

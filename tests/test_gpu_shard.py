@@ -100,16 +100,19 @@ def test_sharded_run_equals_single_gpu_run(kad, world):
 
 def test_sharded_run_ragged_chunks_and_kernels(kad):
     # an epoch size that 3 ranks cannot split evenly, a disconnected graph, the
-    # warp-per-sample kernel on one configuration, and a diamond chain whose
+    # warp-per-sample kernel on one configuration, a hub graph whose meeting
+    # rounds take the pairwise test at every chance, and a diamond chain whose
     # path counts saturate (overflowed samples are counted alike)
     cases = [(gen.grid(40, seed=3), 0.05, 3, dict(epoch_size=250)),
              (GRAPHS_MIXED(), 0.05, 4, {}),
              (gen.rmat(11, 8, seed=2), 0.04, 5, dict(samples_per_block=8)),
+             (gen.rmat(12, 16, seed=4), 0.04, 7, dict(pair_cost=1)),
              (diamond(70), 0.05, 6, {})]
     for g, eps, seed, opt in cases:
         ref = O.kadabra(g, eps, 0.1, seed, epoch=opt.get("epoch_size", 1000))
         for r in run_ranks(kad, g, 3, eps, 0.1, seed, **opt):
             same_as(r, ref)
+            assert r["pair_cost_used"] == opt.get("pair_cost", 16)
 
 
 def test_sharded_truncated_run_at_full_size(kad):
@@ -129,6 +132,8 @@ def test_sharded_run_rejects_bad_arguments(kad):
             G.run_sharded(0.05, 0.1, 1, 2, 2, lambda b: b)  # rank out of range
         with pytest.raises(RuntimeError):
             G.run_sharded(0.05, 0.1, 1, 0, 1, lambda b: b, flags=kad.KAD_RUN_COMPLETION_ORDER)
+        with pytest.raises(RuntimeError):
+            G.run_sharded(0.05, 0.1, 1, 0, 1, lambda b: b, pair_cost=-1)
         with pytest.raises(RuntimeError):
             G.run_sharded(0.05, 0.1, 1, 0, 1, lambda b: None)  # a failing collective
 
