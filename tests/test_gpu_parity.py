@@ -290,6 +290,25 @@ def test_autotuner_keeps_results_and_choice(kad):
         np.testing.assert_array_equal(r["counts"], ref["counts"])
 
 
+def test_autotuner_cost_stage_after_a_fixed_cost_run(kad):
+    # The variant tuned under a caller's cost factor is kept; a later run that
+    # leaves the factor open times all three factors on that variant.
+    g = gen.rmat(15, 16, seed=7)
+    assert g.n >= 16384
+    ref = O.kadabra(g, 0.05, 0.1, 3)
+    with kad.Graph.from_csr(g) as G:
+        r1 = G.run(0.05, 0.1, 3, flags=kad.KAD_RUN_AUTOTUNE, pair_cost=2)
+        r2 = G.run(0.05, 0.1, 3, flags=kad.KAD_RUN_AUTOTUNE)
+        r3 = G.run(0.05, 0.1, 3, flags=kad.KAD_RUN_AUTOTUNE)
+    pick = lambda r: (r["block_threads_used"], r["blocks_per_sm_used"], r["samples_per_block_used"])
+    assert pick(r1) == pick(r2) == pick(r3)
+    assert r1["pair_cost_used"] == 2
+    assert r2["pair_cost_used"] in {4, 8, 16} and r3["pair_cost_used"] == r2["pair_cost_used"]
+    for r in (r1, r2, r3):
+        assert r["tau"] == ref["tau"]
+        np.testing.assert_array_equal(r["counts"], ref["counts"])
+
+
 def test_fg_kernel_matches_oracle(kad):
     g = gen.rmat(12, 8, seed=1)
     ref = O.kadabra(g, 0.05, 0.1, 1)
