@@ -46,17 +46,17 @@ BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=0, 
 # the kernel source file it was measured on.  A workload without an entry, or
 # whose kernel source has changed since, reports traffic null.  Each figure is a
 # query's first sampling launch, which under ncu computes every sample its ring
-# admits: rmat20 2.691 GB over 31,000 samples; rmat20d (directed) 2.147 GB over
-# 36,000; rmat18 0.770 GB over 31,000; hyp4m 28.65 GB over 142,000; grid2048
-# 714.8 GB over 56,000 (profiles/k_sample_rmat20_dram.md,
+# admits: rmat20 2.710 GB over 31,000 samples; rmat20d (directed) 2.160 GB over
+# 36,000; rmat18 0.772 GB over 31,000; hyp4m 28.79 GB over 142,000; grid2048
+# 715.1 GB over 56,000 (profiles/k_sample_rmat20_dram.md,
 # profiles/k_sample_rmat20d_dram.md, profiles/k_sample_hyp4m_grid2048_dram.md;
 # rmat18 from the same command with --workload rmat18).
 NCU_TRAFFIC_PER_SAMPLE = {
-    ("k_sample", "rmat20"): (86_816, "01deaa8b217a9845"),
-    ("k_sample", "rmat20d"): (59_632, "01deaa8b217a9845"),
-    ("k_sample", "rmat18"): (24_826, "01deaa8b217a9845"),
-    ("k_sample", "hyp4m"): (201_789, "01deaa8b217a9845"),
-    ("k_sample", "grid2048"): (12_765_063, "01deaa8b217a9845"),
+    ("k_sample", "rmat20"): (87_432, "58167c3abbacc959"),
+    ("k_sample", "rmat20d"): (60_008, "58167c3abbacc959"),
+    ("k_sample", "rmat18"): (24_913, "58167c3abbacc959"),
+    ("k_sample", "hyp4m"): (202_755, "58167c3abbacc959"),
+    ("k_sample", "grid2048"): (12_768_751, "58167c3abbacc959"),
 }
 KERNEL_SOURCE = {"k_sample": "kad_sample.cu", "k_wsample": "kad_wsample.cu"}
 

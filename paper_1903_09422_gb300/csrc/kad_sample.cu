@@ -118,7 +118,66 @@ struct Smem {
     unsigned long long ovf_acc;
     unsigned long long acc[KAD_WORK_WORDS];
     long long tmark;
+    // the next sample's pair, drawn ahead by warp 1 while warp 0 draws a small
+    // meeting set: the raw index, s and t, whether they share a component, the
+    // bounds of their rows, and the stream after the two draws (pre_ok: set;
+    // pre_use: the next sample is that index)
+    unsigned long long pre_g, pre_w0, pre_w1;
+    uint32_t pre_blk;
+    int pre_pos, pre_ok, pre_use, pre_s, pre_t, pre_same;
+    int pre_rs[2], pre_re[2];
 };
+
+// The sample a raw index g of the launch's counter stands for (~0: none):
+// calibration samples first, then adaptive ones (RING); [i0, i1) in RECORD mode.
+__device__ __forceinline__ unsigned long long sample_of(const SampleArgs &a, unsigned long long g, int &calib,
+                                                        uint32_t &dom) {
+    calib = 0;
+    dom = a.domain;
+    if (a.mode == KAD_MODE_RECORD) return (g < a.i1) ? g : ~0ull;
+    if (g < a.calib_n) {
+        calib = 1;
+        dom = 1;
+        return g;
+    }
+    dom = 0;
+    return (a.i0 + (g - a.calib_n) < a.i1) ? a.i0 + (g - a.calib_n) : ~0ull;
+}
+
+// One thread draws the pair of the sample after this one (the same draws, in
+// the same stream, as the pair draw at the start of a sample) and leaves it in
+// shared memory with the loads the start of the sample needs.
+template <int BLOCK>
+__device__ __noinline__ void draw_ahead(const SampleArgs &a, Smem<BLOCK> &sm) {
+    const int32_t n = a.n;
+    const unsigned long long g = atomicAdd(&a.ctl->next, 1ull);
+    int calib;
+    uint32_t dom;
+    const unsigned long long idx = sample_of(a, g, calib, dom);
+    sm.pre_g = g;
+    if (idx != ~0ull) {
+        Stream ps;
+        ps.init(a.key0, a.key1, idx, dom);
+        const int s = (int)ps.uniform((unsigned long long)n, a.ctl);
+        int t = (int)ps.uniform((unsigned long long)(n - 1), a.ctl);
+        if (t >= s) t++;
+        const int cs = __ldg(a.comp + s), ct = __ldg(a.comp + t);
+        const int r0 = __ldg(a.rows[0] + s), r0e = __ldg(a.rows[0] + s + 1);
+        const int r1 = __ldg(a.rows[1] + t), r1e = __ldg(a.rows[1] + t + 1);
+        sm.pre_s = s;
+        sm.pre_t = t;
+        sm.pre_blk = ps.blk;
+        sm.pre_pos = ps.pos;
+        sm.pre_w0 = ps.w0;
+        sm.pre_w1 = ps.w1;
+        sm.pre_same = (cs == ct) ? 1 : 0;
+        sm.pre_rs[0] = r0;
+        sm.pre_re[0] = r0e;
+        sm.pre_rs[1] = r1;
+        sm.pre_re[1] = r1e;
+    }
+    sm.pre_ok = 1;
+}
 
 template <int BLOCK>
 __device__ __forceinline__ int block_excl_scan(int v, int *wtmp, int &total) {
@@ -1167,6 +1226,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
     if (tid == 0) {
         sm.probe_score = 4;
         sm.probe_rounds = 0;
+        sm.pre_ok = 0;
     }
     if (tid == 0 && a.mode == KAD_MODE_RING) atomicCAS(&a.ctl->t_start, 0ull, global_ns());
     Stream st;
@@ -1183,20 +1243,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             int calib = 0;
             uint32_t dom = a.domain;
             const bool stopped = (a.mode == KAD_MODE_RING) && (*(volatile int *)&a.ctl->stop != 0);
+            const bool ahead = sm.pre_ok != 0; // the index was taken (and its pair drawn) by draw_ahead
             if (!stopped) {
-                const unsigned long long g = (g_pre != ~0ull) ? g_pre : atomicAdd(&a.ctl->next, 1ull);
-                g_pre = ~0ull;
-                if (a.mode == KAD_MODE_RECORD) {
-                    if (g < a.i1) idx = g;
-                } else if (g < a.calib_n) {
-                    idx = g;
-                    calib = 1;
-                    dom = 1;
-                } else if (a.i0 + (g - a.calib_n) < a.i1) {
-                    idx = a.i0 + (g - a.calib_n);
-                    dom = 0;
-                }
+                const unsigned long long g =
+                    (g_pre != ~0ull) ? g_pre : ahead ? sm.pre_g : atomicAdd(&a.ctl->next, 1ull);
+                idx = sample_of(a, g, calib, dom);
             }
+            g_pre = ~0ull;
+            sm.pre_ok = 0;
+            sm.pre_use = (ahead && idx != ~0ull) ? 1 : 0;
             sm.idx = idx;
             sm.calib = calib;
             sm.dom = dom;
@@ -1211,17 +1266,32 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
 
         // ---------------------------------------------------- pair draw
         if (tid == 0) {
-            st.init(a.key0, a.key1, idx, sm.dom);
-            const int s = (int)st.uniform((unsigned long long)n, a.ctl);
-            int t = (int)st.uniform((unsigned long long)(n - 1), a.ctl);
-            if (t >= s) t++;
+            const bool ahead = sm.pre_use != 0;
+            int s, t;
+            if (ahead) {
+                st.k0 = a.key0;
+                st.k1 = a.key1;
+                st.idx = idx;
+                st.dom = sm.dom;
+                st.blk = sm.pre_blk;
+                st.pos = sm.pre_pos;
+                st.w0 = sm.pre_w0;
+                st.w1 = sm.pre_w1;
+                s = sm.pre_s;
+                t = sm.pre_t;
+            } else {
+                st.init(a.key0, a.key1, idx, sm.dom);
+                s = (int)st.uniform((unsigned long long)n, a.ctl);
+                t = (int)st.uniform((unsigned long long)(n - 1), a.ctl);
+                if (t >= s) t++;
+            }
             sm.s = s;
             sm.t = t;
             sm.tail[0] = sm.tail[1] = 0;
             sm.D = 0;
             sm.abort = 0;
             sm.mcount = 0;
-            if (__ldg(a.comp + s) == __ldg(a.comp + t)) {
+            if (ahead ? sm.pre_same != 0 : __ldg(a.comp + s) == __ldg(a.comp + t)) {
                 *(uint4 *)lab_at(label, s) = make_uint4(1u, 0u, 1u, 0u);            // s side, level 0, sigma 1
                 *(uint4 *)lab_at(label, t) = make_uint4(KAD_SIDE | 1u, 0u, 1u, 0u); // t side, level 0, sigma 1
                 if (!nobits) {
@@ -1237,10 +1307,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                 sm.lvs[0][0] = sm.lvs[1][0] = 0;
                 sm.lvs[0][1] = sm.lvs[1][1] = 1;
                 // each root's row in its side's direction: out-arcs of s, in-arcs of t
-                sm.root_rs[0] = __ldg(a.rows[0] + s);
-                sm.root_rs[1] = __ldg(a.rows[1] + t);
-                sm.dsum[0] = (unsigned long long)(__ldg(a.rows[0] + s + 1) - sm.root_rs[0]);
-                sm.dsum[1] = (unsigned long long)(__ldg(a.rows[1] + t + 1) - sm.root_rs[1]);
+                const int r0 = ahead ? sm.pre_rs[0] : __ldg(a.rows[0] + s);
+                const int r1 = ahead ? sm.pre_rs[1] : __ldg(a.rows[1] + t);
+                const int r0e = ahead ? sm.pre_re[0] : __ldg(a.rows[0] + s + 1);
+                const int r1e = ahead ? sm.pre_re[1] : __ldg(a.rows[1] + t + 1);
+                sm.root_rs[0] = r0;
+                sm.root_rs[1] = r1;
+                sm.dsum[0] = (unsigned long long)(r0e - r0);
+                sm.dsum[1] = (unsigned long long)(r1e - r1);
                 sm.D = -1; // searching
                 // round 0: its flags, and its expansion counted ahead (one root)
                 sm.met[0] = 0;
@@ -1538,6 +1612,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             rnd++;
         }
 
+        const int D = sm.D;
+        // a small recorded M is drawn by warp 0 alone, and warp 1 draws the next
+        // sample's pair meanwhile
+        const bool small_m = D > 0 && sm.mcount <= 32 && sm.mcount <= mcap + mext;
         if (tid == 0) {
             const long long now = clock64();
             sm.acc[9] += (unsigned long long)(now - sm.tmark);
@@ -1545,9 +1623,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             // the next sample's index, fetched while this one is finished (an
             // index taken after the run stopped is simply not computed: its
             // epoch lies beyond the stop epoch)
-            g_pre = atomicAdd(&a.ctl->next, 1ull);
+            if (!small_m) g_pre = atomicAdd(&a.ctl->next, 1ull);
         }
-        const int D = sm.D;
         unsigned long long sst = 0;
         // ---------------------------------------------------- meeting draw
         if (D > 0) {
@@ -1557,7 +1634,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
             // memory, the next mext in the slot's extension
             const int mtot = mcap + mext;
             const int mc0 = sm.mcount; // final: the round ended at a barrier
-            if (mc0 <= 32 && mc0 <= mtot) {
+            if (small_m) {
                 // A small recorded M (most samples): warp 0 alone, one member per
                 // lane -- weights, their saturating sum, the draw, and each
                 // member's exclusive prefix in id order by shuffles.
@@ -1594,6 +1671,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sample(const SampleArgs a) {
                     const unsigned hit = __ballot_sync(FULL_MASK, lane < mc0 && ex <= r && kad_sat_add(ex, w) > r);
                     const int chosen = __shfl_sync(FULL_MASK, id, hit ? __ffs(hit) - 1 : 0);
                     if (tid == 0) sm.mid = hit ? chosen : -1;
+                } else if (tid == 32) {
+                    draw_ahead<BLOCK>(a, sm);
                 }
                 __syncthreads();
                 sst = sm.sst;
