@@ -480,7 +480,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tight-vd", action="store_true", help="the double-sweep vertex-diameter bound (undirected)")
     ap.add_argument("--no-completion-order", action="store_true", help="skip the completion-order comparison")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
@@ -683,7 +683,8 @@ def main():
                          "kernel_ms": statistics.median(kt)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * (g.n + 1) + 4 * g.m),
                     "d2h_bytes_per_step": int(8 * g.n), "steps": args.e2e_steps,
-                    "ms_per_step": 1000 * statistics.mean(e2e_times)},
+                    "ms_per_step": 1000 * statistics.mean(e2e_times),
+                    "step_ms": [round(1000 * t, 3) for t in e2e_times]},
             "phase_share": phase_share(results),
             "phase_cycles_per_sample": {k: round(v / max(1, sum(r["samples_computed"] for r in results)))
                                         for k, v in phase_total(results).items()},
