@@ -43,29 +43,34 @@ BYTES_PER = dict(expanded=8, scanned=8, labelled=12, pred_arcs=8, trace_arcs=0, 
 
 # DRAM traffic of the sampling kernel measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), bytes per computed sample, with the SHA-256 prefix of
-# the kernel source file it was measured on.  A workload without an entry, or
+# the kernel source it was measured on (source_hash).  A workload without an entry, or
 # whose kernel source has changed since, reports traffic null.  Each figure is a
 # query's first sampling launch, which under ncu computes every sample its ring
-# admits: rmat20 2.710 GB over 31,000 samples; rmat20d (directed) 2.160 GB over
-# 36,000; rmat18 0.772 GB over 31,000; hyp4m 28.79 GB over 142,000; grid2048
-# 715.1 GB over 56,000 (profiles/k_sample_rmat20_dram.md,
+# admits: rmat20 2.727 GB over 31,000 samples; rmat20d (directed) 2.212 GB over
+# 36,000; rmat18 0.757 GB over 31,000; hyp4m 28.79 GB over 142,000; grid2048
+# 715.3 GB over 56,000 (profiles/k_sample_rmat20_dram.md,
 # profiles/k_sample_rmat20d_dram.md, profiles/k_sample_hyp4m_grid2048_dram.md;
 # rmat18 from the same command with --workload rmat18).
 NCU_TRAFFIC_PER_SAMPLE = {
-    ("k_sample", "rmat20"): (87_432, "58167c3abbacc959"),
-    ("k_sample", "rmat20d"): (60_008, "58167c3abbacc959"),
-    ("k_sample", "rmat18"): (24_913, "58167c3abbacc959"),
-    ("k_sample", "hyp4m"): (202_755, "58167c3abbacc959"),
-    ("k_sample", "grid2048"): (12_768_751, "58167c3abbacc959"),
+    ("k_sample", "rmat20"): (87_975, "9232d11af77f9ede"),
+    ("k_sample", "rmat20d"): (61_436, "9232d11af77f9ede"),
+    ("k_sample", "rmat18"): (24_431, "9232d11af77f9ede"),
+    ("k_sample", "hyp4m"): (202_770, "9232d11af77f9ede"),
+    ("k_sample", "grid2048"): (12_772_322, "9232d11af77f9ede"),
 }
-KERNEL_SOURCE = {"k_sample": "kad_sample.cu", "k_wsample": "kad_wsample.cu"}
+# a kernel's source file and the headers it includes (launch arguments, defaults)
+KERNEL_SOURCE = {"k_sample": ("kad_sample.cu", "kad_internal.cuh", "kad_device.cuh"),
+                 "k_wsample": ("kad_wsample.cu", "kad_internal.cuh", "kad_device.cuh")}
 
 
 def source_hash(kernel):
+    """SHA-256 prefix of the kernel's source file and its headers, in that order."""
     import hashlib
-    path = os.path.join(ROOT, "paper_1903_09422_gb300", "csrc", KERNEL_SOURCE[kernel])
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCE[kernel]:
+        with open(os.path.join(ROOT, "paper_1903_09422_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic_per_sample(kernel, workload):

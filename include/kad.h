@@ -135,7 +135,7 @@ typedef struct {
     int32_t pair_cost;   /* the meeting round's pairwise test (|F_X| x |F_Y| adjacency tests between
                             the two frontiers instead of scanning X's rows) runs when |F_X| x |F_Y| x
                             pair_cost is below the arcs of F_X: the cost of one test counted in arc
-                            reads.  1..1048576; 0 = 16, or with KAD_RUN_AUTOTUNE the fastest of 4, 8
+                            reads.  1..1048576; 0 = 8, or with KAD_RUN_AUTOTUNE the fastest of 4, 8
                             and 16 on this graph; KAD_ERR_INVALID_ARG outside.  Results do not depend
                             on it */
 } kad_options;
@@ -146,8 +146,8 @@ typedef struct {
                                   candidate -- block per sample 512x2, 256x4, 256x2, 1024x1, 128x8, and
                                   warp per sample with 8 or 24 samples per block -- and keeps the fastest
                                   for the graph's later runs; then, when pair_cost is 0, it times the
-                                  chosen variant the same way with pair_cost 8 and 4 and keeps the
-                                  fastest of those and 16 (graphs under 16384 vertices keep the
+                                  chosen variant the same way with pair_cost 4 and 16 and keeps the
+                                  fastest of those and 8 (graphs under 16384 vertices keep the
                                   defaults).  Off by default: the degree rule picks the fastest on every
                                   configured workload, and tuning costs 18 truncated runs */
 #define KAD_RUN_COMPLETION_ORDER 4u /* the non-deterministic mode of the epoch-based framework

@@ -823,7 +823,7 @@ kad_status autotune(kad_graph *g, Workspace &w, double eps, double delta, const 
     if (o.pair_cost == 0) {
         if (!g->tuned_pair_cost && small) g->tuned_pair_cost = kDefaultPairCost;
         if (!g->tuned_pair_cost) {
-            static const int pcand[3] = {kDefaultPairCost, 8, 4};
+            static const int pcand[3] = {kDefaultPairCost, 4, 16};
             double pbest = 0.0;
             for (int c = 0; c < 3; c++) {
                 double ms = best_ms;

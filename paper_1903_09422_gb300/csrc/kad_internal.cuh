@@ -24,7 +24,7 @@
 
 #define KAD_U64MAX 0xffffffffffffffffull
 #define KAD_WORK_WORDS 16
-#define KAD_DEFAULT_PAIR_COST 16 // one pairwise adjacency test counted as 16 arc reads
+#define KAD_DEFAULT_PAIR_COST 8 // one pairwise adjacency test counted as 8 arc reads
 
 // sample-kernel output modes
 #define KAD_MODE_RING 1   // a KADABRA run: calibration samples first (counted into c0 and

@@ -284,7 +284,7 @@ def test_autotuner_keeps_results_and_choice(kad):
     assert r1["pair_cost_used"] in {4, 8, 16} and r2["pair_cost_used"] == r1["pair_cost_used"]
     assert r4["pair_cost_used"] == 32
     assert (r3["block_threads_used"], r3["blocks_per_sm_used"]) == ((256, 4) if g.m <= 8 * g.n else (512, 2))
-    assert r3["pair_cost_used"] == 16
+    assert r3["pair_cost_used"] == 8
     for r in (r1, r2, r3, r4):
         assert r["tau"] == ref["tau"]
         np.testing.assert_array_equal(r["counts"], ref["counts"])
@@ -414,7 +414,7 @@ def test_invalid_run_arguments(kad):
                 G.sample_records(1, 0, 10, pair_cost=pc)
             assert e.value.status == 1
         r = G.run(0.1, 0.1, 1)  # the handle stays usable
-        assert r["tau"] > 0 and r["pair_cost_used"] == 16
+        assert r["tau"] > 0 and r["pair_cost_used"] == 8
 
 
 def test_workspace_kept_across_graphs(kad):

@@ -112,7 +112,7 @@ def test_sharded_run_ragged_chunks_and_kernels(kad):
         ref = O.kadabra(g, eps, 0.1, seed, epoch=opt.get("epoch_size", 1000))
         for r in run_ranks(kad, g, 3, eps, 0.1, seed, **opt):
             same_as(r, ref)
-            assert r["pair_cost_used"] == opt.get("pair_cost", 16)
+            assert r["pair_cost_used"] == opt.get("pair_cost", 8)
 
 
 def test_sharded_truncated_run_at_full_size(kad):
