@@ -507,8 +507,8 @@ def main():
     if args.workload == "serve":
         return run_serve(args)
 
-    # the serving record's graphs are generated by spawned processes while the
-    # main measurement runs (single GPU only)
+    # the serving record's graphs are generated by spawned processes while this
+    # process builds the library and its own graph (single GPU only)
     serve_pool = serve_async = None
     if not args.no_serving and args.gpus == 1 and int(os.environ.get("WORLD_SIZE", "1")) == 1:
         import multiprocessing as mpx
@@ -541,6 +541,13 @@ def main():
     opts = dict(block_threads=args.block_threads or None, slots=args.slots or None,
                 blocks_per_sm=args.blocks_per_sm or None, samples_per_block=args.samples_per_block or None)
     stream = torch.cuda.current_stream()
+
+    # the graph generators of the serving and other-workload records run on the
+    # host's cores: let them finish first, so that no timed leg (the host's L
+    # table inside a query, the end-to-end leg's host work) shares the host
+    for pending in (serve_async, others_async):
+        if pending is not None:
+            pending.wait(timeout=900)
 
     # inputs resident in HBM before timing
     d_rp = torch.from_numpy(g.row_ptr).to(dev)
