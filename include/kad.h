@@ -132,12 +132,13 @@ typedef struct {
                                   samples, all of them expanding large rounds for each other through
                                   a job board in shared memory; 0 = the library's choice of kernel.
                                   block_threads / blocks_per_sm then do not apply */
-    int32_t pair_cost;   /* the meeting round's pairwise test (|F_X| x |F_Y| adjacency tests between
-                            the two frontiers instead of scanning X's rows) runs when |F_X| x |F_Y| x
-                            pair_cost is below the arcs of F_X: the cost of one test counted in arc
-                            reads.  1..1048576; 0 = 8, or with KAD_RUN_AUTOTUNE the fastest of 4, 8
-                            and 16 on this graph; KAD_ERR_INVALID_ARG outside.  Results do not depend
-                            on it */
+    int32_t pair_cost;   /* the frontier-switch threshold: a round's pairwise test (|F_X| x |F_Y|
+                            adjacency tests between the two frontiers before scanning X's rows) runs
+                            when |F_X| x |F_Y| x pair_cost is below the arcs of F_X, those arcs are at
+                            least 1024 and F_X fits one block's threads (one warp's in the
+                            warp-per-sample kernel): the cost of one test counted in arc reads.
+                            1..1048576; 0 = 8, or with KAD_RUN_AUTOTUNE the fastest of 4, 8 and 16
+                            on this graph; KAD_ERR_INVALID_ARG outside.  Results do not depend on it */
 } kad_options;
 
 #define KAD_RUN_TIMING 1u      /* fill kad_result.t_* with CUDA-event times of each phase */
