@@ -62,3 +62,28 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
         steps = 1
         warmup = 3
     assert bench.run_reference(A()) == 0  # returns before touching the oracle
+
+
+def test_traffic_goes_stale_when_the_kernel_or_its_headers_change(tmp_path, monkeypatch):
+    # bench.py reports the ncu DRAM traffic only for the source it was measured
+    # on: the kernel file and the headers that hold its launch arguments and
+    # defaults.  A copy of the tree with one header byte changed must read stale.
+    import shutil
+    import bench
+    src = os.path.join(ROOT, "paper_1903_09422_gb300", "csrc")
+    dst = tmp_path / "paper_1903_09422_gb300" / "csrc"
+    shutil.copytree(src, dst)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.source_hash("k_sample")
+    assert h0 == bench.source_hash("k_sample")
+    for name in bench.KERNEL_SOURCE["k_sample"]:
+        p = dst / name
+        body = p.read_bytes()
+        p.write_bytes(body + b"\n")
+        assert bench.source_hash("k_sample") != h0, name
+        p.write_bytes(body)
+    assert bench.source_hash("k_sample") == h0
+    monkeypatch.setitem(bench.NCU_TRAFFIC_PER_SAMPLE, ("k_sample", "probe"), (1, h0))
+    assert bench.ncu_traffic_per_sample("k_sample", "probe")[0] == 1
+    monkeypatch.setitem(bench.NCU_TRAFFIC_PER_SAMPLE, ("k_sample", "probe"), (1, "0" * 16))
+    assert bench.ncu_traffic_per_sample("k_sample", "probe")[0] is None
