@@ -1,6 +1,8 @@
-"""Host logic of bench.py's multi-GPU path (replicas, one query stream per
-rank): run as two gloo ranks on the CPU.  The whole-job value takes the slowest
-rank's time and the samples of every rank; the reference arm runs on rank 0 only."""
+"""Host logic of bench.py.  The multi-GPU path (replicas, one query stream per
+rank) runs as two gloo ranks on the CPU: the whole-job value takes the slowest
+rank's time and the samples of every rank; the reference arm runs on rank 0 only.
+The ncu traffic figures are reported only for the kernel source they were
+measured on."""
 import os
 import socket
 import sys
